@@ -1,0 +1,395 @@
+"""FP64 CPU oracle for the memory-efficient INR gradient for CT.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously correct
+statement of what the CUDA path computes, written from the paper.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It shares no code with the product package and
+never imports it; both sides only consume the same seeded inputs.
+
+Contents, each following the passage named in its docstring:
+
+* grid coordinates (Sec. 3: regular grid x_1..x_n inside the FOV);
+* the INR f_theta: Fourier-feature ReLU MLP and SIREN (Sec. 4, the two
+  architectures with a forward/backward we can write out), with a
+  hand-derived reverse mode;
+* the Joseph projector P and its transpose (``joseph.c``; Sec. 3 writes the
+  projection as P E{f});
+* the LS loss and its residual (Sec. 2, Sec. 3 note after Algorithm 1);
+* the full chain-rule gradient (Sec. 3, the sum over all n grid points);
+* the subsampled estimator, Eq. (2), and the virtual loss, Eq. (3);
+* Algorithm 1 composed with an Adam update (Sec. 4 trains with Adam).
+
+Everything is FP64.  Parity pins: see ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "joseph.c")
+
+PAR2D, FAN2D, CONE3D = 0, 1, 2
+_KIND = {"par2d": PAR2D, "fan2d": FAN2D, "cone3d": CONE3D}
+
+
+def build(force: bool = False) -> str:
+    """Compile ``joseph.c`` into ``liboracle.so`` with gcc (FP64, no FMA contraction)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-std=c11", _SRC, "-o", _SO + ".tmp", "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("N", ctypes.c_int), ("V", ctypes.c_int),
+                ("A", ctypes.c_int), ("B", ctypes.c_int),
+                ("du", ctypes.c_double), ("dv", ctypes.c_double),
+                ("sod", ctypes.c_double), ("sdd", ctypes.c_double),
+                ("angle0", ctypes.c_double), ("span", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        g = ctypes.POINTER(_Geom)
+        _lib.orc_project.argtypes = [g, dp, dp]
+        _lib.orc_backproject.argtypes = [g, dp, dp]
+        _lib.orc_project_at.argtypes = [g, dp, ctypes.c_int64, i64p, dp]
+        _lib.orc_backproject_at.argtypes = [g, dp, ctypes.c_int64, i64p, dp]
+        _lib.orc_matrix_entry.argtypes = [g, ctypes.c_int64, ctypes.c_int64]
+        _lib.orc_matrix_entry.restype = ctypes.c_double
+        _lib.orc_num_rays.argtypes = [g]
+        _lib.orc_num_rays.restype = ctypes.c_int64
+        _lib.orc_ray.argtypes = [g, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+    return _lib
+
+
+# ----------------------------------------------------------------------------
+# Geometry (Sec. 3: P in R^{m x n}; conventions are readings, listed in DESIGN)
+# ----------------------------------------------------------------------------
+@dataclass
+class Geometry:
+    """Scan geometry.  Lengths in pixel units at the isocentre; angles in radians.
+
+    kind: 'par2d' | 'fan2d' | 'cone3d'.  N: grid side.  V: views over
+    [angle0, angle0 + span).  A: detector bins (columns).  B: detector rows
+    (cone only).  du, dv: bin pitch at the isocentre in pixels.  sod, sdd:
+    source-to-isocentre and source-to-detector distances in pixels.
+    """
+    kind: str
+    N: int
+    V: int
+    A: int
+    B: int = 1
+    du: float = 1.0
+    dv: float = 1.0
+    sod: float = 1000.0
+    sdd: float = 1500.0
+    angle0: float = 0.0
+    span: float = float(np.pi)
+
+    @property
+    def d(self) -> int:
+        return 3 if self.kind == "cone3d" else 2
+
+    @property
+    def n(self) -> int:
+        return self.N ** self.d
+
+    @property
+    def m(self) -> int:
+        return self.V * (self.B if self.kind == "cone3d" else 1) * self.A
+
+    @property
+    def sino_shape(self):
+        return (self.V, self.B, self.A) if self.kind == "cone3d" else (self.V, self.A)
+
+    @property
+    def img_shape(self):
+        return (self.N,) * self.d
+
+    def _c(self) -> _Geom:
+        return _Geom(_KIND[self.kind], self.N, self.V, self.A,
+                     self.B if self.kind == "cone3d" else 1,
+                     self.du, self.dv, self.sod, self.sdd, self.angle0, self.span)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def project(g: Geometry, img) -> np.ndarray:
+    """z = P x for every ray (Sec. 3).  img: shape (N,)*d or flat; returns flat [m]."""
+    x = np.ascontiguousarray(np.asarray(img, dtype=np.float64).reshape(-1))
+    assert x.size == g.n
+    z = np.empty(g.m, dtype=np.float64)
+    gc = g._c()
+    _L().orc_project(ctypes.byref(gc), _dp(x), _dp(z))
+    return z
+
+
+def backproject(g: Geometry, sino) -> np.ndarray:
+    """v = P^T r (Sec. 3, v = P^T r), as the literal transpose of ``project``."""
+    r = np.ascontiguousarray(np.asarray(sino, dtype=np.float64).reshape(-1))
+    assert r.size == g.m
+    v = np.empty(g.n, dtype=np.float64)
+    gc = g._c()
+    _L().orc_backproject(ctypes.byref(gc), _dp(r), _dp(v))
+    return v
+
+
+def project_at(g: Geometry, img, rays) -> np.ndarray:
+    """(P x)_r for the listed flat ray indices."""
+    x = np.ascontiguousarray(np.asarray(img, dtype=np.float64).reshape(-1))
+    rr = np.ascontiguousarray(np.asarray(rays, dtype=np.int64))
+    out = np.empty(rr.size, dtype=np.float64)
+    gc = g._c()
+    _L().orc_project_at(ctypes.byref(gc), _dp(x), rr.size,
+                        rr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
+    return out
+
+
+def backproject_at(g: Geometry, sino, pix) -> np.ndarray:
+    """(P^T r)_i for the listed flat pixel indices, from the matrix entries directly."""
+    r = np.ascontiguousarray(np.asarray(sino, dtype=np.float64).reshape(-1))
+    pp = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
+    out = np.empty(pp.size, dtype=np.float64)
+    gc = g._c()
+    _L().orc_backproject_at(ctypes.byref(gc), _dp(r), pp.size,
+                            pp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
+    return out
+
+
+def matrix_entry(g: Geometry, ray: int, pix: int) -> float:
+    gc = g._c()
+    return _L().orc_matrix_entry(ctypes.byref(gc), int(ray), int(pix))
+
+
+def ray(g: Geometry, k: int, row: int, col: int):
+    """(point, unit direction) of one ray, both length-3 arrays."""
+    s = np.zeros(3)
+    e = np.zeros(3)
+    gc = g._c()
+    _L().orc_ray(ctypes.byref(gc), k, row, col, _dp(s), _dp(e))
+    return s, e
+
+
+# ----------------------------------------------------------------------------
+# Grid (Sec. 3: regular grid of coordinates x_1..x_n in [-1, 1]^d)
+# ----------------------------------------------------------------------------
+def grid_coords(d: int, N: int, idx=None) -> np.ndarray:
+    """Pixel/voxel centres c_k = -1 + (k + 1/2) 2/N; flat index row-major, x fastest.
+
+    Returns an (n, d) FP64 array whose column 0 is x, 1 is y, 2 is z.
+    """
+    if idx is None:
+        idx = np.arange(N ** d, dtype=np.int64)
+    idx = np.asarray(idx, dtype=np.int64)
+    c = lambda k: -1.0 + (k.astype(np.float64) + 0.5) * (2.0 / N)
+    cols = [c(idx % N), c((idx // N) % N)]
+    if d == 3:
+        cols.append(c(idx // (N * N)))
+    return np.stack(cols, axis=1)
+
+
+# ----------------------------------------------------------------------------
+# INR f_theta (Sec. 4: Fourier-feature ReLU networks and SIREN)
+# ----------------------------------------------------------------------------
+@dataclass
+class Arch:
+    """INR architecture.
+
+    kind 'ffn':   gamma(x) = [cos(2 pi B x), sin(2 pi B x)] (F features each),
+                  then n_hidden layers Linear + ReLU of the given width, then
+                  Linear(width, 1).
+    kind 'siren': n_hidden layers h = sin(omega0 (W h + b)) (the first takes
+                  x itself), then Linear(width, 1).
+    theta layout: for every layer in order, W row-major [out][in], then b [out].
+    """
+    kind: str
+    d: int
+    width: int
+    n_hidden: int
+    n_feat: int = 0
+    B: np.ndarray | None = None   # F x d, FFN only
+    omega0: float = 30.0
+
+    @property
+    def d_in(self) -> int:
+        return 2 * self.n_feat if self.kind == "ffn" else self.d
+
+    def layer_shapes(self):
+        shapes = [(self.width, self.d_in)]
+        shapes += [(self.width, self.width)] * (self.n_hidden - 1)
+        shapes.append((1, self.width))
+        return shapes
+
+    @property
+    def p(self) -> int:
+        return sum(o * i + o for o, i in self.layer_shapes())
+
+
+def unpack(arch: Arch, theta):
+    """Split the flat theta into [(W_l, b_l)] views in layer order."""
+    theta = np.asarray(theta, dtype=np.float64)
+    out, off = [], 0
+    for o, i in arch.layer_shapes():
+        W = theta[off:off + o * i].reshape(o, i)
+        off += o * i
+        b = theta[off:off + o]
+        off += o
+        out.append((W, b))
+    assert off == theta.size, (off, theta.size)
+    return out
+
+
+def encode(arch: Arch, X: np.ndarray) -> np.ndarray:
+    """Network input: gamma(x) for FFN (cos block first, then sin), x for SIREN."""
+    X = np.asarray(X, dtype=np.float64)
+    if arch.kind == "ffn":
+        P = 2.0 * np.pi * (X @ np.asarray(arch.B, dtype=np.float64).T)
+        return np.concatenate([np.cos(P), np.sin(P)], axis=1)
+    return X
+
+
+def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False):
+    """f_theta(x_i) for every row of X.  With keep=True also returns the
+    per-layer inputs h_{l-1} and pre-activations z_l needed by ``vjp``."""
+    layers = unpack(arch, theta)
+    h = encode(arch, X)
+    hs, zs = [h], []
+    for li, (W, b) in enumerate(layers):
+        z = h @ W.T + b
+        zs.append(z)
+        if li == len(layers) - 1:
+            h = z
+        elif arch.kind == "ffn":
+            h = np.maximum(z, 0.0)
+        else:
+            h = np.sin(arch.omega0 * z)
+        hs.append(h)
+    f = h[:, 0]
+    return (f, hs, zs) if keep else f
+
+
+def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """sum_i w_i grad_theta f_theta(x_i), by reverse mode written out layer by layer.
+
+    This is the Jacobian-transpose product [d E{f}/d theta]^T w of Sec. 3.
+    ReLU'(0) is taken as 0.
+    """
+    layers = unpack(arch, theta)
+    _, hs, zs = forward(arch, theta, X, keep=True)
+    w = np.asarray(w, dtype=np.float64)
+    grads = [None] * len(layers)
+    # df/dz_out = 1, weighted per point by w_i
+    delta = w[:, None]                                  # (n, 1)
+    for li in range(len(layers) - 1, -1, -1):
+        W, _ = layers[li]
+        h_in = hs[li]
+        grads[li] = (delta.T @ h_in, delta.sum(axis=0))   # dW = delta^T h, db = sum delta
+        if li == 0:
+            break
+        g_h = delta @ W                                 # dL/dh_{li}
+        z_prev = zs[li - 1]
+        if arch.kind == "ffn":
+            delta = g_h * (z_prev > 0.0)
+        else:
+            delta = g_h * (arch.omega0 * np.cos(arch.omega0 * z_prev))
+    flat = []
+    for gW, gb in grads:
+        flat.append(gW.reshape(-1))
+        flat.append(gb.reshape(-1))
+    return np.concatenate(flat)
+
+
+# ----------------------------------------------------------------------------
+# Loss, full gradient, estimator (Sec. 2, Sec. 3, Eq. (2), Eq. (3), Algorithm 1)
+# ----------------------------------------------------------------------------
+def ls_loss(z, y):
+    """L_LS(z, y) = 1/2 ||z - y||^2 and its gradient r = z - y (Sec. 2; Sec. 3)."""
+    r = np.asarray(z, dtype=np.float64) - np.asarray(y, dtype=np.float64)
+    return 0.5 * float(r @ r), r
+
+
+def evaluate_image(arch: Arch, theta, g: Geometry) -> np.ndarray:
+    """E{f_theta} = [f(x_1) .. f(x_n)] on the full grid (Sec. 3), flat."""
+    return forward(arch, theta, grid_coords(g.d, g.N))
+
+
+def backprojected_residual(arch: Arch, theta, g: Geometry, y):
+    """Algorithm 1, steps 1-2: z = P E{f}, v = P^T dL/dz.  Returns (L, z, r, v)."""
+    x = evaluate_image(arch, theta, g)
+    z = project(g, x)
+    L, r = ls_loss(z, y)
+    v = backproject(g, r)
+    return L, z, r, v
+
+
+def full_gradient(arch: Arch, theta, g: Geometry, y):
+    """grad L(theta) = sum_{i=1..n} v_i grad f(x_i) (Sec. 3).  Returns (L, grad, v)."""
+    L, _, _, v = backprojected_residual(arch, theta, g, y)
+    grad = vjp(arch, theta, grid_coords(g.d, g.N), v)
+    return L, grad, v
+
+
+def estimator(arch: Arch, theta, g: Geometry, v, I, scale=None) -> np.ndarray:
+    """Eq. (2): (n/|I|) sum_{i in I} v_i grad f(x_i), for the given index set I.
+
+    ``scale`` defaults to n/|I|; v is the backprojected residual (P^T r).
+    """
+    I = np.asarray(I, dtype=np.int64)
+    n = g.n
+    if scale is None:
+        scale = n / I.size
+    X = grid_coords(g.d, g.N, I)
+    return vjp(arch, theta, X, scale * np.asarray(v, dtype=np.float64)[I])
+
+
+def virtual_loss(arch: Arch, theta, g: Geometry, v, I, scale=None) -> float:
+    """Eq. (3): (n/|I|) sum_{i in I} v_i f(x_i), with v held constant."""
+    I = np.asarray(I, dtype=np.int64)
+    if scale is None:
+        scale = g.n / I.size
+    X = grid_coords(g.d, g.N, I)
+    return float(scale * (np.asarray(v, dtype=np.float64)[I] @ forward(arch, theta, X)))
+
+
+@dataclass
+class AdamState:
+    m: np.ndarray
+    s: np.ndarray
+    t: int = 0
+
+
+def adam_step(theta, grad, st: AdamState, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update with bias correction (Kingma & Ba; the paper trains with Adam
+    and gives no hyper-parameters, so these are the usual defaults)."""
+    st.t += 1
+    st.m = beta1 * st.m + (1.0 - beta1) * grad
+    st.s = beta2 * st.s + (1.0 - beta2) * grad * grad
+    mhat = st.m / (1.0 - beta1 ** st.t)
+    shat = st.s / (1.0 - beta2 ** st.t)
+    return theta - lr * mhat / (np.sqrt(shat) + eps)
+
+
+def grad_step(arch: Arch, theta, g: Geometry, y, I, st: AdamState, lr: float,
+              scale=None, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Algorithm 1 followed by an Adam update.  Returns (new_theta, L, ghat)."""
+    L, _, _, v = backprojected_residual(arch, theta, g, y)
+    ghat = estimator(arch, theta, g, v, I, scale)
+    return adam_step(theta, ghat, st, lr, beta1, beta2, eps), L, ghat
