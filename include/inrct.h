@@ -1,0 +1,200 @@
+/*
+ * inrct.h -- C ABI of the GB300-native memory-efficient INR gradient for CT.
+ *
+ * The library computes, on one GPU, the stochastic gradient of an implicit
+ * neural representation (INR) fitted to CT data, following "Memory-efficient
+ * optimization of implicit neural representations for CT reconstruction"
+ * (arXiv 2604.09884):
+ *
+ *   min_theta L(P E{f_theta}, y)                         (Sec. 2, Eq. 1)
+ *   z = P E{f_theta},  v = P^T dL/dz                     (Sec. 3; Algorithm 1, steps 1-2)
+ *   g = (n/|I|) sum_{i in I} v_i grad_theta f_theta(x_i)  (Sec. 3, Eq. 2; Algorithm 1, steps 3-5)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every pointer argument to a call (image, sinogram, theta, indices,
+ *   gradients, workspace) is DEVICE memory owned by the caller, unless the
+ *   argument's comment says "host".  The library never allocates, frees or
+ *   keeps a pointer after a call returns.  Descriptor structs are host memory
+ *   and are read during the call only.
+ * - Calls are asynchronous on the given stream and return a status code.
+ *   A non-zero status means nothing was launched (argument errors) or a CUDA
+ *   launch failed; inrct_last_error() then returns a message for the calling
+ *   thread.  Status codes: see INRCT_OK..INRCT_ERR_TIMEOUT.
+ * - Grid: N^d pixels/voxels with centres c_k = -1 + (k + 1/2)(2/N) on
+ *   [-1, 1]^d; flat index i = ((iz*N) + iy)*N + ix (x fastest).
+ * - Sinogram layout: 2-D [view][bin]; 3-D [view][row v][column u].
+ * - theta layout: for every layer in order, W row-major [out][in] then b[out].
+ *   FFN: Linear(2F -> w) + ReLU, (n_hidden - 1) x [Linear(w -> w) + ReLU],
+ *   Linear(w -> 1).  SIREN: sin(omega0 (W x + b)) layers, same count, then
+ *   Linear(w -> 1).
+ * - Scratch memory is passed as (ws, ws_bytes); each call documents how to
+ *   size it.  Workspace contents need not be initialised.
+ */
+#ifndef INRCT_H
+#define INRCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cudaStream_t;
+
+/* status codes */
+#define INRCT_OK 0
+#define INRCT_ERR_INVALID_ARG 1
+#define INRCT_ERR_UNSUPPORTED 2
+#define INRCT_ERR_WORKSPACE 3
+#define INRCT_ERR_CUDA 4
+#define INRCT_ERR_TIMEOUT 5
+
+/* geometry kinds */
+#define INRCT_PAR2D 0  /* 2-D parallel beam */
+#define INRCT_FAN2D 1  /* 2-D fan beam, equiangular (curved) detector */
+#define INRCT_CONE3D 2 /* 3-D circular cone beam, flat panel */
+
+/* INR kinds and arithmetic of the MLP */
+#define INRCT_FFN_RELU 0 /* Gaussian Fourier features + ReLU MLP */
+#define INRCT_SIREN 1    /* sine-activated MLP */
+#define INRCT_FP32 0     /* SIMT FP32 path (the plain comparator) */
+#define INRCT_BF16 1     /* tcgen05 BF16 x BF16 -> FP32 tensor-core path */
+
+/* loss kinds */
+#define INRCT_LOSS_LS 0  /* 1/2 ||z - y||^2, dL/dz = z - y (Sec. 2) */
+#define INRCT_LOSS_FLS 1 /* 1/2 (z-y)^T F (z-y), dL/dz = F (z - y), F = ramp filter (Sec. 2) */
+
+/*
+ * Scan geometry (the discrete projector P of Sec. 3; the paper does not fix a
+ * projector model, this library implements Joseph's ray-driven interpolation).
+ * Lengths are in pixel units at the isocentre, angles in radians.
+ *   view angle k:  angle0 + angle_span * k / n_views
+ *   PAR2D:  bin b lies at (b - (n_bins_u-1)/2) * du pixels from the centre.
+ *   FAN2D:  source at distance sod; fan angle of bin b is (b - (n_bins_u-1)/2) * du / sod.
+ *   CONE3D: source at distance sod, flat panel at distance sdd from the source,
+ *           pitches du, dv measured at the isocentre; n_bins_v rows.
+ */
+typedef struct {
+  int kind;
+  int n_views;
+  int n_bins_u;
+  int n_bins_v; /* 1 for 2-D */
+  double du, dv;
+  double sod, sdd;
+  double angle0, angle_span;
+} inrct_geom;
+
+/* Grid: d in {2, 3}, N pixels per side. */
+typedef struct {
+  int d;
+  int N;
+} inrct_grid;
+
+/*
+ * INR architecture (Sec. 4 uses FFN, SIREN and hash-encoded MLPs; FFN and
+ * SIREN are implemented).  B: device pointer, n_feat x d FP32 row-major
+ * Fourier matrix (FFN only; may be NULL for SIREN).  The FFN input is
+ * [cos(2 pi B x); sin(2 pi B x)] (cos block first).
+ */
+typedef struct {
+  int kind;    /* INRCT_FFN_RELU or INRCT_SIREN */
+  int d;       /* input dimension, equals the grid's */
+  int n_feat;  /* F, FFN only */
+  const float* B;
+  float omega0; /* SIREN only */
+  int n_hidden; /* number of nonlinear layers */
+  int width;    /* hidden width */
+  int prec;     /* INRCT_FP32 or INRCT_BF16 */
+} inrct_mlp;
+
+/* Adam hyper-parameters; t is the 1-based index of the step being taken. */
+typedef struct {
+  double lr, beta1, beta2, eps;
+  int64_t t;
+} inrct_adam;
+
+/* ------------------------------------------------------------------------ */
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* inrct_last_error(void);
+
+/* Number of parameters p of an MLP descriptor (0 if invalid). */
+int64_t inrct_num_params(const inrct_mlp* mlp);
+
+/* Number of rays m = views x rows x bins (0 if invalid). */
+int64_t inrct_num_rays(const inrct_geom* geom);
+
+/* ------------------------------------------------------------------------ */
+/*
+ * project -- z = P x (Sec. 3; Algorithm 1, step 1, "no gradient tracking").
+ *   image[n] FP32 in, sino[m] FP32 out (overwritten).
+ *   Optional loss epilogue (Sec. 2, LS loss): if y != NULL, also writes
+ *   resid[m] = z - y and loss_out[0] = 1/2 sum (z - y)^2 (one FP64 device
+ *   scalar, overwritten); resid and loss_out may be NULL when y is NULL.
+ *   ws: at least inrct_project_ws_bytes(geom, grid) bytes.
+ */
+size_t inrct_project_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
+int project(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
+            const float* y, float* resid, double* loss_out, void* ws, size_t ws_bytes,
+            cudaStream_t stream);
+
+/*
+ * backproject -- v = P^T r (Sec. 3, v = P^T r; Algorithm 1, step 2), the exact
+ * adjoint of project (same interpolation weights), in gather form: every
+ * pixel sums its own contributions, so the result is deterministic.
+ *   sino[m] FP32 in, image[n] FP32 out (overwritten, not accumulated).
+ *   ws: at least inrct_backproject_ws_bytes(geom, grid) bytes.
+ */
+size_t inrct_backproject_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
+int backproject(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
+                void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * inr_eval_grid -- E{f_theta} = [f(x_1) .. f(x_n)] on the full grid (Sec. 3).
+ *   theta[p] FP32 in; image[n] FP32 out.  mlp->prec picks the FP32 SIMT or the
+ *   BF16 tcgen05 path.  ws: at least inrct_eval_ws_bytes(mlp, grid) bytes.
+ */
+size_t inrct_eval_ws_bytes(const inrct_mlp* mlp, const inrct_grid* grid);
+int inr_eval_grid(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid, float* image,
+                  void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * inr_weighted_vjp -- scale * sum_{k < n_idx} v[idx[k]] grad_theta f(x_{idx[k]})
+ * (Sec. 3, Eq. 2 with scale = n/|I|; equivalently the gradient of the virtual
+ * loss of Eq. 3).  Activations are recomputed for the listed points only, so
+ * scratch grows with n_idx, never with the grid.
+ *   idx[n_idx] int32 flat grid indices (any order, repeats allowed), each in
+ *   [0, n); v[n] FP32 (the backprojected residual on the whole grid).
+ *   grad_f64[p] FP64 out (overwritten); grad_f32[p] FP32 out, may be NULL.
+ *   ws: at least inrct_vjp_ws_bytes(mlp, grid, n_idx) bytes.
+ *   n_idx = 0 is INRCT_ERR_INVALID_ARG.
+ */
+size_t inrct_vjp_ws_bytes(const inrct_mlp* mlp, const inrct_grid* grid, int64_t n_idx);
+int inr_weighted_vjp(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid,
+                     const int32_t* idx, int64_t n_idx, const float* v, double scale,
+                     double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes,
+                     cudaStream_t stream);
+
+/*
+ * grad_step -- Algorithm 1 followed by one Adam update (Sec. 4 trains with Adam):
+ *   x = E{f_theta}; z = P x; r = dL/dz; v = P^T r; g = scale * sum_{i in I} v_i grad f(x_i);
+ *   theta <- Adam(theta, g).
+ *   theta[p] FP32 in/out; y[m] FP32; idx[n_idx] int32; adam_m, adam_s[p] FP32
+ *   in/out (zero before the first step); loss_out: one FP64 device scalar
+ *   (the loss at the incoming theta), may be NULL; grad_out[p] FP64 device
+ *   copy of g, may be NULL.  loss selects LS or FLS.  If adam is NULL theta
+ *   is not updated.  ws: at least inrct_step_ws_bytes(...) bytes.
+ */
+size_t inrct_step_ws_bytes(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* mlp,
+                           int64_t n_idx);
+int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* mlp, int loss,
+              float* theta, const float* y, const int32_t* idx, int64_t n_idx, double scale,
+              const inrct_adam* adam, float* adam_m, float* adam_s, double* loss_out,
+              double* grad_out, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INRCT_H */

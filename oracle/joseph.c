@@ -15,7 +15,8 @@
  *   grid      N^d pixel/voxel centres c_k = -1 + (k + 1/2) * D, D = 2/N,
  *             flat index i = ((iz*N) + iy)*N + ix  (row-major, x fastest).
  *   ray       point s, unit direction e.
- *   driving   axis a = argmax_k |e_k|, ties to the lowest axis (x, y, z).
+ *   driving   axis a = argmax_k |e_k|, ties (within a relative 1e-12) to the
+ *             lowest axis (x, y, z).
  *   sum       for every slice j = 0..N-1 of axis a: intersect the ray with the
  *             plane/line x_a = c_j, convert the transverse coordinates to
  *             fractional indices u = (p + 1)/D - 1/2, interpolate linearly
@@ -106,10 +107,16 @@ static int64_t flat_index(int d, int N, const int idx[3]) {
   return ((int64_t)idx[2] * N + idx[1]) * N + idx[0];
 }
 
+/*
+ * Driving axis: the axis of largest |e_k|.  An axis only wins over a lower one
+ * when it is larger by more than a relative 1e-12, so that rays at exactly 45
+ * degrees (whose components agree up to the rounding of cos/sin) drive the
+ * lowest axis whatever the platform's trigonometric rounding.
+ */
 static int driving_axis(int d, const double e[3]) {
   int a = 0;
   for (int q = 1; q < d; q++)
-    if (fabs(e[q]) > fabs(e[a])) a = q;
+    if (fabs(e[q]) > fabs(e[a]) * (1.0 + 1e-12)) a = q;
   return a;
 }
 
