@@ -152,6 +152,21 @@ int backproject(const inrct_geom* geom, const inrct_grid* grid, const float* sin
                 void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /*
+ * ramp_filter -- out = F r and loss_out[0] = 1/2 r^T F r for the filtered
+ * least-squares loss (Sec. 2: L_FLS = 1/2 (z-y)^T F (z-y), F a ramp filter
+ * along the detector rows; Sec. 3: dL/dz = F (z - y)).  F convolves every
+ * detector row (one view; one detector row v for the cone) along the bin axis
+ * with the Ram-Lak kernel sampled at tau = du * 2/N:
+ * (F r)_b = tau sum_k h[k] r_{b-k}, h[0] = 1/(4 tau^2), h[odd k] = -1/(pi^2 k^2 tau^2),
+ * h[even k != 0] = 0, zero outside the detector.
+ *   r[m] FP32 in, out[m] FP32 out (must not alias r), loss_out one FP64 device
+ *   scalar.  At most 6144 bins per row.  ws: inrct_ramp_ws_bytes(geom, grid).
+ */
+size_t inrct_ramp_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
+int ramp_filter(const inrct_geom* geom, const inrct_grid* grid, const float* r, float* out,
+                double* loss_out, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
  * inr_eval_grid -- E{f_theta} = [f(x_1) .. f(x_n)] on the full grid (Sec. 3).
  *   theta[p] FP32 in; image[n] FP32 out.  mlp->prec picks the FP32 SIMT or the
  *   BF16 tcgen05 path.  ws: at least inrct_eval_ws_bytes(mlp, grid) bytes.
@@ -166,7 +181,9 @@ int inr_eval_grid(const inrct_mlp* mlp, const float* theta, const inrct_grid* gr
  * loss of Eq. 3).  Activations are recomputed for the listed points only, so
  * scratch grows with n_idx, never with the grid.
  *   idx[n_idx] int32 flat grid indices (any order, repeats allowed), each in
- *   [0, n); v[n] FP32 (the backprojected residual on the whole grid).
+ *   [0, n); an index outside [0, n) contributes nothing (it is not checked on
+ *   the host, which would need a device-to-host copy).  v[n] FP32 (the
+ *   backprojected residual on the whole grid).
  *   grad_f64[p] FP64 out (overwritten); grad_f32[p] FP32 out, may be NULL.
  *   ws: at least inrct_vjp_ws_bytes(mlp, grid, n_idx) bytes.
  *   n_idx = 0 is INRCT_ERR_INVALID_ARG.

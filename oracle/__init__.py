@@ -17,7 +17,8 @@ Contents, each following the passage named in its docstring:
 * the LS loss and its residual (Sec. 2, Sec. 3 note after Algorithm 1);
 * the full chain-rule gradient (Sec. 3, the sum over all n grid points);
 * the subsampled estimator, Eq. (2), and the virtual loss, Eq. (3);
-* Algorithm 1 composed with an Adam update (Sec. 4 trains with Adam).
+* Algorithm 1 composed with an Adam update (Sec. 4 trains with Adam);
+* the ramp filter F of the FLS loss (Sec. 2) as a plain convolution.
 
 Everything is FP64.  Parity pins: see ``tests/test_oracle_*.py``.
 """
@@ -393,3 +394,37 @@ def grad_step(arch: Arch, theta, g: Geometry, y, I, st: AdamState, lr: float,
     L, _, _, v = backprojected_residual(arch, theta, g, y)
     ghat = estimator(arch, theta, g, v, I, scale)
     return adam_step(theta, ghat, st, lr, beta1, beta2, eps), L, ghat
+
+
+# ----------------------------------------------------------------------------
+# FLS loss (Sec. 2: L_FLS(z, y) = 1/2 (z - y)^T F (z - y), F a ramp filter)
+# ----------------------------------------------------------------------------
+def ramp_kernel(A: int, tau: float) -> np.ndarray:
+    """Band-limited ramp (Ram-Lak) taps h[k], k = -(A-1)..(A-1), sampled at pitch tau
+    (Kak & Slaney's FBP kernel): h[0] = 1/(4 tau^2), h[odd k] = -1/(pi^2 k^2 tau^2),
+    h[even k != 0] = 0."""
+    k = np.arange(-(A - 1), A)
+    h = np.zeros(k.size)
+    h[k == 0] = 1.0 / (4 * tau * tau)
+    odd = (k % 2) != 0
+    h[odd] = -1.0 / (np.pi ** 2 * k[odd].astype(np.float64) ** 2 * tau * tau)
+    return h
+
+
+def ramp_filter(g: Geometry, r) -> np.ndarray:
+    """F r: every detector row (one view; one row v for the cone) convolved along the
+    bin axis with tau * h, tau = du * D, bins outside the detector taken as zero."""
+    tau = g.du * 2.0 / g.N
+    rows = np.asarray(r, dtype=np.float64).reshape(-1, g.A)
+    h = ramp_kernel(g.A, tau)
+    # full convolution of a length-A row with the length-(2A-1) kernel; the entries
+    # aligned with the detector bins are those from index A-1 to 2A-2
+    out = np.stack([tau * np.convolve(row, h)[g.A - 1:2 * g.A - 1] for row in rows])
+    return out.reshape(-1)
+
+
+def fls_loss(g: Geometry, z, y):
+    """L_FLS = 1/2 (z - y)^T F (z - y) and its gradient F (z - y) (Sec. 3)."""
+    d = np.asarray(z, dtype=np.float64) - np.asarray(y, dtype=np.float64)
+    Fd = ramp_filter(g, d)
+    return 0.5 * float(d @ Fd), Fd

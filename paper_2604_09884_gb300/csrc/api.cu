@@ -1,0 +1,229 @@
+// C-ABI entry points (include/inrct.h): argument checks, workspace carving and
+// the composition of Algorithm 1 (Sec. 3) with an Adam update.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "filter.cuh"
+#include "mlp.cuh"
+#include "projector.cuh"
+
+namespace inrct {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+static bool use_tc(const inrct_mlp* mlp) { return mlp->prec == INRCT_BF16; }
+
+static size_t eval_ws(const inrct_mlp* mlp, const Net& n) {
+  return use_tc(mlp) ? tc_eval_ws_bytes(n) : simt_eval_ws_bytes(n);
+}
+
+static size_t vjp_ws(const inrct_mlp* mlp, const Net& n, int64_t n_idx) {
+  return use_tc(mlp) ? tc_vjp_ws_bytes(n, n_idx) : simt_vjp_ws_bytes(n, n_idx);
+}
+
+static int check_tc(const inrct_mlp* mlp, const Net& n) {
+  if (!use_tc(mlp)) return INRCT_OK;
+  char why[256];
+  if (!tc_supported(n, why, sizeof(why))) {
+    set_error("BF16 tensor-core path: %s", why);
+    return INRCT_ERR_UNSUPPORTED;
+  }
+  return INRCT_OK;
+}
+
+static int eval_dispatch(const inrct_mlp* mlp, const Net& n, const float* theta, int N, int64_t npts,
+                         float* image, void* ws, size_t ws_bytes, cudaStream_t st) {
+  return use_tc(mlp) ? tc_eval(n, theta, N, npts, image, ws, ws_bytes, st)
+                     : simt_eval(n, theta, N, npts, image, ws, ws_bytes, st);
+}
+
+static int vjp_dispatch(const inrct_mlp* mlp, const Net& n, const float* theta, int N,
+                        const int32_t* idx, int64_t n_idx, const float* v, double scale,
+                        double* g64, float* g32, void* ws, size_t ws_bytes, cudaStream_t st) {
+  return use_tc(mlp) ? tc_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, ws, ws_bytes, st)
+                     : simt_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, ws, ws_bytes, st);
+}
+
+}  // namespace inrct
+
+using namespace inrct;
+
+extern "C" {
+
+const char* inrct_last_error(void) { return g_err; }
+
+int64_t inrct_num_params(const inrct_mlp* mlp) {
+  Net n;
+  if (make_net(mlp, nullptr, &n) != INRCT_OK) return 0;
+  return n.p;
+}
+
+int64_t inrct_num_rays(const inrct_geom* geom) { return num_rays(geom); }
+
+size_t inrct_project_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
+  return project_ws_bytes(geom, grid);
+}
+
+int project(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
+            const float* y, float* resid, double* loss_out, void* ws, size_t ws_bytes,
+            cudaStream_t stream) {
+  clear_error();
+  return project_impl(geom, grid, image, sino, y, resid, loss_out, ws, ws_bytes, stream);
+}
+
+size_t inrct_backproject_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
+  return backproject_ws_bytes(geom, grid);
+}
+
+int backproject(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
+                void* ws, size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  return backproject_impl(geom, grid, sino, image, ws, ws_bytes, stream);
+}
+
+size_t inrct_ramp_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
+  if (check_geom(geom, grid) != INRCT_OK) return 0;
+  return ramp_ws_bytes(geom);
+}
+
+int ramp_filter(const inrct_geom* geom, const inrct_grid* grid, const float* r, float* out,
+                double* loss_out, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  return ramp_filter_impl(geom, grid, r, out, loss_out, ws, ws_bytes, stream);
+}
+
+size_t inrct_eval_ws_bytes(const inrct_mlp* mlp, const inrct_grid* grid) {
+  Net n;
+  if (!grid || make_net(mlp, grid, &n) != INRCT_OK) return 0;
+  return eval_ws(mlp, n);
+}
+
+int inr_eval_grid(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid, float* image,
+                  void* ws, size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  INRCT_REQUIRE(grid && grid->N > 0 && grid->N <= 4096, "invalid grid");
+  INRCT_REQUIRE(theta && image, "theta and image must not be NULL");
+  Net n;
+  INRCT_TRY(make_net(mlp, grid, &n));
+  INRCT_TRY(check_tc(mlp, n));
+  return eval_dispatch(mlp, n, theta, grid->N, grid_points(grid), image, ws, ws_bytes, stream);
+}
+
+size_t inrct_vjp_ws_bytes(const inrct_mlp* mlp, const inrct_grid* grid, int64_t n_idx) {
+  Net n;
+  if (!grid || n_idx <= 0 || make_net(mlp, grid, &n) != INRCT_OK) return 0;
+  return vjp_ws(mlp, n, n_idx);
+}
+
+int inr_weighted_vjp(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid,
+                     const int32_t* idx, int64_t n_idx, const float* v, double scale,
+                     double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes,
+                     cudaStream_t stream) {
+  clear_error();
+  INRCT_REQUIRE(grid && grid->N > 0 && grid->N <= 4096, "invalid grid");
+  INRCT_REQUIRE(n_idx > 0, "n_idx must be positive (got %lld)", (long long)n_idx);
+  INRCT_REQUIRE(n_idx <= (int64_t)1 << 31, "n_idx too large");
+  INRCT_REQUIRE(theta && idx && v && grad_f64, "theta, idx, v and grad_f64 must not be NULL");
+  Net n;
+  INRCT_TRY(make_net(mlp, grid, &n));
+  INRCT_TRY(check_tc(mlp, n));
+  return vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, v, scale, grad_f64, grad_f32, ws,
+                      ws_bytes, stream);
+}
+
+// grad_step workspace: x[n], z[m], r[m], v[n], grad[p] (FP64), loss (FP64), then
+// one region reused by each stage (the largest stage need).
+struct StepWs {
+  float *x, *z, *r, *v;
+  double *g, *loss;
+  void* stage;
+  size_t stage_bytes;
+};
+
+static size_t step_layout(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* mlp,
+                          const Net& n, int64_t n_idx, int loss, void* ws, size_t cap, StepWs* out,
+                          bool* ok) {
+  Carver c(ws, cap);
+  StepWs w;
+  const int64_t npix = grid_points(grid), m = num_rays(geom);
+  w.x = c.take<float>(npix);
+  w.z = c.take<float>(m);
+  w.r = c.take<float>(m);
+  w.v = c.take<float>(npix);
+  w.g = c.take<double>(n.p);
+  w.loss = c.take<double>(1);
+  size_t st = project_ws_bytes(geom, grid);
+  st = std::max(st, backproject_ws_bytes(geom, grid));
+  st = std::max(st, eval_ws(mlp, n));
+  st = std::max(st, vjp_ws(mlp, n, n_idx));
+  if (loss == INRCT_LOSS_FLS) st = std::max(st, ramp_ws_bytes(geom));
+  w.stage_bytes = st;
+  w.stage = c.take<char>(st);
+  if (out) *out = w;
+  if (ok) *ok = c.ok;
+  return c.off + 256;
+}
+
+size_t inrct_step_ws_bytes(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* mlp,
+                           int64_t n_idx) {
+  Net n;
+  if (check_geom(geom, grid) != INRCT_OK || make_net(mlp, grid, &n) != INRCT_OK || n_idx <= 0)
+    return 0;
+  return step_layout(geom, grid, mlp, n, n_idx, INRCT_LOSS_FLS, nullptr, 0, nullptr, nullptr);
+}
+
+int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* mlp, int loss,
+              float* theta, const float* y, const int32_t* idx, int64_t n_idx, double scale,
+              const inrct_adam* adam, float* adam_m, float* adam_s, double* loss_out,
+              double* grad_out, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  INRCT_TRY(check_geom(geom, grid));
+  Net n;
+  INRCT_TRY(make_net(mlp, grid, &n));
+  INRCT_TRY(check_tc(mlp, n));
+  INRCT_REQUIRE(loss == INRCT_LOSS_LS || loss == INRCT_LOSS_FLS, "unknown loss kind %d", loss);
+  INRCT_REQUIRE(theta && y && idx, "theta, y and idx must not be NULL");
+  INRCT_REQUIRE(n_idx > 0, "n_idx must be positive (got %lld)", (long long)n_idx);
+  StepWs w;
+  bool ok;
+  const size_t need = step_layout(geom, grid, mlp, n, n_idx, loss, ws, ws_bytes, &w, &ok);
+  if (!ws || !ok) {
+    set_error("grad_step: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  // Algorithm 1, step 1: z = P E{f_theta} (no gradient tracking); loss epilogue
+  INRCT_TRY(eval_dispatch(mlp, n, theta, grid->N, grid_points(grid), w.x, w.stage, w.stage_bytes,
+                          stream));
+  INRCT_TRY(project_impl(geom, grid, w.x, w.z, y, w.r, w.loss, w.stage, w.stage_bytes, stream));
+  // Algorithm 1, step 2: v = P^T dL/dz  (LS: z - y; FLS: F (z - y), Sec. 3)
+  if (loss == INRCT_LOSS_FLS) {
+    INRCT_TRY(ramp_filter_impl(geom, grid, w.r, w.z, w.loss, w.stage, w.stage_bytes, stream));
+    INRCT_TRY(backproject_impl(geom, grid, w.z, w.v, w.stage, w.stage_bytes, stream));
+  } else {
+    INRCT_TRY(backproject_impl(geom, grid, w.r, w.v, w.stage, w.stage_bytes, stream));
+  }
+  // steps 3-5: the index set is the caller's; gradient of the virtual loss (Eq. 3)
+  double* g = grad_out ? grad_out : w.g;
+  INRCT_TRY(vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, w.v, scale, g, nullptr, w.stage,
+                         w.stage_bytes, stream));
+  if (loss_out) {
+    cudaError_t e = cudaMemcpyAsync(loss_out, w.loss, sizeof(double), cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) {
+      set_error("loss copy: %s", cudaGetErrorString(e));
+      return INRCT_ERR_CUDA;
+    }
+  }
+  if (adam) INRCT_TRY(adam_update(theta, g, adam_m, adam_s, n.p, adam, stream));
+  return INRCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Shared helpers of the inrct CUDA library (error state, launch checks, small math).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <cstdarg>
+
+#include "../../include/inrct.h"
+
+namespace inrct {
+
+// Thread-local message of the last failing call (read by inrct_last_error()).
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define INRCT_REQUIRE(cond, ...)            \
+  do {                                      \
+    if (!(cond)) {                          \
+      ::inrct::set_error(__VA_ARGS__);      \
+      return INRCT_ERR_INVALID_ARG;         \
+    }                                       \
+  } while (0)
+
+#define INRCT_CHECK_LAUNCH(what)                                                   \
+  do {                                                                             \
+    cudaError_t e_ = cudaGetLastError();                                           \
+    if (e_ != cudaSuccess) {                                                       \
+      ::inrct::set_error("%s: %s", what, cudaGetErrorString(e_));                  \
+      return INRCT_ERR_CUDA;                                                       \
+    }                                                                              \
+  } while (0)
+
+#define INRCT_TRY(expr)           \
+  do {                            \
+    int rc_ = (expr);             \
+    if (rc_ != INRCT_OK) return rc_; \
+  } while (0)
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves aligned sub-buffers out of the caller's workspace, in order.
+struct Carver {
+  char* base;
+  size_t cap;
+  size_t off = 0;
+  bool ok = true;
+  Carver(void* b, size_t c) : base(static_cast<char*>(b)), cap(c) {}
+  template <class T>
+  T* take(size_t count, size_t align = 256) {
+    off = align_up(off, align);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    if (off > cap) ok = false;
+    return p;
+  }
+};
+
+inline int64_t grid_points(const inrct_grid* g) {
+  int64_t n = 1;
+  for (int k = 0; k < g->d; k++) n *= g->N;
+  return n;
+}
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace inrct

@@ -1,0 +1,60 @@
+// Internal interface of the MLP translation units (FP32 SIMT and BF16 tcgen05).
+#pragma once
+#include "common.cuh"
+
+namespace inrct {
+
+constexpr int kMaxLayers = 10;  // n_hidden + 1 <= kMaxLayers
+
+// Network description with theta offsets, built on the host from inrct_mlp.
+struct Net {
+  int kind;      // INRCT_FFN_RELU / INRCT_SIREN
+  int d, F, W, L;  // input dim, Fourier features, width, nonlinear layers
+  float omega0;
+  const float* B;  // device F x d
+  int K0;          // input width of layer 1 (2F or d)
+  int64_t p;       // parameter count
+  int64_t offW[kMaxLayers], offb[kMaxLayers];  // layer l = 0..L (L is the output layer)
+  int in_dim[kMaxLayers], out_dim[kMaxLayers];
+};
+
+int make_net(const inrct_mlp* mlp, const inrct_grid* grid, Net* net);
+
+// Flat grid index -> coordinate on [-1, 1] of one axis.
+__device__ __forceinline__ float grid_coord(int64_t k, float D) { return -1.f + ((float)k + 0.5f) * D; }
+
+__device__ __forceinline__ void point_coords(int64_t i, int N, int d, float* x) {
+  const float D = 2.f / (float)N;
+  x[0] = grid_coord(i % N, D);
+  x[1] = grid_coord((i / N) % N, D);
+  x[2] = d == 3 ? grid_coord(i / ((int64_t)N * N), D) : 0.f;
+}
+
+// FP32 SIMT path
+size_t simt_eval_ws_bytes(const Net& net);
+int simt_eval(const Net& net, const float* theta, int N, int64_t n, float* image, void* ws,
+              size_t ws_bytes, cudaStream_t st);
+size_t simt_vjp_ws_bytes(const Net& net, int64_t n_idx);
+int simt_vjp(const Net& net, const float* theta, int N, const int32_t* idx, int64_t n_idx,
+             const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
+             size_t ws_bytes, cudaStream_t st);
+
+// BF16 tcgen05 path
+bool tc_supported(const Net& net, char* why, size_t why_len);
+size_t tc_eval_ws_bytes(const Net& net);
+int tc_eval(const Net& net, const float* theta, int N, int64_t n, float* image, void* ws,
+            size_t ws_bytes, cudaStream_t st);
+size_t tc_vjp_ws_bytes(const Net& net, int64_t n_idx);
+int tc_vjp(const Net& net, const float* theta, int N, const int32_t* idx, int64_t n_idx,
+           const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
+           size_t ws_bytes, cudaStream_t st);
+
+// shared small kernels (optim.cu)
+int adam_update(float* theta, const double* grad, float* m, float* s, int64_t p,
+                const inrct_adam* adam, cudaStream_t st);
+int f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t st);
+
+// Points processed per VJP chunk: scratch is sized for min(n_idx, this).
+constexpr int64_t kVjpChunk = int64_t(1) << 20;
+
+}  // namespace inrct

@@ -1,0 +1,451 @@
+// FP32 SIMT path of the INR: the plain comparator of the BF16 tensor-core path.
+//
+// Computes E{f_theta} on the grid (Sec. 3) and the weighted Jacobian-transpose
+// product sum_i w_i grad_theta f(x_i) with w_i = scale * v_i at listed points
+// (Sec. 3, Eq. 2; with every grid point listed it is the full gradient).
+//
+// Layout: theta follows inrct.h (W row-major [out][in], then b).  The forward
+// reads a transposed FP32 copy W^T [in][out] so that the thread computing
+// output o reads consecutive addresses; the backward chain reads W itself for
+// the same reason.  A VJP runs per chunk of at most kVjpChunk points:
+//   1. forward at the chunk, storing the layer-1 input E and the
+//      pre-activations Z_l (scratch grows with the chunk, never with the grid);
+//   2. backward chain delta_l = (W_{l+1}^T delta_{l+1}) * sigma'(z_l), stored;
+//   3. dW_l = sum_points delta_l a_{l-1}^T and db_l = sum delta_l as a split-K
+//      SIMT GEMM with FP32 partials per split;
+//   4. FP64 reduction of the partials into the gradient (accumulated over chunks).
+#include <math.h>
+
+#include "mlp.cuh"
+
+namespace inrct {
+
+namespace {
+
+struct NetDev {
+  int kind, d, F, W, L, K0, N;
+  float omega0;
+  const float* B;
+};
+
+struct LayerOffs {
+  int64_t W[kMaxLayers], b[kMaxLayers], Wt[kMaxLayers];
+};
+
+NetDev dev_of(const Net& n, int N) {
+  NetDev d;
+  d.kind = n.kind;
+  d.d = n.d;
+  d.F = n.F;
+  d.W = n.W;
+  d.L = n.L;
+  d.K0 = n.K0;
+  d.N = N;
+  d.omega0 = n.omega0;
+  d.B = n.B;
+  return d;
+}
+
+// Offsets of the transposed copies of layers 0..L-1 inside the W^T buffer.
+int64_t wt_layout(const Net& n, LayerOffs* lo) {
+  int64_t off = 0;
+  for (int l = 0; l <= n.L; ++l) {
+    lo->W[l] = n.offW[l];
+    lo->b[l] = n.offb[l];
+    lo->Wt[l] = off;
+    if (l < n.L) off += (int64_t)n.in_dim[l] * n.out_dim[l];
+  }
+  return off;
+}
+
+__device__ __forceinline__ int64_t grid_size(const NetDev& n) {
+  return n.d == 3 ? (int64_t)n.N * n.N * n.N : (int64_t)n.N * n.N;
+}
+
+__device__ __forceinline__ float act(const NetDev& n, float z) {
+  return n.kind == INRCT_FFN_RELU ? fmaxf(z, 0.f) : sinf(n.omega0 * z);
+}
+__device__ __forceinline__ float dact(const NetDev& n, float z) {
+  return n.kind == INRCT_FFN_RELU ? (z > 0.f ? 1.f : 0.f) : n.omega0 * cosf(n.omega0 * z);
+}
+
+__global__ void transpose_w_kernel(const float* __restrict__ theta, int64_t offW, int out, int in,
+                                   float* __restrict__ Wt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)out * in) return;
+  const int k = (int)(t / out), o = (int)(t % out);
+  Wt[t] = theta[offW + (int64_t)o * in + k];
+}
+
+constexpr int TP = 16;  // points per block
+
+// Forward at npts points (grid order when idx == NULL).  Optional outputs:
+// out_f[q] = f(x_q); E[q][K0] = layer-1 input; Z[l][q][W] = pre-activations.
+__global__ void __launch_bounds__(256)
+    simt_fwd_kernel(NetDev net, LayerOffs lo, const float* __restrict__ theta,
+                    const float* __restrict__ Wt, int64_t npts, const int32_t* __restrict__ idx,
+                    float* __restrict__ out_f, float* __restrict__ E, float* __restrict__ Z) {
+  extern __shared__ float sh[];
+  __shared__ float xs[TP][3];
+  __shared__ float red[TP][8];
+  const int W = net.W, K0 = net.K0;
+  const int Kmax = K0 > W ? K0 : W;
+  float* bufA = sh;             // [TP][Kmax]
+  float* bufB = sh + TP * Kmax;  // [TP][W]
+  const int t = threadIdx.x;     // blockDim.x == W
+  const int64_t p0 = (int64_t)blockIdx.x * TP;
+  if (t < TP) {
+    const int64_t q = p0 + t;
+    int64_t i = q < npts ? (idx ? (int64_t)idx[q] : q) : 0;
+    if (i < 0 || i >= grid_size(net)) i = 0;  // out-of-range indices contribute nothing
+    float x[3];
+    point_coords(i, net.N, net.d, x);
+    xs[t][0] = x[0];
+    xs[t][1] = x[1];
+    xs[t][2] = x[2];
+  }
+  __syncthreads();
+  if (net.kind == INRCT_FFN_RELU) {
+    for (int e = t; e < TP * net.F; e += W) {
+      const int p = e / net.F, f = e % net.F;
+      const float* Bf = net.B + (int64_t)f * net.d;
+      float ph = Bf[0] * xs[p][0] + Bf[1] * xs[p][1];
+      if (net.d == 3) ph += Bf[2] * xs[p][2];
+      float s, c;
+      sincospif(2.f * ph, &s, &c);
+      bufA[p * Kmax + f] = c;
+      bufA[p * Kmax + net.F + f] = s;
+    }
+  } else {
+    for (int e = t; e < TP * net.d; e += W) bufA[(e / net.d) * Kmax + e % net.d] = xs[e / net.d][e % net.d];
+  }
+  __syncthreads();
+  if (E) {
+    for (int e = t; e < TP * K0; e += W) {
+      const int p = e / K0, k = e % K0;
+      if (p0 + p < npts) E[(p0 + p) * K0 + k] = bufA[p * Kmax + k];
+    }
+  }
+  const float* in = bufA;
+  int ld_in = Kmax, K = K0;
+  for (int l = 0; l < net.L; ++l) {
+    float acc[TP];
+    const float bias = theta[lo.b[l] + t];
+#pragma unroll
+    for (int p = 0; p < TP; ++p) acc[p] = bias;
+    const float* wt = Wt + lo.Wt[l];
+    for (int k = 0; k < K; ++k) {
+      const float w = __ldg(wt + (int64_t)k * W + t);
+#pragma unroll
+      for (int p = 0; p < TP; ++p) acc[p] = fmaf(in[p * ld_in + k], w, acc[p]);
+    }
+    float* out = (in == bufA) ? bufB : bufA;
+    const int ld_out = (out == bufA) ? Kmax : W;
+    __syncthreads();  // everyone done reading `in` (out may alias a previous input)
+#pragma unroll
+    for (int p = 0; p < TP; ++p) {
+      if (Z && p0 + p < npts) Z[((int64_t)l * npts + p0 + p) * W + t] = acc[p];
+      out[p * ld_out + t] = act(net, acc[p]);
+    }
+    __syncthreads();
+    in = out;
+    ld_in = ld_out;
+    K = W;
+  }
+  if (out_f) {
+    const float wo = theta[lo.W[net.L] + t];
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int p = 0; p < TP; ++p) {
+      float v = in[p * ld_in + t] * wo;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[p][warp] = v;
+    }
+    __syncthreads();
+    if (t < TP && p0 + t < npts) {
+      float s = theta[lo.b[net.L]];
+      for (int w = 0; w < (W >> 5); ++w) s += red[t][w];
+      out_f[p0 + t] = s;
+    }
+  }
+}
+
+// Backward chain at the chunk: delta_out = scale v_i, delta_{L-1} = delta_out w_out
+// sigma'(z_{L-1}), delta_{l-1} = (W_l^T delta_l) sigma'(z_{l-1}).
+__global__ void __launch_bounds__(256)
+    simt_bwd_kernel(NetDev net, LayerOffs lo, const float* __restrict__ theta, int64_t npts,
+                    const int32_t* __restrict__ idx, const float* __restrict__ v, float scale,
+                    const float* __restrict__ Z, float* __restrict__ Dl, float* __restrict__ dout) {
+  extern __shared__ float dsh[];  // [TP][W]
+  __shared__ float dsc[TP];
+  const int W = net.W, L = net.L;
+  const int t = threadIdx.x;
+  const int64_t p0 = (int64_t)blockIdx.x * TP;
+  if (t < TP) {
+    const int64_t q = p0 + t;
+    float s = 0.f;
+    if (q < npts) {
+      const int64_t i = idx ? (int64_t)idx[q] : q;
+      s = (i >= 0 && i < grid_size(net)) ? scale * v[i] : 0.f;
+      dout[q] = s;
+    }
+    dsc[t] = s;
+  }
+  __syncthreads();
+  const float wo = theta[lo.W[L] + t];
+#pragma unroll
+  for (int p = 0; p < TP; ++p) {
+    float d = 0.f;
+    if (p0 + p < npts) {
+      const float z = Z[((int64_t)(L - 1) * npts + p0 + p) * W + t];
+      d = dsc[p] * wo * dact(net, z);
+      Dl[((int64_t)(L - 1) * npts + p0 + p) * W + t] = d;
+    }
+    dsh[p * W + t] = d;
+  }
+  __syncthreads();
+  for (int l = L - 1; l >= 1; --l) {
+    float acc[TP];
+#pragma unroll
+    for (int p = 0; p < TP; ++p) acc[p] = 0.f;
+    const float* Wl = theta + lo.W[l];  // [W][W], row o holds the weights of output o
+    for (int o = 0; o < W; ++o) {
+      const float w = __ldg(Wl + (int64_t)o * W + t);
+#pragma unroll
+      for (int p = 0; p < TP; ++p) acc[p] = fmaf(dsh[p * W + o], w, acc[p]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < TP; ++p) {
+      float d = 0.f;
+      if (p0 + p < npts) {
+        const float z = Z[((int64_t)(l - 1) * npts + p0 + p) * W + t];
+        d = acc[p] * dact(net, z);
+        Dl[((int64_t)(l - 1) * npts + p0 + p) * W + t] = d;
+      }
+      dsh[p * W + t] = d;
+    }
+    __syncthreads();
+  }
+}
+
+// C[o][k] (k <= K; column K is the bias) partial sums over one split of points:
+//   C[o][k] = sum_q X[q][o] * Y'(q, k),  Y'(q, k) = f(Y[q][k]) for k < K, 1 for k = K,
+// with f the identity (ymode 0), ReLU (1) or sin(omega0 .) (2).
+constexpr int GT = 64, GK = 16;
+__global__ void __launch_bounds__(256)
+    simt_dw_kernel(const float* __restrict__ X, int O, const float* __restrict__ Y, int K, int ymode,
+                   float omega0, int64_t npts, int64_t per_split, float* __restrict__ part) {
+  __shared__ float xs[GK][GT + 1];
+  __shared__ float ys[GK][GT + 1];
+  const int to = blockIdx.x, tk = blockIdx.y, sp = blockIdx.z;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t q0 = (int64_t)sp * per_split;
+  const int64_t q1 = min(npts, q0 + per_split);
+  float acc[4][4] = {};
+  for (int64_t qb = q0; qb < q1; qb += GK) {
+    for (int e = threadIdx.x; e < GK * GT; e += 256) {
+      const int qq = e / GT, c = e % GT;
+      const int64_t q = qb + qq;
+      const int o = to * GT + c, k = tk * GT + c;
+      float xv = 0.f, yv = 0.f;
+      if (q < q1) {
+        if (o < O) xv = X[q * O + o];
+        if (k < K) {
+          yv = Y[q * K + k];
+          if (ymode == 1) yv = fmaxf(yv, 0.f);
+          else if (ymode == 2) yv = sinf(omega0 * yv);
+        } else if (k == K) {
+          yv = 1.f;
+        }
+      }
+      xs[qq][c] = xv;
+      ys[qq][c] = yv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int qq = 0; qq < GK; ++qq) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = xs[qq][ty * 4 + i];
+        b[i] = ys[qq][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const int ld = K + 1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = to * GT + ty * 4 + i, k = tk * GT + tx * 4 + j;
+      if (o < O && k <= K) part[((int64_t)sp * O + o) * ld + k] = acc[i][j];
+    }
+}
+
+// grad[offW + o*K + k] (+)= sum_s part[s][o][k];  grad[offb + o] (+)= sum_s part[s][o][K].
+__global__ void reduce_layer_kernel(const float* __restrict__ part, int S, int O, int K,
+                                    int64_t offW, int64_t offb, double mult, int accumulate,
+                                    double* __restrict__ grad) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ld = K + 1;
+  if (e >= (int64_t)O * ld) return;
+  double s = 0.0;
+  for (int q = 0; q < S; ++q) s += (double)part[(int64_t)q * O * ld + e];
+  s *= mult;
+  const int o = (int)(e / ld), k = (int)(e % ld);
+  const int64_t dst = k < K ? offW + (int64_t)o * K + k : offb + o;
+  grad[dst] = accumulate ? grad[dst] + s : s;
+}
+
+struct VjpWs {
+  float* Wt;
+  float* E;
+  float* Z;
+  float* D;
+  float* dout;
+  float* part;
+  int S;
+};
+
+int splits_for(int64_t npts) {
+  int S = (int)((npts + 4095) / 4096);
+  if (S > 16) S = 16;
+  if (S < 1) S = 1;
+  return S;
+}
+
+size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, VjpWs* out, bool* ok) {
+  Carver c(ws, cap);
+  LayerOffs lo;
+  VjpWs w;
+  w.Wt = c.take<float>(wt_layout(n, &lo));
+  w.E = c.take<float>(chunk * n.K0);
+  w.Z = c.take<float>(chunk * n.L * n.W);
+  w.D = c.take<float>(chunk * n.L * n.W);
+  w.dout = c.take<float>(chunk);
+  w.S = splits_for(chunk);
+  int64_t pe = 0;
+  for (int l = 0; l <= n.L; ++l) pe = std::max<int64_t>(pe, (int64_t)n.out_dim[l] * (n.in_dim[l] + 1));
+  w.part = c.take<float>(pe * w.S);
+  if (out) *out = w;
+  if (ok) *ok = c.ok;
+  return c.off + 256;
+}
+
+int prep_wt(const Net& n, const float* theta, float* Wt, LayerOffs* lo, cudaStream_t st) {
+  wt_layout(n, lo);
+  for (int l = 0; l < n.L; ++l) {
+    const int64_t cnt = (int64_t)n.in_dim[l] * n.out_dim[l];
+    transpose_w_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(theta, n.offW[l], n.out_dim[l],
+                                                          n.in_dim[l], Wt + lo->Wt[l]);
+  }
+  INRCT_CHECK_LAUNCH("weight transpose");
+  return INRCT_OK;
+}
+
+size_t fwd_smem(const Net& n) {
+  const int Kmax = n.K0 > n.W ? n.K0 : n.W;
+  return sizeof(float) * TP * (Kmax + n.W);
+}
+
+int set_fwd_smem(const Net& n) {
+  const size_t sm = fwd_smem(n);
+  if (sm > 40 * 1024) {  // dynamic plus static shared memory may exceed the 48 KB default
+    cudaError_t e = cudaFuncSetAttribute(simt_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) {
+      set_error("simt forward smem attribute: %s", cudaGetErrorString(e));
+      return INRCT_ERR_CUDA;
+    }
+  }
+  return INRCT_OK;
+}
+
+}  // namespace
+
+size_t simt_eval_ws_bytes(const Net& n) {
+  LayerOffs lo;
+  return align_up(sizeof(float) * wt_layout(n, &lo), 256) + 256;
+}
+
+int simt_eval(const Net& n, const float* theta, int N, int64_t npts, float* image, void* ws,
+              size_t ws_bytes, cudaStream_t st) {
+  const size_t need = simt_eval_ws_bytes(n);
+  if (!ws || ws_bytes < need) {
+    set_error("inr_eval_grid (fp32): workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  LayerOffs lo;
+  float* Wt = static_cast<float*>(ws);
+  INRCT_TRY(prep_wt(n, theta, Wt, &lo, st));
+  INRCT_TRY(set_fwd_smem(n));
+  simt_fwd_kernel<<<ceil_div(npts, TP), n.W, fwd_smem(n), st>>>(dev_of(n, N), lo, theta, Wt, npts,
+                                                               nullptr, image, nullptr, nullptr);
+  INRCT_CHECK_LAUNCH("simt forward");
+  return INRCT_OK;
+}
+
+size_t simt_vjp_ws_bytes(const Net& n, int64_t n_idx) {
+  const int64_t chunk = n_idx < kVjpChunk ? n_idx : kVjpChunk;
+  return vjp_layout(n, chunk, nullptr, 0, nullptr, nullptr);
+}
+
+int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t n_idx,
+             const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
+             size_t ws_bytes, cudaStream_t st) {
+  const int64_t chunk = n_idx < kVjpChunk ? n_idx : kVjpChunk;
+  VjpWs w;
+  bool ok;
+  const size_t need = vjp_layout(n, chunk, ws, ws_bytes, &w, &ok);
+  if (!ws || !ok) {
+    set_error("inr_weighted_vjp (fp32): workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  LayerOffs lo;
+  INRCT_TRY(prep_wt(n, theta, w.Wt, &lo, st));
+  INRCT_TRY(set_fwd_smem(n));
+  const NetDev nd = dev_of(n, N);
+  for (int64_t c0 = 0; c0 < n_idx; c0 += chunk) {
+    const int64_t np = std::min(chunk, n_idx - c0);
+    const int32_t* id = idx + c0;
+    const unsigned nb = ceil_div(np, TP);
+    simt_fwd_kernel<<<nb, n.W, fwd_smem(n), st>>>(nd, lo, theta, w.Wt, np, id, nullptr, w.E, w.Z);
+    INRCT_CHECK_LAUNCH("simt vjp forward");
+    simt_bwd_kernel<<<nb, n.W, sizeof(float) * TP * n.W, st>>>(nd, lo, theta, np, id, v,
+                                                                (float)scale, w.Z, w.D, w.dout);
+    INRCT_CHECK_LAUNCH("simt vjp backward");
+    const int S = splits_for(np);
+    const int64_t per = (np + S - 1) / S;
+    for (int l = 0; l <= n.L; ++l) {
+      const int O = n.out_dim[l], K = n.in_dim[l];
+      const float* X = l < n.L ? w.D + (int64_t)l * np * n.W : w.dout;
+      const float* Y;
+      int ymode;
+      if (l == 0) {
+        Y = w.E;
+        ymode = 0;
+      } else {
+        Y = w.Z + (int64_t)(l - 1) * np * n.W;
+        ymode = n.kind == INRCT_FFN_RELU ? 1 : 2;
+      }
+      dim3 grd(ceil_div(O, GT), ceil_div(K + 1, GT), S);
+      simt_dw_kernel<<<grd, 256, 0, st>>>(X, O, Y, K, ymode, n.omega0, np, per, w.part);
+      INRCT_CHECK_LAUNCH("simt dW");
+      const int64_t ent = (int64_t)O * (K + 1);
+      reduce_layer_kernel<<<ceil_div(ent, 256), 256, 0, st>>>(w.part, S, O, K, n.offW[l], n.offb[l],
+                                                              1.0, c0 > 0, grad_f64);
+      INRCT_CHECK_LAUNCH("simt reduce");
+    }
+  }
+  if (grad_f32) INRCT_TRY(f64_to_f32(grad_f64, grad_f32, n.p, st));
+  return INRCT_OK;
+}
+
+}  // namespace inrct

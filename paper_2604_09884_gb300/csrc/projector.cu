@@ -1,0 +1,722 @@
+// Joseph ray-driven projector P and its exactly matched adjoint P^T on sm_103a.
+//
+// The paper factorises the projection as z = P E{f} with a discrete projector
+// P in R^{m x n} and needs v = P^T r (Sec. 3; Algorithm 1, steps 1-2).  The
+// model implemented here is Joseph's: a ray picks the grid axis along which it
+// advances fastest (the driving axis), crosses every slice of that axis, and
+// linearly (2-D) or bilinearly (3-D) interpolates the image at the crossing,
+// with zero outside the grid; the sum is scaled by the path length per slice.
+//
+// Arithmetic layout
+// -----------------
+// * Per-ray constants are computed once per call in FP64 by a table kernel
+//   (driving axis, crossing at the middle slice, slope, step length); the
+//   crossing is then carried in 32.32 fixed point and stepped by exact integer
+//   addition (see the table section), so its error stays near 1e-7 pixel.
+// * The forward kernel and the gather-form adjoint evaluate the crossing
+//   with the same integer operations and convert it to weights with the same
+//   FP32 operations, so both see bit-identical interpolation weights: P^T is
+//   the transpose of P up to the FP32 summation order only.
+// * Forward: a block holds 32 neighbouring rays x SEG segments of each ray;
+//   neighbouring rays cross neighbouring pixels of the same slice, so warp
+//   loads coalesce.  Rays driven along x read a transposed copy of the image
+//   so that their two taps are also contiguous.
+// * Adjoint: gather form, one thread per pixel (2-D) or per voxel column and
+//   z-chunk (3-D).  Every pixel enumerates, view by view, the few detector
+//   bins whose rays can reach it, recomputes their weights from the same ray
+//   table and sums locally: deterministic, no atomics.
+#include <math.h>
+
+#include "common.cuh"
+#include "projector.cuh"
+
+namespace inrct {
+
+// ---------------------------------------------------------------------------
+// ray tables (FP64 set-up, fixed-point result)
+//
+// Crossings are carried in 32.32 fixed point: U = round(u * 2^32) in an int64,
+// where u is the fractional transverse index.  Along a ray u is affine in the
+// slice index j, u(j) = U0 + (j - jref) * S with jref = N/2, so the forward
+// kernel steps it by integer addition and the adjoint evaluates the same
+// integer expression directly: both get the same bits, with a position error
+// of about 1e-7 pixel (instead of ~1e-5 for an FP32 crossing at N = 512).
+// The interpolation weights are f = (low 32 bits) * 2^-32 and 1 - f in FP32.
+// ---------------------------------------------------------------------------
+constexpr double kFx32 = 4294967296.0;         // 2^32
+constexpr double kFx30 = 1073741824.0;         // 2^30 (slopes, |slope| <= 1)
+constexpr double kFx48 = 281474976710656.0;    // 2^48 (cone z-slope coefficient)
+
+__device__ __forceinline__ bool drive_x(double ex, double ey) {
+  // x drives unless |e_y| exceeds |e_x| by more than a relative 1e-12
+  return !(fabs(ey) > fabs(ex) * (1.0 + 1e-12));
+}
+
+__device__ __forceinline__ int4 pack_ray(double uref, double slope, float scale_signed) {
+  const long long U0 = __double2ll_rn(uref * kFx32);
+  const int S = (int)__double2ll_rn(slope * kFx30);
+  return make_int4((int)(unsigned)(U0 & 0xffffffffll), (int)(U0 >> 32), S,
+                   __float_as_int(scale_signed));
+}
+
+__device__ __forceinline__ int64_t ray_U0(const int4& t) {
+  return ((int64_t)t.y << 32) | (int64_t)(uint32_t)t.x;
+}
+
+__global__ void build_rays2d_kernel(GeomDev g, int4* __restrict__ tab, float2* __restrict__ views) {
+  const int64_t m = (int64_t)g.V * g.A;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < g.V) {
+    const double ang = g.angle0 + g.span * (double)r / (double)g.V;
+    double s, c;
+    sincos(ang, &s, &c);
+    views[r] = make_float2((float)c, (float)s);
+  }
+  if (r >= m) return;
+  const int k = (int)(r / g.A), b = (int)(r % g.A);
+  const double D = 2.0 / g.N;
+  const double ang = g.angle0 + g.span * (double)k / (double)g.V;
+  double sb, cb;
+  sincos(ang, &sb, &cb);
+  double px, py, ex, ey;
+  if (g.kind == INRCT_PAR2D) {
+    const double t = ((double)b - 0.5 * (g.A - 1)) * g.du * D;
+    px = t * cb;
+    py = t * sb;
+    ex = -sb;
+    ey = cb;
+  } else {
+    const double R = g.sod * D;
+    const double gam = ((double)b - 0.5 * (g.A - 1)) * g.du / g.sod;
+    double sg, cg;
+    sincos(gam, &sg, &cg);
+    ex = -(cb * cg - sb * sg);
+    ey = -(sb * cg + cb * sg);
+    const double Sx = R * cb, Sy = R * sb;
+    const double dot = Sx * ex + Sy * ey;  // point of the ray nearest the isocentre
+    px = Sx - dot * ex;
+    py = Sy - dot * ey;
+  }
+  const bool xd = drive_x(ex, ey);
+  const double ea = xd ? ex : ey, eq = xd ? ey : ex;
+  const double pa = xd ? px : py, pq = xd ? py : px;
+  const double a0 = (pa + 1.0) / D - 0.5;  // fractional slice index of the reference point
+  const double q0 = (pq + 1.0) / D - 0.5;  // its fractional transverse index
+  const double slope = eq / ea;
+  const double uref = q0 + ((double)(g.N / 2) - a0) * slope;
+  const float sc = (float)(D / fabs(ea));
+  tab[r] = pack_ray(uref, slope, xd ? sc : -sc);
+}
+
+__global__ void build_cols3d_kernel(GeomDev g, int4* __restrict__ t0, int4* __restrict__ t1,
+                                    float* __restrict__ t2, float2* __restrict__ views) {
+  const int64_t cnt = (int64_t)g.V * g.A;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < g.V) {
+    const double ang = g.angle0 + g.span * (double)r / (double)g.V;
+    double s, c;
+    sincos(ang, &s, &c);
+    views[r] = make_float2((float)c, (float)s);
+  }
+  if (r >= cnt) return;
+  const int k = (int)(r / g.A), a = (int)(r % g.A);
+  const double D = 2.0 / g.N;
+  const double ang = g.angle0 + g.span * (double)k / (double)g.V;
+  double sb, cb;
+  sincos(ang, &sb, &cb);
+  const double R = g.sod * D;
+  const double pu = g.du * D * g.sdd / g.sod;
+  const double pv = g.dv * D * g.sdd / g.sod;
+  const double ua = ((double)a - 0.5 * (g.A - 1)) * pu;
+  const double dc = -(g.sdd - g.sod) * D;
+  const double Sx = R * cb, Sy = R * sb;
+  const double ex = (dc * cb - ua * sb) - Sx;  // bin - source, xy part (depends on the column only)
+  const double ey = (dc * sb + ua * cb) - Sy;
+  const double L2 = ex * ex + ey * ey;
+  const double tau0 = -(Sx * ex + Sy * ey) / L2;  // nearest point to the z axis
+  const double px = Sx + tau0 * ex, py = Sy + tau0 * ey;
+  const bool xd = drive_x(ex, ey);
+  const double ea = xd ? ex : ey, eq = xd ? ey : ex;
+  const double pa = xd ? px : py, pq = xd ? py : px;
+  const double a0 = (pa + 1.0) / D - 0.5;
+  const double q0 = (pq + 1.0) / D - 0.5;
+  const double slope = eq / ea;
+  const double jref = (double)(g.N / 2);
+  const float sa = (float)(D / fabs(ea));
+  t0[r] = pack_ray(q0 + (jref - a0) * slope, slope, xd ? sa : -sa);
+  // z crossing: u_z(j) = Cz + vb * G(j), vb = m_r * pv/2 (m_r = 2 row - (B-1)),
+  // G(j) = tau(j)/D = G_ref + (j - jref) / e_a
+  const double Gref = tau0 / D + (jref - a0) / ea;
+  const long long Hh = __double2ll_rn(0.5 * pv * Gref * kFx32);
+  const long long Kk = __double2ll_rn(0.5 * pv / ea * kFx48);
+  t1[r] = make_int4((int)(unsigned)(Hh & 0xffffffffll), (int)(Hh >> 32),
+                    (int)(unsigned)(Kk & 0xffffffffll), (int)(Kk >> 32));
+  t2[r] = (float)L2;
+}
+
+// ---------------------------------------------------------------------------
+// shared helpers: identical integer/FP32 operations in P and P^T
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_fx(int64_t u, int& i0, float& f) {
+  i0 = (int)(u >> 32);
+  f = __uint2float_rn((uint32_t)(u & 0xffffffffll)) * 2.3283064365386963e-10f;  // * 2^-32
+}
+
+// Interpolation weight that crossing u gives to integer index q
+// (the forward gives 1 - f to floor(u) and f to floor(u) + 1).
+__device__ __forceinline__ float tap_weight(int64_t u, int q) {
+  int i0;
+  float f;
+  split_fx(u, i0, f);
+  return q == i0 ? __fsub_rn(1.f, f) : (q == i0 + 1 ? f : 0.f);
+}
+
+__device__ __forceinline__ int64_t slope_fx(const int4& t) { return (int64_t)t.z << 2; }
+
+struct ConeRay {
+  int64_t Z0, Sz;  // z crossing at jref and its step, 32.32
+  float vb;        // v coordinate of the detector row (world units)
+};
+
+__device__ __forceinline__ ConeRay cone_ray(const int4& t1, int mr, int64_t CzF, float pv_half) {
+  const int64_t Hh = ((int64_t)t1.y << 32) | (int64_t)(uint32_t)t1.x;
+  const int64_t Kk = ((int64_t)t1.w << 32) | (int64_t)(uint32_t)t1.z;
+  ConeRay c;
+  c.Z0 = CzF + (int64_t)mr * Hh;
+  c.Sz = ((int64_t)mr * Kk) >> 16;
+  c.vb = __fmul_rn((float)mr, pv_half);
+  return c;
+}
+
+__device__ __forceinline__ float cone_scale(float vb, float L2, float sa) {
+  return __fmul_rn(__fsqrt_rn(__fmaf_rn(vb, vb, L2)), sa);
+}
+
+// Slices j in [lo, hi) where u(j) = uref + (j - jref) * slope may lie in (-1, N).
+__device__ __forceinline__ void active_range(float uref, float slope, int jref, int N, int& lo,
+                                             int& hi) {
+  if (fabsf(slope) < 1e-12f) {
+    if (uref > -1.f && uref < (float)N) {
+      lo = 0;
+      hi = N;
+    } else {
+      lo = hi = 0;
+    }
+    return;
+  }
+  const float ja = (float)jref + (-1.f - uref) / slope, jb = (float)jref + ((float)N - uref) / slope;
+  float l = fminf(ja, jb), h = fmaxf(ja, jb);
+  l = fmaxf(l - 1.f, -1.f);
+  h = fminf(h + 1.f, (float)N + 1.f);
+  lo = max(0, (int)floorf(l));
+  hi = min(N, (int)ceilf(h) + 1);
+  if (hi < lo) hi = lo;
+}
+
+__device__ __forceinline__ float fx_to_float(int64_t u) { return (float)((double)u * (1.0 / kFx32)); }
+
+// ---------------------------------------------------------------------------
+// transposes (x-driven rays read img^T so that their taps are contiguous)
+// ---------------------------------------------------------------------------
+__global__ void transpose_xy_kernel(const float* __restrict__ in, float* __restrict__ out, int N) {
+  __shared__ float tile[32][33];
+  const size_t zoff = (size_t)blockIdx.z * N * N;
+  int x = blockIdx.x * 32 + threadIdx.x;
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    int y = blockIdx.y * 32 + yy;
+    if (x < N && y < N) tile[yy][threadIdx.x] = in[zoff + (size_t)y * N + x];
+  }
+  __syncthreads();
+  int y = blockIdx.y * 32 + threadIdx.x;
+  for (int xx = threadIdx.y; xx < 32; xx += blockDim.y) {
+    int xo = blockIdx.x * 32 + xx;
+    if (xo < N && y < N) out[zoff + (size_t)xo * N + y] = tile[threadIdx.x][xx];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forward projection
+// ---------------------------------------------------------------------------
+template <int SEG>
+__global__ void __launch_bounds__(32 * SEG)
+    project2d_kernel(const int4* __restrict__ tab, int m, int N, const float* __restrict__ img,
+                     const float* __restrict__ imgT, float* __restrict__ sino,
+                     const float* __restrict__ y, float* __restrict__ resid,
+                     double* __restrict__ loss_part) {
+  __shared__ float part[SEG][33];
+  const int lane = threadIdx.x, s = threadIdx.y;
+  const int r = blockIdx.x * 32 + lane;
+  const int jref = N / 2;
+  float sum = 0.f, sc = 0.f;
+  if (r < m) {
+    const int4 P = __ldg(tab + r);
+    sc = __int_as_float(P.w);
+    const float* base = sc > 0.f ? imgT : img;
+    sc = fabsf(sc);
+    const int64_t U0 = ray_U0(P), S4 = slope_fx(P);
+    int lo, hi;
+    active_range(fx_to_float(U0), (float)P.z * 9.313225746154785e-10f, jref, N, lo, hi);
+    const int per = (hi - lo + SEG - 1) / SEG;
+    const int j0 = lo + s * per, j1 = min(hi, j0 + per);
+    int64_t u = U0 + (int64_t)(j0 - jref) * S4;
+    for (int j = j0; j < j1; ++j, u += S4) {
+      int i0;
+      float f;
+      split_fx(u, i0, f);
+      const float* row = base + (size_t)j * N;
+      const float v0 = (i0 >= 0 && i0 < N) ? __ldg(row + i0) : 0.f;
+      const float v1 = (i0 >= -1 && i0 + 1 < N) ? __ldg(row + i0 + 1) : 0.f;
+      sum = fmaf(__fsub_rn(1.f, f), v0, fmaf(f, v1, sum));
+    }
+  }
+  part[s][lane] = sum;
+  __syncthreads();
+  if (s == 0) {
+    float z = 0.f;
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) z += part[k][lane];
+    z *= sc;
+    float l = 0.f;
+    if (r < m) {
+      sino[r] = z;
+      if (y) {
+        const float d = z - y[r];
+        resid[r] = d;
+        l = d * d;
+      }
+    }
+    if (y) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+      if (lane == 0) loss_part[blockIdx.x] = 0.5 * (double)l;
+    }
+  }
+}
+
+template <int SEG>
+__global__ void __launch_bounds__(32 * SEG)
+    project3d_kernel(const int4* __restrict__ t0, const int4* __restrict__ t1,
+                     const float* __restrict__ t2, int A, int B, int N, float pv_half, int64_t CzF,
+                     const float* __restrict__ vol, const float* __restrict__ volT,
+                     float* __restrict__ sino, const float* __restrict__ y,
+                     float* __restrict__ resid, double* __restrict__ loss_part) {
+  __shared__ float part[SEG][33];
+  const int lane = threadIdx.x, s = threadIdx.y;
+  const int a = blockIdx.x * 32 + lane, row = blockIdx.y, k = blockIdx.z;
+  const int jref = N / 2;
+  float sum = 0.f, sc = 0.f;
+  if (a < A) {
+    const size_t ci = (size_t)k * A + a;
+    const int4 P = __ldg(t0 + ci);
+    const ConeRay cr = cone_ray(__ldg(t1 + ci), 2 * row - (B - 1), CzF, pv_half);
+    const float sa = __int_as_float(P.w);
+    sc = cone_scale(cr.vb, __ldg(t2 + ci), fabsf(sa));
+    const float* base = sa > 0.f ? volT : vol;
+    const int64_t Uq = ray_U0(P), Sq = slope_fx(P);
+    int lo, hi, lz, hz;
+    active_range(fx_to_float(Uq), (float)P.z * 9.313225746154785e-10f, jref, N, lo, hi);
+    active_range(fx_to_float(cr.Z0), fx_to_float(cr.Sz), jref, N, lz, hz);
+    lo = max(lo, lz);
+    hi = min(hi, hz);
+    if (hi < lo) hi = lo;
+    const int per = (hi - lo + SEG - 1) / SEG;
+    const int j0 = lo + s * per, j1 = min(hi, j0 + per);
+    const size_t NN = (size_t)N * N;
+    int64_t uq = Uq + (int64_t)(j0 - jref) * Sq;
+    int64_t uz = cr.Z0 + (int64_t)(j0 - jref) * cr.Sz;
+    for (int j = j0; j < j1; ++j, uq += Sq, uz += cr.Sz) {
+      int iq, iz;
+      float fq, fz;
+      split_fx(uq, iq, fq);
+      split_fx(uz, iz, fz);
+      const float wq0 = __fsub_rn(1.f, fq), wz0 = __fsub_rn(1.f, fz);
+      const bool q0ok = iq >= 0 && iq < N, q1ok = iq >= -1 && iq + 1 < N;
+      const bool z0ok = iz >= 0 && iz < N, z1ok = iz >= -1 && iz + 1 < N;
+      const float* p0 = base + (ptrdiff_t)iz * (ptrdiff_t)NN + (ptrdiff_t)j * N + iq;
+      const float* p1 = p0 + NN;
+      const float v00 = (z0ok && q0ok) ? __ldg(p0) : 0.f;
+      const float v01 = (z0ok && q1ok) ? __ldg(p0 + 1) : 0.f;
+      const float v10 = (z1ok && q0ok) ? __ldg(p1) : 0.f;
+      const float v11 = (z1ok && q1ok) ? __ldg(p1 + 1) : 0.f;
+      sum = fmaf(wz0 * wq0, v00, sum);
+      sum = fmaf(wz0 * fq, v01, sum);
+      sum = fmaf(fz * wq0, v10, sum);
+      sum = fmaf(fz * fq, v11, sum);
+    }
+  }
+  part[s][lane] = sum;
+  __syncthreads();
+  if (s == 0) {
+    float z = 0.f;
+#pragma unroll
+    for (int q = 0; q < SEG; ++q) z += part[q][lane];
+    z *= sc;
+    float l = 0.f;
+    const size_t r = ((size_t)k * B + row) * A + a;
+    if (a < A) {
+      sino[r] = z;
+      if (y) {
+        const float d = z - y[r];
+        resid[r] = d;
+        l = d * d;
+      }
+    }
+    if (y) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+      if (lane == 0)
+        loss_part[((size_t)k * B + row) * gridDim.x + blockIdx.x] = 0.5 * (double)l;
+    }
+  }
+}
+
+// Deterministic FP64 sum of n partials into out[0] (one block).
+__global__ void reduce_f64_kernel(const double* __restrict__ in, int64_t n, double* __restrict__ out) {
+  __shared__ double sh[1024];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += in[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (gather form)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    backproject2d_kernel(GeomDev g, const int4* __restrict__ tab, const float2* __restrict__ views,
+                         const float* __restrict__ sino, float* __restrict__ img) {
+  extern __shared__ float2 sv[];
+  for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < g.V; k += blockDim.x * blockDim.y)
+    sv[k] = views[k];
+  __syncthreads();
+  const int N = g.N, A = g.A;
+  const int jref = N / 2;
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+  if (ix >= N || iy >= N) return;
+  const float D = 2.f / (float)N;
+  const float px = -1.f + ((float)ix + 0.5f) * D, py = -1.f + ((float)iy + 0.5f) * D;
+  const float cA = 0.5f * (float)(A - 1);
+  const bool par = g.kind == INRCT_PAR2D;
+  const float inv_pitch = (float)(1.0 / (g.du * (2.0 / N)));  // parallel: bins per world unit
+  const float inv_dgam = (float)(g.sod / g.du);                // fan: bins per radian
+  const float R = (float)(g.sod * (2.0 / N));
+  const float hpar = (float)(1.0 / g.du) + 0.02f;
+  float acc = 0.f;
+  for (int k = 0; k < g.V; ++k) {
+    const float cb = sv[k].x, sb = sv[k].y;
+    float bc, h;
+    if (par) {
+      bc = fmaf(px * cb + py * sb, inv_pitch, cA);
+      h = hpar;
+    } else {
+      const float wx = px - R * cb, wy = py - R * sb;
+      const float along = -(wx * cb + wy * sb);
+      const float across = sb * wx - cb * wy;
+      bc = fmaf(atan2f(across, along), inv_dgam, cA);
+      const float x = D * rsqrtf(wx * wx + wy * wy);
+      h = x * (1.f + x * x * (1.f / 6.f) + 4e-3f) * inv_dgam + 0.02f;
+    }
+    const int b0 = max(0, (int)ceilf(bc - h));
+    const int b1 = min(A - 1, (int)floorf(bc + h));
+    const int4* trow = tab + (size_t)k * A;
+    const float* srow = sino + (size_t)k * A;
+    for (int b = b0; b <= b1; ++b) {
+      const int4 P = __ldg(trow + b);
+      const float sc = __int_as_float(P.w);
+      const bool xd = sc > 0.f;
+      const int j = xd ? ix : iy, q = xd ? iy : ix;
+      const float w = tap_weight(ray_U0(P) + (int64_t)(j - jref) * slope_fx(P), q);
+      if (w != 0.f) acc = fmaf(w * fabsf(sc), __ldg(srow + b), acc);
+    }
+  }
+  img[(size_t)iy * N + ix] = acc;
+}
+
+template <int ZC>
+__global__ void __launch_bounds__(128)
+    backproject3d_kernel(GeomDev g, const int4* __restrict__ t0, const int4* __restrict__ t1,
+                         const float* __restrict__ t2, const float2* __restrict__ views,
+                         float pv_half, int64_t CzF, const float* __restrict__ sino,
+                         float* __restrict__ vol) {
+  extern __shared__ float2 sv[];
+  for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < g.V; k += blockDim.x * blockDim.y)
+    sv[k] = views[k];
+  __syncthreads();
+  const int N = g.N, A = g.A, B = g.B;
+  const int jref = N / 2;
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z0 = blockIdx.z * ZC;
+  if (ix >= N || iy >= N) return;
+  const float D = 2.f / (float)N;
+  const float px = -1.f + ((float)ix + 0.5f) * D, py = -1.f + ((float)iy + 0.5f) * D;
+  const float cA = 0.5f * (float)(A - 1), Bm1 = (float)(B - 1);
+  const float Cz = 0.5f * (float)N - 0.5f;
+  const float R = (float)(g.sod * (2.0 / N));
+  const float kcol = (float)(g.sod / g.du);                   // columns per unit of (u / depth)
+  const float kha = (float)(1.3 * (2.0 / N) * g.sod / g.du);  // half window numerator
+  float acc[ZC];
+#pragma unroll
+  for (int q = 0; q < ZC; ++q) acc[q] = 0.f;
+  for (int k = 0; k < g.V; ++k) {
+    const float cb = sv[k].x, sb = sv[k].y;
+    const float depth = R - (cb * px + sb * py);
+    const float ucoord = -sb * px + cb * py;
+    const float ac = fmaf(ucoord / depth, kcol, cA);
+    const float ha = kha / depth + 0.02f;
+    const int a0i = max(0, (int)ceilf(ac - ha));
+    const int a1i = min(A - 1, (int)floorf(ac + ha));
+    for (int a = a0i; a <= a1i; ++a) {
+      const size_t ci = (size_t)k * A + a;
+      const int4 P = __ldg(t0 + ci);
+      const float sa = __int_as_float(P.w);
+      const bool xd = sa > 0.f;
+      const int j = xd ? ix : iy, q = xd ? iy : ix;
+      const float wq = tap_weight(ray_U0(P) + (int64_t)(j - jref) * slope_fx(P), q);
+      if (wq == 0.f) continue;
+      const int4 T1 = __ldg(t1 + ci);
+      const float L2 = __ldg(t2 + ci);
+      // (pv/2) G(j) in float, only to place the row window
+      const int64_t Hh = ((int64_t)T1.y << 32) | (int64_t)(uint32_t)T1.x;
+      const int64_t Kk = ((int64_t)T1.w << 32) | (int64_t)(uint32_t)T1.z;
+      const float hg = (float)(((double)Hh * 65536.0 + (double)(j - jref) * (double)Kk) *
+                               (1.0 / 281474976710656.0));
+      const float inv_hg = 1.f / hg;
+      const float hb = 0.5f * fabsf(inv_hg) * 1.001f + 0.02f;
+      const float* scol = sino + (size_t)k * B * A + a;
+#pragma unroll
+      for (int zq = 0; zq < ZC; ++zq) {
+        const int iz = z0 + zq;
+        if (iz >= N) break;
+        const float bz = 0.5f * fmaf((float)iz - Cz, inv_hg, Bm1);
+        const int bb0 = max(0, (int)ceilf(bz - hb));
+        const int bb1 = min(B - 1, (int)floorf(bz + hb));
+        for (int b = bb0; b <= bb1; ++b) {
+          const ConeRay cr = cone_ray(T1, 2 * b - (B - 1), CzF, pv_half);
+          const float wz = tap_weight(cr.Z0 + (int64_t)(j - jref) * cr.Sz, iz);
+          if (wz != 0.f)
+            acc[zq] = fmaf(wq * wz * cone_scale(cr.vb, L2, fabsf(sa)), __ldg(scol + (size_t)b * A),
+                           acc[zq]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int zq = 0; zq < ZC; ++zq) {
+    const int iz = z0 + zq;
+    if (iz < N) vol[((size_t)iz * N + iy) * N + ix] = acc[zq];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int check_geom(const inrct_geom* geom, const inrct_grid* grid) {
+  INRCT_REQUIRE(geom && grid, "geometry and grid descriptors must not be NULL");
+  INRCT_REQUIRE(grid->N > 0 && grid->N <= 4096, "grid side N=%d out of range (1..4096)", grid->N);
+  INRCT_REQUIRE(geom->n_views > 0 && geom->n_views <= 4096, "n_views=%d out of range (1..4096)",
+                geom->n_views);
+  INRCT_REQUIRE(geom->n_bins_u > 0 && geom->n_bins_u <= 16384, "n_bins_u=%d out of range",
+                geom->n_bins_u);
+  INRCT_REQUIRE(geom->du > 0, "du must be positive");
+  if (geom->kind == INRCT_PAR2D || geom->kind == INRCT_FAN2D) {
+    INRCT_REQUIRE(grid->d == 2, "2-D geometry needs a 2-D grid (d=%d)", grid->d);
+  } else if (geom->kind == INRCT_CONE3D) {
+    INRCT_REQUIRE(grid->d == 3, "cone geometry needs a 3-D grid (d=%d)", grid->d);
+    INRCT_REQUIRE(geom->n_bins_v > 0 && geom->n_bins_v <= 16384, "n_bins_v=%d out of range",
+                  geom->n_bins_v);
+    INRCT_REQUIRE(geom->dv > 0, "dv must be positive");
+  } else {
+    set_error("unknown geometry kind %d", geom->kind);
+    return INRCT_ERR_INVALID_ARG;
+  }
+  if (geom->kind != INRCT_PAR2D) {
+    INRCT_REQUIRE(geom->sod > 0 && geom->sdd > geom->sod,
+                  "need 0 < sod < sdd (sod=%g, sdd=%g)", geom->sod, geom->sdd);
+    // the source must lie outside the grid's circumscribed circle/sphere
+    const double rmax = 0.5 * grid->N * sqrt((double)grid->d);
+    INRCT_REQUIRE(geom->sod > rmax, "source inside the grid (sod=%g <= %g pixels)", geom->sod,
+                  rmax);
+  }
+  if (geom->kind == INRCT_CONE3D) {
+    // z must never be the driving axis: |e_z| < max(|e_x|, |e_y|) on every ray
+    const double vmax = 0.5 * (geom->n_bins_v - 1) * geom->dv;
+    if (!(vmax < geom->sod / sqrt(2.0) * 0.999)) {
+      set_error("cone angle too wide: z would drive some rays (unsupported)");
+      return INRCT_ERR_UNSUPPORTED;
+    }
+  }
+  return INRCT_OK;
+}
+
+GeomDev to_dev(const inrct_geom* geom, const inrct_grid* grid) {
+  GeomDev g;
+  g.kind = geom->kind;
+  g.N = grid->N;
+  g.V = geom->n_views;
+  g.A = geom->n_bins_u;
+  g.B = geom->kind == INRCT_CONE3D ? geom->n_bins_v : 1;
+  g.du = geom->du;
+  g.dv = geom->dv;
+  g.sod = geom->sod;
+  g.sdd = geom->sdd;
+  g.angle0 = geom->angle0;
+  g.span = geom->angle_span;
+  return g;
+}
+
+int64_t num_rays(const inrct_geom* geom) {
+  if (!geom) return 0;
+  const int64_t rows = geom->kind == INRCT_CONE3D ? geom->n_bins_v : 1;
+  return (int64_t)geom->n_views * rows * geom->n_bins_u;
+}
+
+// Workspace: ray tables, view table, transposed image, loss partials.
+struct ProjWs {
+  int4* tab0;
+  int4* tab1;
+  float* tab2;
+  float2* views;
+  float* imgT;
+  double* loss_part;
+};
+
+static size_t proj_layout(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t cap,
+                          ProjWs* out, bool want_transpose, bool* ok) {
+  Carver c(ws, cap);
+  const bool cone = geom->kind == INRCT_CONE3D;
+  const int64_t entries = cone ? (int64_t)geom->n_views * geom->n_bins_u : num_rays(geom);
+  ProjWs w;
+  w.tab0 = c.take<int4>(entries);
+  w.tab1 = cone ? c.take<int4>(entries) : nullptr;
+  w.tab2 = cone ? c.take<float>(entries) : nullptr;
+  w.views = c.take<float2>(geom->n_views);
+  w.imgT = want_transpose ? c.take<float>(grid_points(grid)) : nullptr;
+  const int64_t blocks = cone ? (int64_t)ceil_div(geom->n_bins_u, 32) * geom->n_bins_v * geom->n_views
+                              : (int64_t)ceil_div(num_rays(geom), 32);
+  w.loss_part = c.take<double>(blocks);
+  if (out) *out = w;
+  if (ok) *ok = c.ok;
+  return c.off + 256;
+}
+
+size_t project_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
+  if (check_geom(geom, grid) != INRCT_OK) return 0;
+  return proj_layout(geom, grid, nullptr, 0, nullptr, true, nullptr);
+}
+
+size_t backproject_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
+  if (check_geom(geom, grid) != INRCT_OK) return 0;
+  return proj_layout(geom, grid, nullptr, 0, nullptr, false, nullptr);
+}
+
+static int build_tables(const GeomDev& g, const ProjWs& w, cudaStream_t st) {
+  if (g.kind == INRCT_CONE3D) {
+    const int64_t cnt = (int64_t)g.V * g.A;
+    build_cols3d_kernel<<<ceil_div(cnt > g.V ? cnt : g.V, 256), 256, 0, st>>>(g, w.tab0, w.tab1,
+                                                                             w.tab2, w.views);
+  } else {
+    const int64_t cnt = (int64_t)g.V * g.A;
+    build_rays2d_kernel<<<ceil_div(cnt > g.V ? cnt : g.V, 256), 256, 0, st>>>(g, w.tab0, w.views);
+  }
+  INRCT_CHECK_LAUNCH("ray table");
+  return INRCT_OK;
+}
+
+// Per-geometry cone constants shared by P and P^T: half the row pitch (world
+// units) and the z index of the grid's lower face in 32.32 fixed point.
+static void cone_consts(const GeomDev& g, float* pv_half, int64_t* CzF) {
+  const double D = 2.0 / g.N;
+  *pv_half = (float)(0.5 * g.dv * D * g.sdd / g.sod);
+  *CzF = (int64_t)llrint((0.5 * g.N - 0.5) * 4294967296.0);
+}
+
+int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
+                 const float* y, float* resid, double* loss_out, void* ws, size_t ws_bytes,
+                 cudaStream_t st) {
+  INRCT_TRY(check_geom(geom, grid));
+  INRCT_REQUIRE(image && sino, "image and sino must not be NULL");
+  INRCT_REQUIRE(!y || (resid && loss_out), "y given: resid and loss_out must not be NULL");
+  ProjWs w;
+  bool ok;
+  const size_t need = proj_layout(geom, grid, ws, ws_bytes, &w, true, &ok);
+  if (!ws || !ok) {
+    set_error("project: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  const GeomDev g = to_dev(geom, grid);
+  INRCT_TRY(build_tables(g, w, st));
+  const int N = g.N;
+  dim3 tb(32, 8);
+  dim3 tg(ceil_div(N, 32), ceil_div(N, 32), g.kind == INRCT_CONE3D ? N : 1);
+  transpose_xy_kernel<<<tg, tb, 0, st>>>(image, w.imgT, N);
+  INRCT_CHECK_LAUNCH("transpose");
+  if (g.kind == INRCT_CONE3D) {
+    float pvh;
+    int64_t CzF;
+    cone_consts(g, &pvh, &CzF);
+    constexpr int SEG = 4;
+    dim3 grd(ceil_div(g.A, 32), g.B, g.V);
+    project3d_kernel<SEG><<<grd, dim3(32, SEG), 0, st>>>(w.tab0, w.tab1, w.tab2, g.A, g.B, N, pvh,
+                                                         CzF, image, w.imgT, sino, y, resid,
+                                                         w.loss_part);
+    INRCT_CHECK_LAUNCH("project3d");
+    if (y) {
+      reduce_f64_kernel<<<1, 1024, 0, st>>>(w.loss_part, (int64_t)grd.x * grd.y * grd.z, loss_out);
+      INRCT_CHECK_LAUNCH("loss reduce");
+    }
+  } else {
+    constexpr int SEG = 8;
+    const int64_t m = num_rays(geom);
+    const unsigned nb = ceil_div(m, 32);
+    project2d_kernel<SEG><<<nb, dim3(32, SEG), 0, st>>>(w.tab0, (int)m, N, image, w.imgT, sino, y,
+                                                        resid, w.loss_part);
+    INRCT_CHECK_LAUNCH("project2d");
+    if (y) {
+      reduce_f64_kernel<<<1, 1024, 0, st>>>(w.loss_part, nb, loss_out);
+      INRCT_CHECK_LAUNCH("loss reduce");
+    }
+  }
+  return INRCT_OK;
+}
+
+int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
+                     void* ws, size_t ws_bytes, cudaStream_t st) {
+  INRCT_TRY(check_geom(geom, grid));
+  INRCT_REQUIRE(image && sino, "image and sino must not be NULL");
+  ProjWs w;
+  bool ok;
+  const size_t need = proj_layout(geom, grid, ws, ws_bytes, &w, false, &ok);
+  if (!ws || !ok) {
+    set_error("backproject: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  const GeomDev g = to_dev(geom, grid);
+  INRCT_TRY(build_tables(g, w, st));
+  const size_t shm = sizeof(float2) * g.V;
+  if (g.kind == INRCT_CONE3D) {
+    float pvh;
+    int64_t CzF;
+    cone_consts(g, &pvh, &CzF);
+    constexpr int ZC = 8;
+    dim3 blk(32, 4);
+    dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, ZC));
+    backproject3d_kernel<ZC><<<grd, blk, shm, st>>>(g, w.tab0, w.tab1, w.tab2, w.views, pvh, CzF,
+                                                    sino, image);
+    INRCT_CHECK_LAUNCH("backproject3d");
+  } else {
+    dim3 blk(32, 8);
+    dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 8));
+    backproject2d_kernel<<<grd, blk, shm, st>>>(g, w.tab0, w.views, sino, image);
+    INRCT_CHECK_LAUNCH("backproject2d");
+  }
+  return INRCT_OK;
+}
+
+}  // namespace inrct

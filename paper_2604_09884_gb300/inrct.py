@@ -1,0 +1,288 @@
+"""Thin ctypes binding of libinrct.so (include/inrct.h), same names as the C ABI.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Tensors must be contiguous CUDA tensors of the documented dtype;
+PyTorch provides the device memory (outputs and workspaces) and the current
+stream.  The library is loaded on first use; if it is missing the call raises
+(there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libinrct.so")
+
+PAR2D, FAN2D, CONE3D = 0, 1, 2
+FFN_RELU, SIREN = 0, 1
+FP32, BF16 = 0, 1
+LOSS_LS, LOSS_FLS = 0, 1
+_GKIND = {"par2d": PAR2D, "fan2d": FAN2D, "cone3d": CONE3D}
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "WORKSPACE", 4: "CUDA", 5: "TIMEOUT"}
+
+
+class InrctError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"inrct {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_views", ctypes.c_int), ("n_bins_u", ctypes.c_int),
+                ("n_bins_v", ctypes.c_int), ("du", ctypes.c_double), ("dv", ctypes.c_double),
+                ("sod", ctypes.c_double), ("sdd", ctypes.c_double), ("angle0", ctypes.c_double),
+                ("angle_span", ctypes.c_double)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int)]
+
+
+class Mlp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("d", ctypes.c_int), ("n_feat", ctypes.c_int),
+                ("B", ctypes.c_void_p), ("omega0", ctypes.c_float), ("n_hidden", ctypes.c_int),
+                ("width", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("t", ctypes.c_int64)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_I64 = ctypes.c_int64
+
+
+def lib():
+    """Load libinrct.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise InrctError(4, f"{LIB_PATH} is missing: run paper_2604_09884_gb300.build.build() "
+                            "(or __graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    g, gr, m = ctypes.POINTER(Geom), ctypes.POINTER(Grid), ctypes.POINTER(Mlp)
+    sig = {
+        "inrct_last_error": ([], ctypes.c_char_p),
+        "inrct_num_params": ([m], _I64),
+        "inrct_num_rays": ([g], _I64),
+        "inrct_project_ws_bytes": ([g, gr], _SZ),
+        "project": ([g, gr, _P, _P, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+        "inrct_backproject_ws_bytes": ([g, gr], _SZ),
+        "backproject": ([g, gr, _P, _P, _P, _SZ, _P], ctypes.c_int),
+        "inrct_ramp_ws_bytes": ([g, gr], _SZ),
+        "ramp_filter": ([g, gr, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+        "inrct_eval_ws_bytes": ([m, gr], _SZ),
+        "inr_eval_grid": ([m, _P, gr, _P, _P, _SZ, _P], ctypes.c_int),
+        "inrct_vjp_ws_bytes": ([m, gr, _I64], _SZ),
+        "inr_weighted_vjp": ([m, _P, gr, _P, _I64, _P, ctypes.c_double, _P, _P, _P, _SZ, _P],
+                             ctypes.c_int),
+        "inrct_step_ws_bytes": ([g, gr, m, _I64], _SZ),
+        "grad_step": ([g, gr, m, ctypes.c_int, _P, _P, _P, _I64, ctypes.c_double,
+                       ctypes.POINTER(Adam), _P, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise InrctError(rc, lib().inrct_last_error().decode())
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    if dtype is not None:
+        assert t.dtype == dtype, f"expected {dtype}, got {t.dtype}"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ws(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------------------
+# descriptors
+# ----------------------------------------------------------------------------
+def geom_desc(g: synth.GeomSpec) -> Geom:
+    return Geom(_GKIND[g.kind], g.V, g.A, g.B if g.kind == "cone3d" else 1, g.du, g.dv, g.sod,
+                g.sdd, g.angle0, g.span)
+
+
+def grid_desc(d: int, N: int) -> Grid:
+    return Grid(d, N)
+
+
+@dataclass
+class MlpHandle:
+    """An inrct_mlp descriptor plus the device Fourier matrix it points to."""
+    desc: Mlp
+    B: torch.Tensor | None
+    spec: synth.ArchSpec
+
+    @property
+    def p(self):
+        return self.spec.p
+
+
+def mlp_desc(a: synth.ArchSpec, prec: int, B=None, device="cuda") -> MlpHandle:
+    Bt = None
+    if a.kind == "ffn":
+        Bt = torch.as_tensor(B, dtype=torch.float32, device=device).contiguous()
+        assert Bt.shape == (a.n_feat, a.d)
+    desc = Mlp(FFN_RELU if a.kind == "ffn" else SIREN, a.d, a.n_feat,
+               Bt.data_ptr() if Bt is not None else None, a.omega0, a.n_hidden, a.width, prec)
+    return MlpHandle(desc, Bt, a)
+
+
+# ----------------------------------------------------------------------------
+# calls (names follow the C ABI)
+# ----------------------------------------------------------------------------
+def num_params(mlp: MlpHandle) -> int:
+    return int(lib().inrct_num_params(ctypes.byref(mlp.desc)))
+
+
+def num_rays(g: synth.GeomSpec) -> int:
+    gd = geom_desc(g)
+    return int(lib().inrct_num_rays(ctypes.byref(gd)))
+
+
+def project(g: synth.GeomSpec, image: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+    """z = P x; with y also r = z - y and L = 1/2 ||r||^2.  Returns z, or (z, r, L)."""
+    L = lib()
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    dev = image.device
+    z = torch.empty(g.m, dtype=torch.float32, device=dev)
+    r = torch.empty(g.m, dtype=torch.float32, device=dev) if y is not None else None
+    loss = torch.empty(1, dtype=torch.float64, device=dev) if y is not None else None
+    nb = L.inrct_project_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
+    ws = _ws(nb, dev)
+    _check(L.project(ctypes.byref(gd), ctypes.byref(grd), _ptr(image, torch.float32), _ptr(z),
+                     _ptr(y, torch.float32), _ptr(r), _ptr(loss), _ptr(ws), nb, _stream(stream)))
+    return z if y is None else (z, r, loss)
+
+
+def backproject(g: synth.GeomSpec, sino: torch.Tensor, stream=None) -> torch.Tensor:
+    """v = P^T r (exact adjoint of project)."""
+    L = lib()
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    dev = sino.device
+    v = torch.empty(g.n, dtype=torch.float32, device=dev)
+    nb = L.inrct_backproject_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
+    ws = _ws(nb, dev)
+    _check(L.backproject(ctypes.byref(gd), ctypes.byref(grd), _ptr(sino, torch.float32), _ptr(v),
+                         _ptr(ws), nb, _stream(stream)))
+    return v
+
+
+def ramp_filter(g: synth.GeomSpec, r: torch.Tensor, stream=None):
+    """(F r, 1/2 r^T F r) with F the ramp filter of the FLS loss."""
+    L = lib()
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    out = torch.empty_like(r)
+    loss = torch.empty(1, dtype=torch.float64, device=r.device)
+    nb = L.inrct_ramp_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
+    ws = _ws(nb, r.device)
+    _check(L.ramp_filter(ctypes.byref(gd), ctypes.byref(grd), _ptr(r, torch.float32), _ptr(out),
+                         _ptr(loss), _ptr(ws), nb, _stream(stream)))
+    return out, loss
+
+
+def inr_eval_grid(mlp: MlpHandle, theta: torch.Tensor, N: int, stream=None) -> torch.Tensor:
+    """E{f_theta} on the N^d grid (flat, x fastest)."""
+    L = lib()
+    grd = grid_desc(mlp.spec.d, N)
+    img = torch.empty(N ** mlp.spec.d, dtype=torch.float32, device=theta.device)
+    nb = L.inrct_eval_ws_bytes(ctypes.byref(mlp.desc), ctypes.byref(grd))
+    ws = _ws(nb, theta.device)
+    _check(L.inr_eval_grid(ctypes.byref(mlp.desc), _ptr(theta, torch.float32), ctypes.byref(grd),
+                           _ptr(img), _ptr(ws), nb, _stream(stream)))
+    return img
+
+
+def inr_weighted_vjp(mlp: MlpHandle, theta: torch.Tensor, N: int, idx: torch.Tensor,
+                     v: torch.Tensor, scale: float, want_f32: bool = False, stream=None):
+    """scale * sum_k v[idx[k]] grad f(x_idx[k]) as FP64 (and FP32 if asked)."""
+    L = lib()
+    grd = grid_desc(mlp.spec.d, N)
+    dev = theta.device
+    g64 = torch.empty(mlp.p, dtype=torch.float64, device=dev)
+    g32 = torch.empty(mlp.p, dtype=torch.float32, device=dev) if want_f32 else None
+    nb = L.inrct_vjp_ws_bytes(ctypes.byref(mlp.desc), ctypes.byref(grd), idx.numel())
+    ws = _ws(nb, dev)
+    _check(L.inr_weighted_vjp(ctypes.byref(mlp.desc), _ptr(theta, torch.float32), ctypes.byref(grd),
+                              _ptr(idx, torch.int32), idx.numel(), _ptr(v, torch.float32),
+                              float(scale), _ptr(g64), _ptr(g32), _ptr(ws), nb, _stream(stream)))
+    return (g64, g32) if want_f32 else g64
+
+
+def step_ws_bytes(g: synth.GeomSpec, mlp: MlpHandle, n_idx: int) -> int:
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    return int(lib().inrct_step_ws_bytes(ctypes.byref(gd), ctypes.byref(grd), ctypes.byref(mlp.desc),
+                                         n_idx))
+
+
+def grad_step(g: synth.GeomSpec, mlp: MlpHandle, theta: torch.Tensor, y: torch.Tensor,
+              idx: torch.Tensor, scale: float, adam: Adam | None, m: torch.Tensor | None,
+              s: torch.Tensor | None, loss_out: torch.Tensor | None = None,
+              grad_out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+              loss_kind: int = LOSS_LS, stream=None):
+    """Algorithm 1 + Adam in place on theta/m/s.  ws may be preallocated (step_ws_bytes)."""
+    L = lib()
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    if ws is None:
+        ws = _ws(step_ws_bytes(g, mlp, idx.numel()), theta.device)
+    _check(L.grad_step(ctypes.byref(gd), ctypes.byref(grd), ctypes.byref(mlp.desc), loss_kind,
+                       _ptr(theta, torch.float32), _ptr(y, torch.float32), _ptr(idx, torch.int32),
+                       idx.numel(), float(scale), ctypes.byref(adam) if adam is not None else None,
+                       _ptr(m), _ptr(s), _ptr(loss_out), _ptr(grad_out), _ptr(ws), ws.numel(),
+                       _stream(stream)))
+
+
+def adam(lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, t=1) -> Adam:
+    return Adam(lr, beta1, beta2, eps, t)
+
+
+class InrVirtualLoss(torch.autograd.Function):
+    """Virtual loss of Eq. (3): L~(theta) = scale * sum_{i in I} v_i f_theta(x_i), v held constant.
+
+    forward evaluates L~ with the library's VJP machinery absent: the value
+    needs f at the listed points only, taken from the full-grid evaluation
+    image E{f} that Algorithm 1 already produced (gathered here by index);
+    backward returns grad_out * the library's fused weighted VJP (Eq. 2), so
+    autograd through theta never stores per-point activations.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, image, v, idx, scale, mlp, N):
+        ctx.save_for_backward(theta, v, idx)
+        ctx.scale, ctx.mlp, ctx.N = float(scale), mlp, int(N)
+        vi = v[idx.long()].double()
+        return (ctx.scale * (vi * image[idx.long()].double()).sum()).reshape(())
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        theta, v, idx = ctx.saved_tensors
+        g = inr_weighted_vjp(ctx.mlp, theta, ctx.N, idx, v, ctx.scale)
+        return (grad_out.to(g.dtype) * g).to(theta.dtype), None, None, None, None, None, None

@@ -1,0 +1,96 @@
+"""The C-ABI library loads, exports every symbol include/inrct.h declares, and
+rejects bad arguments on the host before any GPU work (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+
+from paper_2604_09884_gb300 import build as B
+from paper_2604_09884_gb300 import inrct, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "inrct.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return inrct.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert {"project", "backproject", "inr_eval_grid", "inr_weighted_vjp", "grad_step"} <= set(names)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_param_and_ray_counts(L):
+    for w in synth.workloads().values():
+        B_ = torch.zeros(max(w.arch.n_feat, 1), w.arch.d)
+        h = inrct.MlpHandle(inrct.Mlp(0 if w.arch.kind == "ffn" else 1, w.arch.d, w.arch.n_feat,
+                                      ctypes.c_void_p(256).value, w.arch.omega0, w.arch.n_hidden,
+                                      w.arch.width, inrct.FP32), None, w.arch)
+        assert inrct.num_params(h) == w.arch.p
+        assert inrct.num_rays(w.geom) == w.geom.m
+
+
+def _fake(n=4096):
+    return ctypes.c_void_p(n)
+
+
+def test_validation_errors_are_reported_on_the_host(L):
+    g = synth.GeomSpec("fan2d", 64, 10, 91, sod=100.0, sdd=150.0, span=6.283)
+    gd, grd = inrct.geom_desc(g), inrct.grid_desc(2, 64)
+    nb = L.inrct_project_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
+    assert nb > 0
+    # workspace too small
+    rc = L.project(ctypes.byref(gd), ctypes.byref(grd), _fake(), _fake(), None, None, None,
+                   _fake(), nb - 512, None)
+    assert rc == 3 and b"workspace" in L.inrct_last_error()
+    # NULL image
+    rc = L.project(ctypes.byref(gd), ctypes.byref(grd), None, _fake(), None, None, None, _fake(),
+                   nb, None)
+    assert rc == 1
+    # grid/geometry dimension mismatch
+    grd3 = inrct.grid_desc(3, 64)
+    assert L.backproject(ctypes.byref(gd), ctypes.byref(grd3), _fake(), _fake(), _fake(), 1 << 30,
+                         None) == 1
+    # source inside the grid
+    bad = inrct.geom_desc(synth.GeomSpec("fan2d", 64, 10, 91, sod=20.0, sdd=40.0))
+    assert L.backproject(ctypes.byref(bad), ctypes.byref(grd), _fake(), _fake(), _fake(), 1 << 30,
+                         None) == 1
+    # cone too wide for x/y driving axes
+    wide = inrct.geom_desc(synth.GeomSpec("cone3d", 64, 4, 64, 2000, sod=100.0, sdd=150.0))
+    assert L.project(ctypes.byref(wide), ctypes.byref(grd3), _fake(), _fake(), None, None, None,
+                     _fake(), 1 << 40, None) == 2
+    # n_idx = 0
+    a = synth.ArchSpec("siren", 2, 64, 2)
+    m = inrct.Mlp(1, 2, 0, None, 30.0, 2, 64, inrct.FP32)
+    rc = L.inr_weighted_vjp(ctypes.byref(m), _fake(), ctypes.byref(grd), _fake(), 0, _fake(), 1.0,
+                            _fake(), None, _fake(), 1 << 30, None)
+    assert rc == 1 and b"n_idx" in L.inrct_last_error()
+    # unsupported width
+    m_bad = inrct.Mlp(1, 2, 0, None, 30.0, 2, 96, inrct.FP32)
+    assert L.inr_eval_grid(ctypes.byref(m_bad), _fake(), ctypes.byref(grd), _fake(), _fake(),
+                           1 << 30, None) == 1
+    # FFN without its Fourier matrix
+    m_ffn = inrct.Mlp(0, 2, 16, None, 0.0, 2, 64, inrct.FP32)
+    assert L.inr_eval_grid(ctypes.byref(m_ffn), _fake(), ctypes.byref(grd), _fake(), _fake(),
+                           1 << 30, None) == 1
+    assert L.inrct_vjp_ws_bytes(ctypes.byref(m), ctypes.byref(grd), 1000) > 0
+    assert L.inrct_step_ws_bytes(ctypes.byref(gd), ctypes.byref(grd), ctypes.byref(m), 1000) > 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(inrct, "_lib", None)
+    monkeypatch.setattr(inrct, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(inrct.InrctError):
+        inrct.lib()

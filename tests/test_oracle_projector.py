@@ -261,3 +261,31 @@ def test_ray_definitions():
             assert np.linalg.norm(s - S) < 1e-14
             w = (bin_ - S) / np.linalg.norm(bin_ - S)
             assert np.linalg.norm(e - w) < 1e-14
+
+
+def test_ramp_filter_matrix_and_spectrum():
+    # F as an explicit Toeplitz matrix from the textbook taps, and the ramp's
+    # properties: zero response to a constant (away from the detector edges),
+    # symmetric, positive semi-definite (its spectrum is |omega| >= 0).
+    g = O.Geometry("par2d", 32, 2, 41, du=1.0)
+    tau = 2.0 / 32
+    A = g.A
+
+    def h(k):
+        if k == 0:
+            return 1 / (4 * tau * tau)
+        return -1 / (math.pi ** 2 * k * k * tau * tau) if k % 2 else 0.0
+
+    F = np.array([[tau * h(b - c) for c in range(A)] for b in range(A)])
+    r = np.random.default_rng(3).normal(size=g.m)
+    np.testing.assert_allclose(O.ramp_filter(g, r), (r.reshape(2, A) @ F.T).reshape(-1),
+                               rtol=0, atol=1e-12)
+    assert np.allclose(F, F.T)
+    assert np.linalg.eigvalsh(F).min() > -1e-9
+    # long constant row: the centre of the output tends to zero like 1/A
+    g2 = O.Geometry("par2d", 32, 1, 4001, du=1.0)
+    out = O.ramp_filter(g2, np.ones(g2.m))
+    assert abs(out[2000]) < 1e-3 * abs(out[0])
+    L, Fd = O.fls_loss(g, r + 1.0, np.ones(g.m))
+    want = 0.5 * sum(rr @ F @ rr for rr in r.reshape(2, A))
+    assert abs(L - want) < 1e-9 * abs(want)
