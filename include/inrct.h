@@ -211,6 +211,23 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
               const inrct_adam* adam, float* adam_m, float* adam_s, double* loss_out,
               double* grad_out, void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/*
+ * inrct_gemm_tn -- the split-K tensor-core GEMM that forms the weight
+ * gradients of the BF16 path (dW_l = sum over points of delta_l a_{l-1}^T,
+ * Sec. 3, Eq. 2), exposed for diagnostics:
+ *   C[m][n]      = sum_k X[k][m] Y[k][n]      n < N        (main block)
+ *   C[m][N]      = sum_k X[k][m]                            (ones block, 16 columns; first used)
+ *   C[m][N+16+c] = sum_k X[k][m] Y16[c][k]    c < 16       (K-major extra block)
+ * X [K][M], Y [K][N] and Y16 [16][K] are row-major BF16 (Y16 may be NULL:
+ * zeros); C [M][N+32] FP32 row-major, overwritten.  M a multiple of 128
+ * (<= 4096), N in {0, 64, 128, 192, 256}.  Partials per split of K are summed
+ * in FP64.  ws: inrct_gemm_tn_ws_bytes(K, M, N).
+ */
+size_t inrct_gemm_tn_ws_bytes(int64_t K, int M, int N);
+int inrct_gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int N, float* C,
+                  void* ws, size_t ws_bytes, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -207,6 +207,19 @@ def grid_coords(d: int, N: int, idx=None) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
+def grid_coords_fp32(d: int, N: int, idx=None) -> np.ndarray:
+    """The pixel centres as an FP32 kernel forms them, for decisions only: the
+    FP32 value nearest (2k + 1 - N) / N (FP64 division, then FP32)."""
+    if idx is None:
+        idx = np.arange(N ** d, dtype=np.int64)
+    idx = np.asarray(idx, dtype=np.int64)
+    c = lambda k: ((2 * k + 1 - N) / N).astype(np.float32)
+    cols = [c(idx % N), c((idx // N) % N)]
+    if d == 3:
+        cols.append(c(idx // (N * N)))
+    return np.stack(cols, axis=1)
+
+
 # ----------------------------------------------------------------------------
 # INR f_theta (Sec. 4: Fourier-feature ReLU networks and SIREN)
 # ----------------------------------------------------------------------------
@@ -267,34 +280,81 @@ def encode(arch: Arch, X: np.ndarray) -> np.ndarray:
     return X
 
 
-def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False):
+def bf16_round(a) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), as float64 values."""
+    f = np.asarray(a, dtype=np.float64).astype(np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _fp32_features(arch: Arch, X32: np.ndarray) -> np.ndarray:
+    """The Fourier features as an FP32 kernel forms them, for mask decisions only:
+    FP32 coordinates (``grid_coords_fp32``), phase B.x with each product and sum
+    rounded to FP32 (x, then y, then z), reduced to t = ph - rint(ph), then
+    cos / sin(2 pi t) rounded to FP32."""
+    x = np.asarray(X32, dtype=np.float32)
+    B = np.asarray(arch.B, dtype=np.float64).astype(np.float32)
+    ph = (x[:, 0:1] * B[None, :, 0]).astype(np.float32) + (x[:, 1:2] * B[None, :, 1]).astype(np.float32)
+    ph = ph.astype(np.float32)
+    if arch.d == 3:
+        ph = (ph + (x[:, 2:3] * B[None, :, 2]).astype(np.float32)).astype(np.float32)
+    t = (ph - np.rint(ph)).astype(np.float32)
+    a = np.pi * (2.0 * t.astype(np.float64))
+    return np.concatenate([np.cos(a).astype(np.float32), np.sin(a).astype(np.float32)], axis=1)
+
+
+def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | None = None,
+            X32: np.ndarray | None = None):
     """f_theta(x_i) for every row of X.  With keep=True also returns the
-    per-layer inputs h_{l-1} and pre-activations z_l needed by ``vjp``."""
+    per-layer inputs h_{l-1}, pre-activations z_l and ReLU masks used by ``vjp``.
+
+    ReLU masks are decisions that floating point takes.  decide=None takes them
+    on the FP64 pre-activations.  decide='bf16' takes them as a BF16 tensor-core
+    kernel does: on pre-activations formed from BF16-rounded weights and
+    BF16-rounded layer inputs (accumulated wide, bias added unrounded), starting
+    from the FP32 features of ``_fp32_features``, the rounded chain being
+    carried alongside; every value stays FP64 and the ReLU output is mask * z.
+    X32 gives the FP32 coordinates of the decision chain (default: X rounded).
+    """
     layers = unpack(arch, theta)
     h = encode(arch, X)
-    hs, zs = [h], []
+    hd = None
+    if decide == "bf16" and arch.kind == "ffn":
+        X32 = np.asarray(X).astype(np.float32) if X32 is None else X32
+        hd = bf16_round(_fp32_features(arch, X32))
+    hs, zs, masks = [h], [], []
     for li, (W, b) in enumerate(layers):
         z = h @ W.T + b
         zs.append(z)
         if li == len(layers) - 1:
             h = z
         elif arch.kind == "ffn":
-            h = np.maximum(z, 0.0)
+            if hd is not None:
+                zd = hd @ bf16_round(W).T + b
+                m = zd > 0.0
+                hd = bf16_round(np.where(m, zd, 0.0))
+            else:
+                m = z > 0.0
+            masks.append(m)
+            h = np.where(m, z, 0.0)
         else:
             h = np.sin(arch.omega0 * z)
         hs.append(h)
     f = h[:, 0]
-    return (f, hs, zs) if keep else f
+    return (f, hs, zs, masks) if keep else f
 
 
-def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray) -> np.ndarray:
+def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray, decide: str | None = None,
+        X32: np.ndarray | None = None) -> np.ndarray:
     """sum_i w_i grad_theta f_theta(x_i), by reverse mode written out layer by layer.
 
     This is the Jacobian-transpose product [d E{f}/d theta]^T w of Sec. 3.
-    ReLU'(0) is taken as 0.
+    ReLU'(0) is taken as 0; ``decide`` picks how ReLU masks are decided (see
+    ``forward``).
     """
     layers = unpack(arch, theta)
-    _, hs, zs = forward(arch, theta, X, keep=True)
+    _, hs, zs, masks = forward(arch, theta, X, keep=True, decide=decide, X32=X32)
     w = np.asarray(w, dtype=np.float64)
     grads = [None] * len(layers)
     # df/dz_out = 1, weighted per point by w_i
@@ -308,7 +368,7 @@ def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray) -> np.ndarray:
         g_h = delta @ W                                 # dL/dh_{li}
         z_prev = zs[li - 1]
         if arch.kind == "ffn":
-            delta = g_h * (z_prev > 0.0)
+            delta = g_h * masks[li - 1]
         else:
             delta = g_h * (arch.omega0 * np.cos(arch.omega0 * z_prev))
     flat = []
@@ -348,17 +408,19 @@ def full_gradient(arch: Arch, theta, g: Geometry, y):
     return L, grad, v
 
 
-def estimator(arch: Arch, theta, g: Geometry, v, I, scale=None) -> np.ndarray:
+def estimator(arch: Arch, theta, g: Geometry, v, I, scale=None, decide=None) -> np.ndarray:
     """Eq. (2): (n/|I|) sum_{i in I} v_i grad f(x_i), for the given index set I.
 
-    ``scale`` defaults to n/|I|; v is the backprojected residual (P^T r).
+    ``scale`` defaults to n/|I|; v is the backprojected residual (P^T r);
+    ``decide`` picks how ReLU masks are decided (see ``forward``).
     """
     I = np.asarray(I, dtype=np.int64)
     n = g.n
     if scale is None:
         scale = n / I.size
     X = grid_coords(g.d, g.N, I)
-    return vjp(arch, theta, X, scale * np.asarray(v, dtype=np.float64)[I])
+    return vjp(arch, theta, X, scale * np.asarray(v, dtype=np.float64)[I], decide=decide,
+               X32=grid_coords_fp32(g.d, g.N, I))
 
 
 def virtual_loss(arch: Arch, theta, g: Geometry, v, I, scale=None) -> float:

@@ -226,4 +226,12 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
   return INRCT_OK;
 }
 
+size_t inrct_gemm_tn_ws_bytes(int64_t K, int M, int N) { return gemm_tn_ws_bytes(K, M, N); }
+
+int inrct_gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int N, float* C,
+                  void* ws, size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  return gemm_tn(X, Y, Y16, K, M, N, C, ws, ws_bytes, stream);
+}
+
 }  // extern "C"

@@ -20,14 +20,17 @@ struct Net {
 
 int make_net(const inrct_mlp* mlp, const inrct_grid* grid, Net* net);
 
-// Flat grid index -> coordinate on [-1, 1] of one axis.
-__device__ __forceinline__ float grid_coord(int64_t k, float D) { return -1.f + ((float)k + 0.5f) * D; }
+// Grid index k -> pixel-centre coordinate -1 + (k + 1/2) 2/N = (2k + 1 - N) / N, formed
+// as one correctly rounded FP32 division of exact integers (the FP32 value nearest
+// the true centre).
+__device__ __forceinline__ float grid_coord(int64_t k, int N) {
+  return __fdiv_rn((float)(2 * k + 1 - N), (float)N);
+}
 
 __device__ __forceinline__ void point_coords(int64_t i, int N, int d, float* x) {
-  const float D = 2.f / (float)N;
-  x[0] = grid_coord(i % N, D);
-  x[1] = grid_coord((i / N) % N, D);
-  x[2] = d == 3 ? grid_coord(i / ((int64_t)N * N), D) : 0.f;
+  x[0] = grid_coord(i % N, N);
+  x[1] = grid_coord((i / N) % N, N);
+  x[2] = d == 3 ? grid_coord(i / ((int64_t)N * N), N) : 0.f;
 }
 
 // FP32 SIMT path
@@ -48,6 +51,11 @@ size_t tc_vjp_ws_bytes(const Net& net, int64_t n_idx);
 int tc_vjp(const Net& net, const float* theta, int N, const int32_t* idx, int64_t n_idx,
            const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
            size_t ws_bytes, cudaStream_t st);
+
+// split-K TN GEMM of the weight gradients, exposed for diagnostics
+size_t gemm_tn_ws_bytes(int64_t K, int M, int N);
+int gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int N, float* C, void* ws,
+            size_t ws_bytes, cudaStream_t st);
 
 // shared small kernels (optim.cu)
 int adam_update(float* theta, const double* grad, float* m, float* s, int64_t p,

@@ -1,9 +1,1080 @@
-// placeholder: BF16 tensor-core path not built yet
+// BF16 tensor-core (tcgen05) path of the INR: grid evaluation E{f} (Sec. 3)
+// and the residual-weighted VJP of Eq. (2) / the virtual loss of Eq. (3).
+//
+// Fused MLP tile engine (mlp_tile_kernel)
+// ---------------------------------------
+// A persistent CTA walks tiles of 128 points.  Per tile it runs a program of
+// GEMM stages, each D[128 x W] = A[128 x K] * B[W x K]^T with A the stage
+// input (BF16, in shared memory, K-major 64-column panels) and B a weight
+// matrix streamed by TMA through a 4-slot ring; D accumulates in FP32 in
+// tensor memory (two W-column buffers, so stage s+1 accumulates while the
+// epilogue still reads stage s).  Warp roles:
+//   warps 0-7  epilogue: build the first input (Fourier features or the
+//              SIREN first layer, FP32 on the CUDA cores), then after every
+//              stage read D from TMEM, add the bias, apply the activation
+//              (FP32), re-stage the result as the next stage's BF16 A panels.
+//              Panel c of the next stage is released as soon as it is written,
+//              so the next stage's MMAs overlap the rest of the epilogue.
+//   warp 8     TMA producer of the weight ring.
+//   warp 9     MMA issuer (one elected thread).
+// SIREN layers keep omega0 folded into their BF16 weights and FP32 biases
+// (u = omega0 (W h + b) = W' h + b'), so the epilogue applies sin(u).
+//
+// VJP program: the forward stages, then backward stages
+// delta_{l-1} = (W'_l^T delta_l) * sigma'(u_{l-1}) fed by a transposed weight
+// copy.  The epilogues write, for the listed points only, the activations a_l,
+// the deltas delta_l (and cos(u_l) for SIREN) to scratch, [points][features]
+// BF16.  A split-K TN GEMM (tn_gemm_kernel) then forms
+// dW_l = sum_points delta_l a_{l-1}^T and db_l = sum_points delta_l (a ones
+// operand) with MN-major operands straight from that scratch; FP32 partials
+// per split are reduced in FP64 into the gradient.  Scratch grows with the
+// number of listed points (chunked), never with the grid.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
 #include "mlp.cuh"
+#include "tc_ptx.cuh"
+
 namespace inrct {
-bool tc_supported(const Net&, char* why, size_t n) { snprintf(why, n, "not built"); return false; }
-size_t tc_eval_ws_bytes(const Net&) { return 0; }
-int tc_eval(const Net&, const float*, int, int64_t, float*, void*, size_t, cudaStream_t) { return INRCT_ERR_UNSUPPORTED; }
-size_t tc_vjp_ws_bytes(const Net&, int64_t) { return 0; }
-int tc_vjp(const Net&, const float*, int, const int32_t*, int64_t, const float*, double, double*, float*, void*, size_t, cudaStream_t) { return INRCT_ERR_UNSUPPORTED; }
+
+using namespace tc;
+
+namespace {
+
+constexpr int kTile = 128;       // points per tile (MMA M)
+constexpr int kRing = 4;         // weight ring slots
+constexpr int kPanelBytes = kTile * 128;  // one 64-column BF16 panel of 128 rows
+constexpr int kMaxStages = 2 * kMaxLayers;
+constexpr int kEpiThreads = 256;
+constexpr int kThreads = kEpiThreads + 64;
+constexpr int kMaxJobs = 24;
+
+// ---------------------------------------------------------------------------
+// host: tensor maps
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
 }
+
+// 2-D BF16 row-major tensor [outer][inner], 128-byte swizzled boxes of {box_inner, box_outer}.
+int make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+             uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is unavailable from the driver");
+    return INRCT_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d): dims %llu x %llu box %u x %u", (int)r,
+              (unsigned long long)inner, (unsigned long long)outer, box_inner, box_outer);
+    return INRCT_ERR_CUDA;
+  }
+  return INRCT_OK;
+}
+
+struct alignas(64) Maps {
+  CUtensorMap m[kMaxJobs];
+};
+
+// ---------------------------------------------------------------------------
+// weight preparation: BF16 (W' = scale W) row-major and transposed, FP32 biases
+// ---------------------------------------------------------------------------
+__global__ void prep_weights_kernel(const float* __restrict__ theta, int64_t offW, int64_t offb,
+                                    int out, int in, float scale, __nv_bfloat16* __restrict__ Wb,
+                                    __nv_bfloat16* __restrict__ WbT, float* __restrict__ bias) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (int64_t)out * in) {
+    const int o = (int)(t / in), k = (int)(t % in);
+    const __nv_bfloat16 w = __float2bfloat16_rn(scale * theta[offW + t]);
+    Wb[t] = w;
+    if (WbT) WbT[(int64_t)k * out + o] = w;
+  }
+  if (t < out) bias[t] = scale * theta[offb + t];
+}
+
+// ---------------------------------------------------------------------------
+// split-K TN GEMM:  C[m][n] = sum_k X[k][m] * Y[k][n]   (X, Y BF16, MN-major)
+// plus two optional 16-column blocks: ones (C1[m] = sum_k X[k][m]) and a
+// K-major [16][K] operand Y16 (C2[m][c] = sum_k X[k][m] Y16[c][k]).
+// Output: FP32 partial per split, [split][M][ldc] with ldc = N + 32.
+// ---------------------------------------------------------------------------
+struct GemmJob {
+  int M, N, n0;           // rows (multiple of 128), main columns (0 or multiple of 64, <= 256), Y column offset
+  int has_ones, has_y16;  // extra column blocks
+  int mx, my, my16;       // map indices
+  int mtiles;             // M / 128
+  int64_t part_off;       // offset (floats) of this job's partials
+  // reduction into theta's gradient
+  int64_t offW;  // gradient offset of the weight block (row stride ldW)
+  int ldW;       // row length of the weight block in theta
+  int w_src;     // 0: main columns [0, w_cols); 1: y16 columns [0, w_cols)
+  int w_cols;
+  int64_t offb;  // gradient offset of the bias (or -1)
+  double mult;   // omega0 for SIREN sine layers, else 1
+};
+
+struct GemmPlan {
+  int n_jobs;
+  int S;              // splits of K
+  int64_t K;          // points
+  int64_t per_split;  // points per split (multiple of 64)
+  int cta_begin[kMaxJobs + 1];
+  GemmJob job[kMaxJobs];
+};
+
+constexpr int kGemmStages = 4;
+constexpr int kGemmStageBytes = 16384 + 32768 + 2048;  // X (128 x 64), Y (64 x 256), Y16 (16 x 64)
+
+__global__ void __launch_bounds__(192, 1)
+    tn_gemm_kernel(const __grid_constant__ Maps maps, const __grid_constant__ GemmPlan plan,
+                   float* __restrict__ part,
+                   int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  uint8_t* ones = smem + kGemmStages * kGemmStageBytes;  // 16 rows x 128 B of BF16 ones
+  __shared__ uint64_t full[kGemmStages], empty[kGemmStages], accf;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  int jb = 0;
+  while (jb + 1 < plan.n_jobs && (int)blockIdx.x >= plan.cta_begin[jb + 1]) ++jb;
+  const GemmJob& J = plan.job[jb];
+  const int local = blockIdx.x - plan.cta_begin[jb];
+  const int mt = local % J.mtiles, sp = local / J.mtiles;
+  const int64_t k_begin = (int64_t)sp * plan.per_split;
+  const int64_t k_end = min(plan.K, k_begin + plan.per_split);
+  const int nch = k_end > k_begin ? (int)((k_end - k_begin + 63) / 64) : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGemmStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accf, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < 16 * 128 / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ones)[i] = 0x3F803F80u;  // two BF16 ones
+  fence_async_smem();
+  if (warp == 2) tmem_alloc(&tmem_base, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t xbytes = 2 * 8192, ybytes = (uint32_t)J.N * 128, y16bytes = J.has_y16 ? 2048 : 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t ep = 1;
+      for (int c = 0; c < nch; ++c) {
+        const int s = c % kGemmStages;
+        if (c > 0 && s == 0) ep ^= 1;
+        if (!mbar_wait(&empty[s], ep, &abort_flag, err, 101)) break;
+        uint8_t* st = smem + s * kGemmStageBytes;
+        mbar_arrive_expect_tx(&full[s], xbytes + ybytes + y16bytes);
+        const int k0 = (int)(k_begin + 64 * c);
+        tma_load_2d(st, &maps.m[J.mx], &full[s], mt * 128, k0);
+        tma_load_2d(st + 8192, &maps.m[J.mx], &full[s], mt * 128 + 64, k0);
+        for (int b = 0; b < J.N / 64; ++b)
+          tma_load_2d(st + 16384 + b * 8192, &maps.m[J.my], &full[s], J.n0 + 64 * b, k0);
+        if (J.has_y16) tma_load_2d(st + 16384 + 32768, &maps.m[J.my16], &full[s], k0, 0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t fp = 0;
+      const uint32_t id_main = idesc_bf16(128, J.N > 0 ? J.N : 16, true, true);
+      const uint32_t id_16 = idesc_bf16(128, 16, true, false);
+      bool issued = false;
+      for (int c = 0; c < nch; ++c) {
+        const int s = c % kGemmStages;
+        if (c > 0 && s == 0) fp ^= 1;
+        if (!mbar_wait(&full[s], fp, &abort_flag, err, 102)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * kGemmStageBytes);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint64_t ad = desc_sw128(st + j * 2048, 8192, 1024);
+          const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
+          if (J.N > 0) mma_bf16(tmem, ad, desc_sw128(st + 16384 + j * 2048, 8192, 1024), id_main, acc);
+          if (J.has_ones) mma_bf16(tmem + 256, ad, desc_sw128(smem_u32(ones) + j * 32, 16, 1024), id_16, acc);
+          if (J.has_y16)
+            mma_bf16(tmem + 272, ad, desc_sw128(st + 16384 + 32768 + j * 32, 16, 1024), id_16, acc);
+        }
+        issued = true;
+        mma_commit(&empty[s]);
+      }
+      if (issued) mma_commit(&accf);
+      else mbar_arrive(&accf);
+    }
+  } else {
+    // epilogue warps 2..5: lanes 32*(warp%4) .. of TMEM = rows of C
+    const int q = warp & 3;
+    const int row = mt * 128 + q * 32 + lane;
+    const int ldc = J.N + 32;
+    float* out = part + J.part_off + ((int64_t)sp * J.M + row) * ldc;
+    const bool ok = warp_wait(&accf, 0, &abort_flag, err, 103);
+    tc_fence_after();
+    float v[32];
+    auto emit = [&](int col, int tcol) {
+      if (nch > 0 && ok) {
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + tcol, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 32; i += 4)
+        *reinterpret_cast<float4*>(out + col + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    };
+    for (int c0 = 0; c0 < J.N; c0 += 32) emit(c0, c0);
+    // ones block (16 columns) and the Y16 block (16 columns); absent blocks hold zeros
+    if (nch > 0 && ok) {
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + 256, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (!J.has_ones) v[i] = 0.f;
+      if (!J.has_y16) v[16 + i] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i += 4)
+      *reinterpret_cast<float4*>(out + J.N + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// grad[...] (+)= mult * sum_s part[s][m][c] for every (job, m, c) that maps to theta.
+__global__ void gemm_reduce_kernel(const __grid_constant__ GemmPlan plan, const float* __restrict__ part,
+                                   int accumulate, double* __restrict__ grad) {
+  const int jb = blockIdx.y;
+  const GemmJob& J = plan.job[jb];
+  const int cols = J.w_cols + (J.offb >= 0 ? 1 : 0);
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)J.M * cols) return;
+  const int m = (int)(e / cols), c = (int)(e % cols);
+  const int ldc = J.N + 32;
+  int col;
+  int64_t dst;
+  if (c < J.w_cols) {
+    col = J.w_src == 0 ? c : J.N + 16 + c;
+    dst = J.offW + (int64_t)m * J.ldW + J.n0 + c;
+  } else {
+    col = J.N;  // first column of the ones block
+    dst = J.offb + m;
+  }
+  double s = 0.0;
+  for (int q = 0; q < plan.S; ++q) s += (double)part[J.part_off + ((int64_t)q * J.M + m) * ldc + col];
+  s *= J.mult;
+  grad[dst] = accumulate ? grad[dst] + s : s;
+}
+
+// Output-layer bias gradient: grad[off] (+)= sum_k scale * v[idx[k]] (FP64, one block, fixed order).
+__global__ void out_bias_grad_kernel(const int32_t* __restrict__ idx, int64_t npts,
+                                     const float* __restrict__ v, int64_t n_grid, float scale,
+                                     int accumulate, double* __restrict__ grad) {
+  __shared__ double sh[1024];
+  double s = 0.0;
+  for (int64_t k = threadIdx.x; k < npts; k += blockDim.x) {
+    const int64_t i = idx[k];
+    if (i >= 0 && i < n_grid) s += (double)(scale * v[i]);
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) grad[0] = accumulate ? grad[0] + sh[0] : sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// fused MLP tile engine
+// ---------------------------------------------------------------------------
+enum StageKind { kFwdHidden = 0, kFwdLast = 1, kBwd = 2 };
+
+struct TileProg {
+  int mode;  // 0 eval, 1 vjp
+  int kind, d, F, W, L, N;
+  int64_t n_grid, npts;
+  float omega0;
+  const float* B;       // F x d (FFN)
+  const float* theta;   // FP32 parameters (SIREN first layer, output layer)
+  const float* bias;    // folded FP32 biases, [L][W]
+  int64_t offW0, offb0, offWout, offbout;  // theta offsets (first layer, output layer)
+  int n_stages;
+  int st_kind[kMaxStages], st_layer[kMaxStages], st_panels[kMaxStages], st_map[kMaxStages];
+  int in_panels;        // panels of the first stage's input
+  // eval
+  float* out;
+  // vjp
+  const int32_t* idx;
+  const float* v;
+  float scale;
+  __nv_bfloat16* E;     // [npts_pad][2F] layer-1 input (FFN)
+  __nv_bfloat16* Act;   // [L][npts_pad][W] activations a_l
+  __nv_bfloat16* Dlt;   // [L][npts_pad][W] deltas
+  __nv_bfloat16* Cos;   // [L][npts_pad][W] cos(u_l) (SIREN)
+  __nv_bfloat16* Y16c;  // [16][npts_pad] coordinates (SIREN)
+  __nv_bfloat16* Y16o;  // [16][npts_pad] output-layer weights scale * v
+  int64_t npts_pad;
+  int stall;            // diagnostic: the producer issues nothing (tests bounded waits)
+};
+
+__device__ __forceinline__ void store_row32_bf16(__nv_bfloat16* dst, const float* v) {
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    d4[q] = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                       pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+}
+
+__device__ __forceinline__ void load_row32_bf16(const __nv_bfloat16* src, float* v) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4 w = s4[q];
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[8 * q + 2 * k] = __uint_as_float(u[k] << 16);
+      v[8 * q + 2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
+    }
+  }
+}
+
+// Phase B_f . x of Fourier feature f, rounded operation by operation in a fixed
+// order (products, then sums left to right), so that the value is reproducible.
+__device__ __forceinline__ float feat_phase(const float* Bf, const float* x, int d) {
+  float ph = __fadd_rn(__fmul_rn(Bf[0], x[0]), __fmul_rn(Bf[1], x[1]));
+  if (d == 3) ph = __fadd_rn(ph, __fmul_rn(Bf[2], x[2]));
+  return ph;
+}
+
+// cos or sin of 2 pi ph: ph is reduced to t in [-1/2, 1/2] exactly, then
+// sincospif(2t) (accurate to about an FP32 ulp).  The features feed ReLU mask
+// decisions downstream, so they are computed accurately rather than with the
+// hardware approximations.
+__device__ __forceinline__ float four_feat(float ph, bool want_sin) {
+  const float t = __fsub_rn(ph, rintf(ph));
+  float s, c;
+  sincospif(2.f * t, &s, &c);
+  return want_sin ? s : c;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_tile_kernel(const __grid_constant__ Maps maps, const __grid_constant__ TileProg P,
+                    int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  uint8_t* apan = smem;                      // 4 x 16 KB input panels
+  uint8_t* ring = smem + 4 * kPanelBytes;    // kRing x (W x 128 B) weight chunks
+  __shared__ uint64_t w_full[kRing], w_empty[kRing], a_full[4], a_empty[4], acc_full[2], acc_empty[2],
+      dot_bar, drain_bar;
+  __shared__ float dotp[2][kTile];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int W = P.W;
+  const uint32_t chunk_bytes = (uint32_t)W * 128;
+  const int64_t n_tiles = (P.npts + kTile - 1) / kTile;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kRing; ++s) {
+      mbar_init(&w_full[s], 1);
+      mbar_init(&w_empty[s], 1);
+    }
+    for (int s = 0; s < 4; ++s) {
+      mbar_init(&a_full[s], kEpiThreads);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], kEpiThreads);
+    }
+    mbar_init(&dot_bar, kEpiThreads);
+    mbar_init(&drain_bar, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * W);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 8) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0 && !P.stall) {
+      for (int s = 0; s < P.n_stages; ++s) prefetch_map(&maps.m[P.st_map[s]]);
+      uint32_t slot = 0, ep = 1;
+      for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        for (int s = 0; s < P.n_stages; ++s) {
+          for (int c = 0; c < P.st_panels[s]; ++c) {
+            if (!mbar_wait(&w_empty[slot], ep, &abort_flag, err, 201)) goto producer_done;
+            mbar_arrive_expect_tx(&w_full[slot], chunk_bytes);
+            tma_load_2d(ring + slot * chunk_bytes, &maps.m[P.st_map[s]], &w_full[slot], 64 * c, 0);
+            if (++slot == kRing) {
+              slot = 0;
+              ep ^= 1;
+            }
+          }
+        }
+      }
+    }
+  producer_done:;
+  } else if (warp == 9) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t slot = 0, wf = 0, aep[2] = {1, 1}, acc_ctr = 0;
+      uint32_t ap[4] = {0, 0, 0, 0};
+      const uint32_t idesc = idesc_bf16(128, W, false, false);
+      bool issued = false;
+      for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        for (int s = 0; s < P.n_stages; ++s) {
+          const uint32_t b = acc_ctr & 1;
+          if (!mbar_wait(&acc_empty[b], aep[b], &abort_flag, err, 301)) goto mma_done;
+          aep[b] ^= 1;
+          tc_fence_after();
+          const uint32_t dcol = tmem + b * W;
+          for (int c = 0; c < P.st_panels[s]; ++c) {
+            const int as = c & 3;
+            if (!mbar_wait(&a_full[as], ap[as], &abort_flag, err, 302)) goto mma_done;
+            ap[as] ^= 1;
+            if (!mbar_wait(&w_full[slot], wf, &abort_flag, err, 303)) goto mma_done;
+            tc_fence_after();
+            const uint32_t abase = smem_u32(apan + as * kPanelBytes);
+            const uint32_t bbase = smem_u32(ring + slot * chunk_bytes);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              mma_bf16(dcol, desc_sw128(abase + 32 * j, 16, 1024), desc_sw128(bbase + 32 * j, 16, 1024),
+                       idesc, (c > 0 || j > 0) ? 1u : 0u);
+            issued = true;
+            mma_commit(&w_empty[slot]);
+            mma_commit(&a_empty[as]);
+            if (++slot == kRing) {
+              slot = 0;
+              wf ^= 1;
+            }
+          }
+          mma_commit(&acc_full[b]);
+          ++acc_ctr;
+        }
+      }
+    mma_done:
+      if (issued) {
+        // drain: every issued MMA completes before TMEM is released (matters on the
+        // abort path; otherwise the epilogue has already waited for all of them)
+        mma_commit(&drain_bar);
+        mbar_wait_drain(&drain_bar, 0);
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 0..7 ----------------
+    const int q = warp & 3, g = warp >> 2;
+    const int r = q * 32 + lane;                 // row of the tile = TMEM lane
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    uint32_t ae[4] = {1, 1, 1, 1}, af[2] = {0, 0}, dotph = 0, acc_ctr = 0;
+    const float* wout = P.theta + P.offWout;
+    const float bout = P.theta[P.offbout];
+    float v[32];
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      const int64_t pt = t * kTile + r;
+      const bool valid = pt < P.npts;
+      int64_t gi = valid ? (P.idx ? (int64_t)P.idx[pt] : pt) : 0;
+      const bool in_range = gi >= 0 && gi < P.n_grid;
+      if (!in_range) gi = 0;
+      float x[3];
+      point_coords(gi, P.N, P.d, x);
+      const float sv = (P.mode == 1 && valid && in_range) ? P.scale * P.v[gi] : 0.f;
+      const int64_t prow = t * kTile + r;        // scratch row (rows are padded to the tile)
+      // ---- first stage input ----
+      for (int c = 0; c < P.in_panels; ++c) {
+        const int col0 = 64 * c + 32 * g;
+        if (P.kind == INRCT_FFN_RELU) {
+          const bool is_sin = col0 >= P.F;
+          const int f0 = is_sin ? col0 - P.F : col0;
+#pragma unroll 4
+          for (int i = 0; i < 32; ++i) {
+            v[i] = four_feat(feat_phase(P.B + (int64_t)(f0 + i) * P.d, x, P.d), is_sin);
+          }
+          if (P.mode == 1) store_row32_bf16(P.E + prow * (2 * P.F) + col0, v);
+        } else {
+          const float* W1 = P.theta + P.offW0;
+          const float* b1 = P.theta + P.offb0;
+          float cs[32];
+#pragma unroll 4
+          for (int i = 0; i < 32; ++i) {
+            const int o = col0 + i;
+            float z = b1[o] + W1[o * P.d] * x[0] + W1[o * P.d + 1] * x[1];
+            if (P.d == 3) z += W1[o * P.d + 2] * x[2];
+            z *= P.omega0;
+            __sincosf(z, &v[i], &cs[i]);
+          }
+          if (P.mode == 1) {
+            store_row32_bf16(P.Act + prow * W + col0, v);
+            store_row32_bf16(P.Cos + prow * W + col0, cs);
+            if (c == 0 && g == 0) {
+              for (int k = 0; k < P.d; ++k) P.Y16c[(int64_t)k * P.npts_pad + prow] = __float2bfloat16_rn(x[k]);
+            }
+          }
+        }
+        const int as = c & 3;
+        if (!warp_wait(&a_empty[as], ae[as], &abort_flag, err, 401)) goto epi_done;
+        ae[as] ^= 1;
+        st_panel_row32(apan + as * kPanelBytes, r, 4 * g, v);
+        fence_async_smem();
+        mbar_arrive(&a_full[as]);
+      }
+      // ---- GEMM stages ----
+      for (int s = 0; s < P.n_stages; ++s) {
+        const uint32_t b = acc_ctr & 1;
+        if (!warp_wait(&acc_full[b], af[b], &abort_flag, err, 402)) goto epi_done;
+        af[b] ^= 1;
+        tc_fence_after();
+        const int kind = P.st_kind[s], l = P.st_layer[s];
+        float dot = 0.f;
+        for (int c = 0; c < W / 64; ++c) {
+          const int col0 = 64 * c + 32 * g;
+          tmem_ld32(tmem + lane_off + b * W + col0, v);
+          const bool write_panel = s + 1 < P.n_stages;  // the next stage's input
+          if (kind == kBwd) {
+            // v = (W'_l^T delta_l) for layer l; delta_{l-1} = v * sigma'(u_{l-1})
+            float sg[32];
+            if (P.kind == INRCT_FFN_RELU) {
+              load_row32_bf16(P.Act + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) v[i] = sg[i] > 0.f ? v[i] : 0.f;
+            } else {
+              load_row32_bf16(P.Cos + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) v[i] *= sg[i];
+            }
+            if (P.mode == 1) store_row32_bf16(P.Dlt + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, v);
+          } else {
+            const float* bl = P.bias + (int64_t)l * W + col0;
+            float cs[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float z = v[i] + bl[i];
+              if (P.kind == INRCT_FFN_RELU) {
+                v[i] = fmaxf(z, 0.f);
+                cs[i] = z > 0.f ? 1.f : 0.f;
+              } else {
+                __sincosf(z, &v[i], &cs[i]);
+              }
+            }
+            if (P.mode == 1) {
+              store_row32_bf16(P.Act + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
+              if (P.kind == INRCT_SIREN && kind == kFwdHidden)
+                store_row32_bf16(P.Cos + ((int64_t)l * P.npts_pad + prow) * W + col0, cs);
+            }
+            if (kind == kFwdLast) {
+              if (P.mode == 0) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) dot = fmaf(v[i], wout[col0 + i], dot);
+              } else {
+                // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = sv * wout[col0 + i] * cs[i];
+                store_row32_bf16(P.Dlt + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
+                if (c == 0 && g == 0) P.Y16o[prow] = __float2bfloat16_rn(sv);
+              }
+            }
+          }
+          if (write_panel) {
+            if (!warp_wait(&a_empty[c], ae[c], &abort_flag, err, 403)) goto epi_done;
+            ae[c] ^= 1;
+            st_panel_row32(apan + c * kPanelBytes, r, 4 * g, v);
+            fence_async_smem();
+            mbar_arrive(&a_full[c]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[b]);
+        ++acc_ctr;
+        if (kind == kFwdLast && P.mode == 0) {
+          dotp[g][r] = dot;
+          mbar_arrive(&dot_bar);
+          if (!warp_wait(&dot_bar, dotph, &abort_flag, err, 404)) goto epi_done;
+          dotph ^= 1;
+          if (g == 0 && valid) P.out[pt] = bout + dotp[0][r] + dotp[1][r];
+        }
+      }
+    }
+  epi_done:;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * W);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+constexpr size_t kTileSmem = 4 * kPanelBytes + (size_t)kRing * 256 * 128 + 1024;
+constexpr size_t kGemmSmem = (size_t)kGemmStages * kGemmStageBytes + 2048 + 1024;
+
+struct TcWeights {
+  __nv_bfloat16* Wb[kMaxLayers];
+  __nv_bfloat16* WbT[kMaxLayers];
+  float* bias;
+};
+
+// Layers handled by the MMA stages: FFN 0..L-1, SIREN 1..L-1 (the SIREN first layer is FP32).
+int first_mma_layer(const Net& n) { return n.kind == INRCT_SIREN ? 1 : 0; }
+
+size_t weights_bytes(const Net& n, bool transposed) {
+  size_t b = 0;
+  for (int l = first_mma_layer(n); l < n.L; ++l)
+    b += align_up(sizeof(__nv_bfloat16) * n.in_dim[l] * n.out_dim[l], 256) * (transposed ? 2 : 1);
+  return b + align_up(sizeof(float) * n.L * n.W, 256) + 256;
+}
+
+int prep_weights(const Net& n, const float* theta, Carver& c, bool transposed, TcWeights* w,
+                 cudaStream_t st) {
+  w->bias = c.take<float>((size_t)n.L * n.W);
+  for (int l = 0; l < kMaxLayers; ++l) w->Wb[l] = w->WbT[l] = nullptr;
+  for (int l = first_mma_layer(n); l < n.L; ++l) {
+    w->Wb[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
+    if (transposed) w->WbT[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
+  }
+  if (!c.ok) return INRCT_ERR_WORKSPACE;
+  const float sc = n.kind == INRCT_SIREN ? n.omega0 : 1.f;
+  for (int l = first_mma_layer(n); l < n.L; ++l) {
+    const int64_t cnt = (int64_t)n.in_dim[l] * n.out_dim[l];
+    prep_weights_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(theta, n.offW[l], n.offb[l], n.out_dim[l],
+                                                          n.in_dim[l], sc, w->Wb[l], w->WbT[l],
+                                                          w->bias + (int64_t)l * n.W);
+  }
+  INRCT_CHECK_LAUNCH("weight preparation");
+  return INRCT_OK;
+}
+
+int set_smem_attr(const void* fn, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) {
+    set_error("shared memory attribute: %s", cudaGetErrorString(e));
+    return INRCT_ERR_CUDA;
+  }
+  return INRCT_OK;
+}
+
+// Builds the stage program and its weight maps.
+int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* maps) {
+  memset(P, 0, sizeof(*P));
+  P->mode = mode;
+  P->kind = n.kind;
+  P->d = n.d;
+  P->F = n.F;
+  P->W = n.W;
+  P->L = n.L;
+  P->omega0 = n.omega0;
+  P->B = n.B;
+  P->bias = w.bias;
+  P->offW0 = n.offW[0];
+  P->offb0 = n.offb[0];
+  P->offWout = n.offW[n.L];
+  P->offbout = n.offb[n.L];
+  P->in_panels = n.kind == INRCT_FFN_RELU ? n.K0 / 64 : n.W / 64;
+  int s = 0, mi = 0;
+  for (int l = first_mma_layer(n); l < n.L; ++l, ++s) {
+    P->st_kind[s] = l == n.L - 1 ? kFwdLast : kFwdHidden;
+    P->st_layer[s] = l;
+    P->st_panels[s] = n.in_dim[l] / 64;
+    P->st_map[s] = mi;
+    INRCT_TRY(make_map(&maps->m[mi++], w.Wb[l], n.in_dim[l], n.out_dim[l], 64, n.out_dim[l]));
+  }
+  if (mode == 1) {
+    for (int l = n.L - 1; l >= 1; --l, ++s) {
+      P->st_kind[s] = kBwd;
+      P->st_layer[s] = l;
+      P->st_panels[s] = n.out_dim[l] / 64;
+      P->st_map[s] = mi;
+      // W'_l^T is [in][out]: rows = in (the MMA N), K = out
+      INRCT_TRY(make_map(&maps->m[mi++], w.WbT[l], n.out_dim[l], n.in_dim[l], 64, n.in_dim[l]));
+    }
+  }
+  P->n_stages = s;
+  return INRCT_OK;
+}
+
+}  // namespace
+
+bool tc_supported(const Net& n, char* why, size_t len) {
+  if (n.W != 128 && n.W != 256) {
+    snprintf(why, len, "width %d unsupported (128 or 256)", n.W);
+    return false;
+  }
+  if (n.kind == INRCT_SIREN && n.L < 2) {
+    snprintf(why, len, "SIREN needs at least 2 hidden layers on the tensor-core path");
+    return false;
+  }
+  if (n.kind == INRCT_FFN_RELU && (n.F % 32) != 0) {
+    snprintf(why, len, "n_feat=%d must be a multiple of 32", n.F);
+    return false;
+  }
+  if (n.kind == INRCT_FFN_RELU && 2 * n.F > 2048) {
+    snprintf(why, len, "n_feat=%d too large (<= 1024)", n.F);
+    return false;
+  }
+  return true;
+}
+
+size_t tc_eval_ws_bytes(const Net& n) { return 256 + weights_bytes(n, false) + 256; }
+
+int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image, void* ws, size_t ws_bytes,
+            cudaStream_t st) {
+  Carver c(ws, ws_bytes);
+  int* err = c.take<int>(64);
+  TcWeights w;
+  if (!ws || prep_weights(n, theta, c, false, &w, st) != INRCT_OK || !c.ok) {
+    set_error("inr_eval_grid (bf16): workspace of %zu bytes too small (need %zu)", ws_bytes,
+              tc_eval_ws_bytes(n));
+    return INRCT_ERR_WORKSPACE;
+  }
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  static Maps maps;
+  TileProg P;
+  INRCT_TRY(build_prog(n, w, 0, &P, &maps));
+  P.theta = theta;
+  P.N = N;
+  P.n_grid = npts;
+  P.npts = npts;
+  P.out = image;
+  INRCT_TRY(set_smem_attr((const void*)mlp_tile_kernel, kTileSmem));
+  const int64_t tiles = (npts + kTile - 1) / kTile;
+  const int grid = (int)std::min<int64_t>(tiles, num_sms());
+  mlp_tile_kernel<<<grid, kThreads, kTileSmem, st>>>(maps, P, err);
+  INRCT_CHECK_LAUNCH("mlp tile kernel (eval)");
+  return INRCT_OK;
+}
+
+namespace {
+
+struct TcVjpWs {
+  int* err;
+  TcWeights w;
+  __nv_bfloat16 *E, *Act, *Dlt, *Cos, *Y16c, *Y16o;
+  float* part;
+  int64_t pad;
+  size_t part_floats;
+};
+
+GemmPlan plan_gemm(const Net& n, int64_t K, int64_t* part_floats) {
+  GemmPlan G;
+  memset(&G, 0, sizeof(G));
+  G.K = K;
+  const int64_t nch = (K + 63) / 64;
+  int S = (int)std::min<int64_t>(nch, 16);
+  const int64_t per_ch = (nch + S - 1) / S;
+  S = (int)((nch + per_ch - 1) / per_ch);
+  G.S = S;
+  G.per_split = per_ch * 64;
+  int j = 0;
+  int64_t off = 0;
+  const double mult = n.kind == INRCT_SIREN ? n.omega0 : 1.0;
+  auto add = [&](GemmJob J) {
+    J.mtiles = J.M / 128;
+    J.part_off = off;
+    off += (int64_t)S * J.M * (J.N + 32);
+    G.job[j++] = J;
+  };
+  // map indices: 0 = X of layer l at 3l, Y at 3l + 1, Y16 at 3l + 2 (filled in by the caller)
+  for (int l = 0; l < n.L; ++l) {
+    const int in = n.in_dim[l];
+    if (l == 0 && n.kind == INRCT_SIREN) {
+      GemmJob J{};
+      J.M = n.W;
+      J.N = 0;
+      J.has_ones = 1;
+      J.has_y16 = 1;
+      J.mx = 3 * l;
+      J.my16 = 3 * l + 2;
+      J.offW = n.offW[0];
+      J.ldW = n.d;
+      J.w_src = 1;
+      J.w_cols = n.d;
+      J.offb = n.offb[0];
+      J.mult = mult;
+      add(J);
+      continue;
+    }
+    for (int n0 = 0; n0 < in; n0 += 256) {
+      GemmJob J{};
+      J.M = n.W;
+      J.N = std::min(256, in - n0);
+      J.n0 = n0;
+      J.has_ones = n0 == 0;
+      J.mx = 3 * l;
+      J.my = 3 * l + 1;
+      J.offW = n.offW[l];
+      J.ldW = in;
+      J.w_src = 0;
+      J.w_cols = J.N;
+      J.offb = n0 == 0 ? n.offb[l] : -1;
+      J.mult = mult;
+      add(J);
+    }
+  }
+  {  // output layer: dw_out = sum_points (scale v_i) a_{L-1}
+    GemmJob J{};
+    J.M = n.W;
+    J.N = 0;
+    J.has_y16 = 1;
+    J.mx = 3 * n.L;
+    J.my16 = 3 * n.L + 2;
+    J.offW = n.offW[n.L];
+    J.ldW = 1;  // dw_out[m] is column 0 of row m
+    J.w_src = 1;
+    J.w_cols = 1;
+    J.offb = -1;
+    J.mult = 1.0;
+    add(J);
+  }
+  G.n_jobs = j;
+  int cta = 0;
+  for (int q = 0; q < j; ++q) {
+    G.cta_begin[q] = cta;
+    cta += G.job[q].mtiles * S;
+  }
+  G.cta_begin[j] = cta;
+  *part_floats = off;
+  return G;
+}
+
+size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* out, bool* ok) {
+  Carver c(ws, cap);
+  TcVjpWs w;
+  w.err = c.take<int>(64);
+  // weights
+  w.w.bias = c.take<float>((size_t)n.L * n.W);
+  for (int l = 0; l < kMaxLayers; ++l) w.w.Wb[l] = w.w.WbT[l] = nullptr;
+  for (int l = first_mma_layer(n); l < n.L; ++l) {
+    w.w.Wb[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
+    w.w.WbT[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
+  }
+  const int64_t pad = (chunk + kTile - 1) / kTile * kTile;
+  w.pad = pad;
+  w.E = n.kind == INRCT_FFN_RELU ? c.take<__nv_bfloat16>((size_t)pad * n.K0) : nullptr;
+  w.Act = c.take<__nv_bfloat16>((size_t)pad * n.L * n.W);
+  w.Dlt = c.take<__nv_bfloat16>((size_t)pad * n.L * n.W);
+  w.Cos = n.kind == INRCT_SIREN ? c.take<__nv_bfloat16>((size_t)pad * n.L * n.W) : nullptr;
+  w.Y16c = c.take<__nv_bfloat16>((size_t)16 * pad);
+  w.Y16o = c.take<__nv_bfloat16>((size_t)16 * pad);
+  int64_t pf;
+  plan_gemm(n, chunk, &pf);
+  w.part_floats = (size_t)pf;
+  w.part = c.take<float>((size_t)pf);
+  if (out) *out = w;
+  if (ok) *ok = c.ok;
+  return c.off + 256;
+}
+
+}  // namespace
+
+size_t tc_vjp_ws_bytes(const Net& n, int64_t n_idx) {
+  const int64_t chunk = n_idx < kVjpChunk ? n_idx : kVjpChunk;
+  return vjp_layout(n, chunk, nullptr, 0, nullptr, nullptr);
+}
+
+int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t n_idx, const float* v,
+           double scale, double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const int64_t chunk = n_idx < kVjpChunk ? n_idx : kVjpChunk;
+  TcVjpWs w;
+  bool ok;
+  const size_t need = vjp_layout(n, chunk, ws, ws_bytes, &w, &ok);
+  if (!ws || !ok) {
+    set_error("inr_weighted_vjp (bf16): workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  cudaMemsetAsync(w.err, 0, sizeof(int), st);
+  {  // the weight buffers were carved by vjp_layout; convert theta into them
+    const float sc = n.kind == INRCT_SIREN ? n.omega0 : 1.f;
+    for (int l = first_mma_layer(n); l < n.L; ++l) {
+      const int64_t cnt = (int64_t)n.in_dim[l] * n.out_dim[l];
+      prep_weights_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(theta, n.offW[l], n.offb[l], n.out_dim[l],
+                                                            n.in_dim[l], sc, w.w.Wb[l], w.w.WbT[l],
+                                                            w.w.bias + (int64_t)l * n.W);
+    }
+    INRCT_CHECK_LAUNCH("weight preparation");
+  }
+  static Maps tmaps, gmaps;
+  TileProg P;
+  INRCT_TRY(build_prog(n, w.w, 1, &P, &tmaps));
+  P.theta = theta;
+  P.N = N;
+  int64_t ng = 1;
+  for (int k = 0; k < n.d; ++k) ng *= N;
+  P.n_grid = ng;
+  P.v = v;
+  P.scale = (float)scale;
+  P.E = w.E;
+  P.Act = w.Act;
+  P.Dlt = w.Dlt;
+  P.Cos = w.Cos;
+  P.Y16c = w.Y16c;
+  P.Y16o = w.Y16o;
+  P.npts_pad = w.pad;
+  INRCT_TRY(set_smem_attr((const void*)mlp_tile_kernel, kTileSmem));
+  INRCT_TRY(set_smem_attr((const void*)tn_gemm_kernel, kGemmSmem));
+  for (int64_t c0 = 0; c0 < n_idx; c0 += chunk) {
+    const int64_t np = std::min(chunk, n_idx - c0);
+    P.idx = idx + c0;
+    P.npts = np;
+    cudaMemsetAsync(w.Y16c, 0, sizeof(__nv_bfloat16) * 16 * w.pad, st);
+    cudaMemsetAsync(w.Y16o, 0, sizeof(__nv_bfloat16) * 16 * w.pad, st);
+    const int64_t tiles = (np + kTile - 1) / kTile;
+    mlp_tile_kernel<<<(int)std::min<int64_t>(tiles, num_sms()), kThreads, kTileSmem, st>>>(tmaps, P, w.err);
+    INRCT_CHECK_LAUNCH("mlp tile kernel (vjp)");
+    // split-K weight-gradient GEMMs over this chunk's points
+    int64_t pf;
+    GemmPlan G = plan_gemm(n, np, &pf);
+    for (int l = 0; l < n.L; ++l) {
+      INRCT_TRY(make_map(&gmaps.m[3 * l], w.Dlt + (int64_t)l * w.pad * n.W, n.W, np, 64, 64));
+      if (l == 0 && n.kind == INRCT_SIREN) {
+        INRCT_TRY(make_map(&gmaps.m[3 * l + 2], w.Y16c, w.pad, 16, 64, 16));
+      } else if (l == 0) {
+        INRCT_TRY(make_map(&gmaps.m[3 * l + 1], w.E, n.K0, np, 64, 64));
+      } else {
+        INRCT_TRY(make_map(&gmaps.m[3 * l + 1], w.Act + (int64_t)(l - 1) * w.pad * n.W, n.W, np, 64, 64));
+      }
+    }
+    INRCT_TRY(make_map(&gmaps.m[3 * n.L], w.Act + (int64_t)(n.L - 1) * w.pad * n.W, n.W, np, 64, 64));
+    INRCT_TRY(make_map(&gmaps.m[3 * n.L + 2], w.Y16o, w.pad, 16, 64, 16));
+    tn_gemm_kernel<<<G.cta_begin[G.n_jobs], 192, kGemmSmem, st>>>(gmaps, G, w.part, w.err);
+    INRCT_CHECK_LAUNCH("tn gemm");
+    int maxe = 0;
+    for (int q = 0; q < G.n_jobs; ++q)
+      maxe = std::max(maxe, G.job[q].M * (G.job[q].w_cols + 1));
+    gemm_reduce_kernel<<<dim3(ceil_div(maxe, 256), G.n_jobs), 256, 0, st>>>(G, w.part, c0 > 0, grad_f64);
+    INRCT_CHECK_LAUNCH("gemm reduce");
+    out_bias_grad_kernel<<<1, 1024, 0, st>>>(idx + c0, np, v, ng, (float)scale, c0 > 0,
+                                             grad_f64 + n.offb[n.L]);
+    INRCT_CHECK_LAUNCH("output bias gradient");
+  }
+  if (grad_f32) INRCT_TRY(f64_to_f32(grad_f64, grad_f32, n.p, st));
+  return INRCT_OK;
+}
+
+
+namespace {
+__global__ void gemm_diag_reduce_kernel(const float* __restrict__ part, int S, int M, int ldc,
+                                        float* __restrict__ C) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * ldc) return;
+  double s = 0.0;
+  for (int q = 0; q < S; ++q) s += (double)part[(int64_t)q * M * ldc + e];
+  C[e] = (float)s;
+}
+
+GemmPlan diag_plan(int64_t K, int M, int N, bool y16, int64_t* pf) {
+  GemmPlan G;
+  memset(&G, 0, sizeof(G));
+  G.K = K;
+  const int64_t nch = (K + 63) / 64;
+  int S = (int)std::min<int64_t>(nch, 16);
+  const int64_t per_ch = (nch + S - 1) / S;
+  S = (int)((nch + per_ch - 1) / per_ch);
+  G.S = S;
+  G.per_split = per_ch * 64;
+  GemmJob J{};
+  J.M = M;
+  J.N = N;
+  J.has_ones = 1;
+  J.has_y16 = y16 ? 1 : 0;
+  J.mx = 0;
+  J.my = 1;
+  J.my16 = 2;
+  J.mtiles = M / 128;
+  G.job[0] = J;
+  G.n_jobs = 1;
+  G.cta_begin[0] = 0;
+  G.cta_begin[1] = J.mtiles * S;
+  *pf = (int64_t)S * M * (N + 32);
+  return G;
+}
+}  // namespace
+
+size_t gemm_tn_ws_bytes(int64_t K, int M, int N) {
+  int64_t pf;
+  diag_plan(K, M, N, true, &pf);
+  return 256 + align_up(sizeof(float) * pf, 256) + 256;
+}
+
+int gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int N, float* C, void* ws,
+            size_t ws_bytes, cudaStream_t st) {
+  INRCT_REQUIRE(X && C && K > 0 && K < (int64_t)1 << 31, "gemm_tn: bad X, C or K");
+  INRCT_REQUIRE(M > 0 && M % 128 == 0 && M <= 4096, "gemm_tn: M=%d must be a multiple of 128", M);
+  INRCT_REQUIRE(N >= 0 && N <= 256 && N % 64 == 0 && (N == 0 || Y), "gemm_tn: N=%d must be 0..256, step 64",
+                N);
+  int64_t pf;
+  GemmPlan G = diag_plan(K, M, N, Y16 != nullptr, &pf);
+  Carver c(ws, ws_bytes);
+  int* err = c.take<int>(64);
+  float* part = c.take<float>((size_t)pf);
+  if (!ws || !c.ok) {
+    set_error("gemm_tn: workspace of %zu bytes too small (need %zu)", ws_bytes, gemm_tn_ws_bytes(K, M, N));
+    return INRCT_ERR_WORKSPACE;
+  }
+  static Maps maps;
+  INRCT_TRY(make_map(&maps.m[0], X, M, K, 64, 64));
+  if (N > 0) INRCT_TRY(make_map(&maps.m[1], Y, N, K, 64, 64));
+  if (Y16) INRCT_TRY(make_map(&maps.m[2], Y16, K, 16, 64, 16));
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  INRCT_TRY(set_smem_attr((const void*)tn_gemm_kernel, kGemmSmem));
+  tn_gemm_kernel<<<G.cta_begin[1], 192, kGemmSmem, st>>>(maps, G, part, err);
+  INRCT_CHECK_LAUNCH("tn gemm (diagnostic)");
+  const int ldc = N + 32;
+  gemm_diag_reduce_kernel<<<ceil_div((int64_t)M * ldc, 256), 256, 0, st>>>(part, G.S, M, ldc, C);
+  INRCT_CHECK_LAUNCH("tn gemm reduce (diagnostic)");
+  return INRCT_OK;
+}
+
+}  // namespace inrct

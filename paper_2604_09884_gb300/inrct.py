@@ -88,6 +88,8 @@ def lib():
         "inr_weighted_vjp": ([m, _P, gr, _P, _I64, _P, ctypes.c_double, _P, _P, _P, _SZ, _P],
                              ctypes.c_int),
         "inrct_step_ws_bytes": ([g, gr, m, _I64], _SZ),
+        "inrct_gemm_tn_ws_bytes": ([_I64, ctypes.c_int, ctypes.c_int], _SZ),
+        "inrct_gemm_tn": ([_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, _P, _P, _SZ, _P], ctypes.c_int),
         "grad_step": ([g, gr, m, ctypes.c_int, _P, _P, _P, _I64, ctypes.c_double,
                        ctypes.POINTER(Adam), _P, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
     }
@@ -258,6 +260,19 @@ def grad_step(g: synth.GeomSpec, mlp: MlpHandle, theta: torch.Tensor, y: torch.T
                        idx.numel(), float(scale), ctypes.byref(adam) if adam is not None else None,
                        _ptr(m), _ptr(s), _ptr(loss_out), _ptr(grad_out), _ptr(ws), ws.numel(),
                        _stream(stream)))
+
+
+def gemm_tn(X: torch.Tensor, Y: torch.Tensor | None, Y16: torch.Tensor | None, stream=None):
+    """Diagnostic: [X^T Y | X^T 1 (16 cols) | X^T Y16^T] from the weight-gradient GEMM (BF16 in)."""
+    L = lib()
+    K, M = X.shape
+    N = Y.shape[1] if Y is not None else 0
+    C = torch.empty(M, N + 32, dtype=torch.float32, device=X.device)
+    nb = L.inrct_gemm_tn_ws_bytes(K, M, N)
+    ws = _ws(nb, X.device)
+    _check(L.inrct_gemm_tn(_ptr(X, torch.bfloat16), _ptr(Y, torch.bfloat16), _ptr(Y16, torch.bfloat16),
+                           K, M, N, _ptr(C), _ptr(ws), nb, _stream(stream)))
+    return C
 
 
 def adam(lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, t=1) -> Adam:

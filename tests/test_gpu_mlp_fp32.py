@@ -39,7 +39,7 @@ def kink_free(oa, theta, X, tau=1e-4):
     the decision is unique."""
     if oa.kind != "ffn":
         return np.ones(len(X), bool)
-    _, _, zs = O.forward(oa, np.asarray(theta, np.float64), X, keep=True)
+    _, _, zs, _ = O.forward(oa, np.asarray(theta, np.float64), X, keep=True)
     ok = np.ones(len(X), bool)
     for z in zs[:-1]:
         ok &= (np.abs(z) >= tau * np.sqrt((z ** 2).mean())).all(axis=1)

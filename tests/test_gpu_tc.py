@@ -1,0 +1,99 @@
+"""GPU checks of the BF16 tcgen05 path: the weight-gradient GEMM against a library
+matmul on the same BF16 inputs, and the fused MLP tile engine (grid evaluation,
+weighted VJP) against the FP64 oracle (bar: BF16 grad within 1e-2 relative L2
+with cosine >= 0.999)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2604_09884_gb300 import inrct, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cos(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def cuda(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("K,M,N,y16", [(64, 128, 64, True), (1000, 128, 256, True),
+                                       (70000, 256, 128, False), (4160, 256, 0, True),
+                                       (8, 128, 192, True)])
+def test_gemm_tn_matches_matmul(K, M, N, y16):
+    g = torch.Generator(device="cuda").manual_seed(K + M + N)
+    X = torch.randn(K, M, device="cuda", generator=g).bfloat16()
+    Y = torch.randn(K, N, device="cuda", generator=g).bfloat16() if N else None
+    Y16 = torch.randn(16, K, device="cuda", generator=g).bfloat16() if y16 else None
+    C = inrct.gemm_tn(X, Y, Y16).double()
+    Xd = X.double()
+    if N:
+        assert rel(C[:, :N].cpu(), (Xd.T @ Y.double()).cpu()) <= 1e-5
+    assert rel(C[:, N].cpu(), Xd.sum(0).cpu()) <= 1e-5
+    if y16:
+        assert rel(C[:, N + 16:].cpu(), (Xd.T @ Y16.double().T).cpu()) <= 1e-5
+    else:
+        assert float(C[:, N + 16:].abs().max()) == 0.0
+
+
+def arch_pair(spec, seed=0):
+    B = synth.fourier_matrix(spec.n_feat, spec.d, spec.sigma, seed) if spec.kind == "ffn" else None
+    B32 = B.astype(np.float32) if B is not None else None
+    oa = O.Arch(spec.kind, spec.d, spec.width, spec.n_hidden, spec.n_feat,
+                B32.astype(np.float64) if B32 is not None else None, spec.omega0)
+    return oa, B32
+
+
+ARCHS = [
+    synth.ArchSpec("siren", 2, 256, 5, omega0=30.0),        # 512^2 fan workload's network
+    synth.ArchSpec("ffn", 3, 256, 4, n_feat=256, sigma=8.0),  # 256^3 cone workload's network
+    synth.ArchSpec("siren", 2, 128, 3, omega0=30.0),        # batched workload's network
+    synth.ArchSpec("ffn", 2, 128, 2, n_feat=32, sigma=4.0),
+]
+
+
+@pytest.mark.parametrize("spec", ARCHS, ids=lambda a: f"{a.kind}{a.d}d_{a.width}x{a.n_hidden}")
+def test_eval_grid_bf16_matches_oracle(spec):
+    N = 67 if spec.d == 2 else 21          # ragged: the grid is not a multiple of the tile
+    oa, B32 = arch_pair(spec, 1)
+    theta = synth.init_theta(spec, 2).astype(np.float32)
+    h = inrct.mlp_desc(spec, inrct.BF16, B32)
+    img = inrct.inr_eval_grid(h, cuda(theta), N).cpu().numpy()
+    want = O.forward(oa, theta.astype(np.float64), O.grid_coords(spec.d, N))
+    err = rel(img, want)
+    assert err <= 2e-2, err
+
+
+@pytest.mark.parametrize("spec", ARCHS, ids=lambda a: f"{a.kind}{a.d}d_{a.width}x{a.n_hidden}")
+def test_weighted_vjp_bf16_matches_oracle(spec):
+    N = 67 if spec.d == 2 else 21
+    n = N ** spec.d
+    oa, B32 = arch_pair(spec, 3)
+    theta = synth.init_theta(spec, 4).astype(np.float32)
+    v = np.random.default_rng(5).normal(size=n).astype(np.float32)
+    idx = np.concatenate([synth.index_set(n, 1337, 6), [5, 5, 7]]).astype(np.int32)
+    scale = n / idx.size
+    h = inrct.mlp_desc(spec, inrct.BF16, B32)
+    g64, g32 = inrct.inr_weighted_vjp(h, cuda(theta), N, cuda(idx, torch.int32), cuda(v), scale,
+                                      want_f32=True)
+    # ReLU masks are decided at the kernel's precision (BF16 operands) on both sides
+    want = O.vjp(oa, theta.astype(np.float64), O.grid_coords(spec.d, N, idx),
+                 scale * v.astype(np.float64)[idx], decide="bf16",
+                 X32=O.grid_coords_fp32(spec.d, N, idx))
+    got = g64.cpu().numpy()
+    assert rel(got, want) <= 1e-2, rel(got, want)
+    assert cos(got, want) >= 0.999
+    assert rel(g32.cpu().numpy(), got) <= 1e-6
