@@ -1,0 +1,387 @@
+"""Benchmark: INR-CT stochastic gradient steps per second on one GB300 (or N replicas).
+
+One step is Algorithm 1 of the paper followed by an Adam update, through the
+library's grad_step: grid evaluation of the INR (tcgen05 BF16 MLP), Joseph
+projection with the LS loss epilogue, exact adjoint backprojection, the fused
+residual-weighted VJP at |I| sampled points, weight-gradient GEMM, FP64
+reduction, Adam.  Workload (default): 512^2 fan beam, 90 views over 360 deg,
+729 curved bins, SOD/SDD 1000/1500, SIREN 5 x 256 (omega0 = 30), |I| = n/4,
+synthetic 20-ellipse phantom with 1 % noise.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+Under torchrun every rank runs an independent replica (weak scaling, no
+data-path collective); the timed region is bracketed by a barrier and the
+slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "INR-CT grad steps/s, proj+backproj GRays/s; BF16 vs FP32 at <=1e-2 grad err"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="fan2d_512_siren256")
+    p.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    p.add_argument("--frac", type=float, default=None, help="|I|/n (default: the workload's)")
+    p.add_argument("--loss", default="ls", choices=["ls", "fls"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=200)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(w, frac: float, seed: int = 0) -> float:
+    """Seconds of one oracle sample covering `frac` of a full step: forward on
+    frac*n grid points, P and P^T on frac*V views, the estimator on frac*|I|
+    points, Adam.  (Every part of the oracle step scales linearly in these.)"""
+    import oracle as O
+    from paper_2604_09884_gb300 import synth
+    g, a = w.geom, w.arch
+    Vs = max(1, int(round(g.V * frac)))
+    og = O.Geometry(g.kind, g.N, Vs, g.A, g.B, g.du, g.dv, g.sod, g.sdd, g.angle0,
+                    g.span * Vs / g.V)
+    B = synth.fourier_matrix(a.n_feat, a.d, a.sigma, seed) if a.kind == "ffn" else None
+    oa = O.Arch(a.kind, a.d, a.width, a.n_hidden, a.n_feat, B, a.omega0)
+    theta = synth.init_theta(a, seed)
+    n_pts = max(1, int(g.n * frac))
+    n_I = max(1, int(w.batch * frac))
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    f = O.forward(oa, theta, O.grid_coords(g.d, g.N, np.arange(n_pts)))
+    img = np.zeros(g.n)
+    img[:n_pts] = f
+    z = O.project(og, img)
+    L, r = O.ls_loss(z, np.zeros_like(z))
+    v = O.backproject(og, r)
+    I = rng.choice(g.n, n_I, replace=False)
+    ghat = O.vjp(oa, theta, O.grid_coords(g.d, g.N, I), (g.n / w.batch) * v[I])
+    st = O.AdamState(np.zeros_like(theta), np.zeros_like(theta))
+    O.adam_step(theta, ghat, st, lr=w.lr)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(w, budget_s: float, frac: float):
+    """(steps/s, samples timed, frac) of the oracle within about budget_s seconds."""
+    oracle_sample(w, min(frac, 1 / 64))       # warm-up (builds the C projector)
+    total, k = 0.0, 0
+    while total < budget_s or k == 0:
+        total += oracle_sample(w, frac, seed=k)
+        k += 1
+    per_step = total / k / frac
+    return 1.0 / per_step, k
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    # each step is one oracle sample of a fraction of the step, sized so that the
+    # whole --steps run takes about two minutes
+    est = oracle_sample(w, 1 / 64) * 64            # also warms the C projector up
+    frac = min(1 / 16, max(1 / 512, 120.0 / (max(args.steps, 1) * est)))
+    for _ in range(max(1, min(args.warmup, 2))):
+        oracle_sample(w, frac)
+    total = 0.0
+    steps = max(1, args.steps)
+    for k in range(steps):
+        total += oracle_sample(w, frac, seed=k)
+    value = steps * frac / total
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "note": w.note, "batch": w.batch},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} samples of {frac:.4g} of a step each (forward "
+                                       "on that fraction of the grid, P/P^T on that fraction of "
+                                       "the views, VJP on that fraction of |I|), full-step time "
+                                       "extrapolated linearly"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def mlp_flops(a, pts, vjp):
+    """Tensor-core FLOPs of the MMA stages for `pts` points."""
+    shapes = a.layer_shapes()
+    first = 1 if a.kind == "siren" else 0
+    fwd = sum(o * i for o, i in shapes[first:-1])
+    if not vjp:
+        return 2.0 * pts * fwd
+    bwd = sum(o * i for o, i in shapes[1:-1])
+    return 2.0 * pts * (fwd + bwd)
+
+
+def dw_flops(a, pts):
+    shapes = a.layer_shapes()
+    return 2.0 * pts * sum(o * i for o, i in shapes[:-1] if i >= 64)
+
+
+def main():
+    args = parse()
+    import torch
+
+    from paper_2604_09884_gb300 import inrct, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = synth.workloads()
+    if args.workload not in wl:
+        raise SystemExit(f"unknown workload {args.workload}; choose from {sorted(wl)}")
+    w = wl[args.workload]
+    if args.frac is not None:
+        w.batch = max(1, int(round(args.frac * w.geom.n)))
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g, a = w.geom, w.arch
+    seed = w.seed + 1000 * rank                      # every replica its own problem
+    # ---- synthetic problem, resident on the device ----
+    x_true = torch.tensor(synth.phantom(g.d, g.N, w.n_shapes, seed).reshape(-1), dtype=torch.float32,
+                          device=dev)
+    y_clean = inrct.project(g, x_true)
+    y = torch.tensor(synth.noisy(y_clean.cpu().numpy(), w.noise, seed + 1), device=dev)
+    B = synth.fourier_matrix(a.n_feat, a.d, a.sigma, seed + 2) if a.kind == "ffn" else None
+    prec = inrct.BF16 if args.prec == "bf16" else inrct.FP32
+    mlp = inrct.mlp_desc(a, prec, B, device=dev)
+    theta = torch.tensor(synth.init_theta(a, seed + 3), dtype=torch.float32, device=dev)
+    m = torch.zeros_like(theta)
+    s = torch.zeros_like(theta)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    n_idx = w.batch
+    scale = g.n / n_idx
+    ws = torch.empty(inrct.step_ws_bytes(g, mlp, n_idx), dtype=torch.uint8, device=dev)
+    loss_kind = inrct.LOSS_FLS if args.loss == "fls" else inrct.LOSS_LS
+    # index sets: a fresh uniform subset per step (drawn on the host, staged in HBM)
+    n_sets = 16
+    idx_host = [torch.from_numpy(synth.index_set(g.n, n_idx, seed + 10 + k)).pin_memory()
+                for k in range(n_sets)]
+    idx_dev = [t.to(dev) for t in idx_host]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(t, idx):
+        inrct.grad_step(g, mlp, theta, y, idx, scale, inrct.adam(lr=w.lr, t=t), m, s, loss, None,
+                        ws, loss_kind)
+
+    t = 0
+    for _ in range(args.warmup):
+        t += 1
+        step(t, idx_dev[t % n_sets])
+    torch.cuda.synchronize()
+
+    # ---- timed region (device): inputs resident, L2 flushed between steps (untimed) ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    prof_steps = min(args.steps, 256)
+    inrct.profile_begin(prof_steps)
+    l0 = inrct.launch_count()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            t += 1
+            starts[k].record(stream)
+            step(t, idx_dev[t % n_sets])
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    launches = inrct.launch_count() - l0
+    stages, nprof = inrct.profile_end()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [st.elapsed_time(en) for st, en in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- end to end through the public API, host buffers, copies inside the timed region ----
+    loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    idx_stage = torch.empty_like(idx_dev[0])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        t += 1
+        idx_stage.copy_(idx_host[t % n_sets], non_blocking=True)
+        step(t, idx_stage)
+        loss_host.copy_(loss, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * e2e_steps / e2e_s
+
+    # ---- kernel rates from the stage profile (live, inside the timed steps) ----
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    peak_src = "measured" if peaks else "fallback"
+    per = {k: v / max(nprof, 1) for k, v in stages.items()}
+    kernels = {}
+    f_eval = mlp_flops(a, g.n, vjp=False)
+    f_vjp = mlp_flops(a, n_idx, vjp=True)
+    f_dw = dw_flops(a, n_idx)
+    if per["eval_mlp_kernel"] > 0:
+        kernels["eval_mlp_kernel"] = {"ms": per["eval_mlp_kernel"],
+                                      "TFLOP/s": f_eval / per["eval_mlp_kernel"] / 1e9}
+    if per["vjp_mlp_kernel"] > 0:
+        kernels["vjp_mlp_kernel"] = {"ms": per["vjp_mlp_kernel"],
+                                     "TFLOP/s": f_vjp / per["vjp_mlp_kernel"] / 1e9}
+    if per["vjp_dw_gemm_reduce"] > 0:
+        kernels["vjp_dw_gemm_reduce"] = {"ms": per["vjp_dw_gemm_reduce"],
+                                         "TFLOP/s": f_dw / per["vjp_dw_gemm_reduce"] / 1e9}
+    # projector: compulsory bytes = image once + sinogram out (+ y in, residual out)
+    proj_bytes = 4.0 * (g.n + 3 * g.m)
+    back_bytes = 4.0 * (g.n + g.m)
+    kernels["project_loss"] = {"ms": per["project_loss"],
+                               "GB/s": proj_bytes / per["project_loss"] / 1e6,
+                               "GRays/s": g.m / per["project_loss"] / 1e6}
+    kernels["backproject"] = {"ms": per["backproject"],
+                              "GB/s": back_bytes / per["backproject"] / 1e6,
+                              "GRays/s": g.m / per["backproject"] / 1e6}
+    pair_ms = per["project_loss"] + per["backproject"]
+    dominant = max(("eval_mlp_kernel", "vjp_mlp_kernel"), key=lambda k: per[k])
+    flops = f_eval if dominant == "eval_mlp_kernel" else f_vjp
+    achieved = flops / per[dominant] / 1e9
+    roofline = {"kernel": "mlp_tile_kernel (" + ("grid evaluation" if dominant == "eval_mlp_kernel"
+                                                 else "VJP") + ")",
+                "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": achieved / bf16_peak, "peak_source": f"{peak_src} (bf16 burst)",
+                "traffic": None}
+    if args.prec != "bf16":
+        roofline = {"kernel": "simt_fwd_kernel", "bound": "alu", "achieved": achieved, "peak": None,
+                    "unit": "TFLOP/s", "frac": None, "traffic": None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, k = oracle_rate(w, budget_s=15.0, frac=1 / 16)
+        cpu = {"value": rate, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{k} samples of 1/16 of a step each (forward on n/16 points, P/P^T on "
+                         "V/16 views, VJP on |I|/16 points), full-step time extrapolated linearly"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
+                "config": {"workload": w.name, "note": w.note, "batch": n_idx,
+                           "loss": args.loss, "precision": args.prec,
+                           "l2": "flushed between timed steps (untimed 258 MB write)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "gray_s_proj_backproj": g.m / pair_ms / 1e6 if pair_ms > 0 else None,
+                "stage_ms": per, "kernels": kernels, "roofline": roofline,
+                "e2e": {"value": e2e_value, "unit": "steps/s",
+                        "h2d_bytes_per_step": int(idx_host[0].numel() * 4), "d2h_bytes_per_step": 8},
+                "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": cpu,
+                "loss_last": float(loss_host.item())}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

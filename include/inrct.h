@@ -212,6 +212,26 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
               double* grad_out, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Instrumentation (host-side, not part of the method) */
+
+/* Number of kernel launches this library has issued since it was loaded. */
+long long inrct_launch_count(void);
+
+/*
+ * Stage profile of grad_step: while active, grad_step records a CUDA event on
+ * its stream at each stage boundary.  inrct_profile_end synchronises the
+ * device and writes, for stage k (0-based), the summed milliseconds over the
+ * recorded steps between consecutive marks:
+ *   0 weight preparation of the evaluation, 1 grid-evaluation MLP kernel,
+ *   2 projection + loss, 3 backprojection (+ ramp filter), 4 VJP preparation,
+ *   5 VJP MLP kernel, 6 weight-gradient GEMM and reductions, 7 Adam.
+ * stage_ms: host array of n_stages (<= 8) doubles; steps_out (host, may be
+ * NULL) receives the number of steps recorded (at most max_steps).
+ */
+int inrct_profile_begin(int max_steps);
+int inrct_profile_end(double* stage_ms, int n_stages, int* steps_out);
+
+/* ------------------------------------------------------------------------ */
 /*
  * inrct_gemm_tn -- the split-K tensor-core GEMM that forms the weight
  * gradients of the BF16 path (dW_l = sum over points of delta_l a_{l-1}^T,

@@ -4,6 +4,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
+#include <vector>
+
 #include "filter.cuh"
 #include "mlp.cuh"
 #include "projector.cuh"
@@ -19,6 +23,32 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 void clear_error() { g_err[0] = 0; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Stage profile of grad_step: one event per mark per step, recorded on the
+// step's stream while active.
+struct Profile {
+  std::mutex mu;
+  bool on = false;
+  int max_steps = 0, step = -1;
+  std::vector<cudaEvent_t> ev;  // [max_steps][kNumMarks]
+  std::vector<unsigned char> hit;
+};
+static Profile g_prof;
+
+void prof_mark(int mark, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (!g_prof.on || g_prof.step < 0 || g_prof.step >= g_prof.max_steps) return;
+  const size_t i = (size_t)g_prof.step * kNumMarks + mark;
+  if (cudaEventRecord(g_prof.ev[i], st) == cudaSuccess) g_prof.hit[i] = 1;
+}
+
+static void prof_step_begin() {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (g_prof.on) ++g_prof.step;
+}
 
 static bool use_tc(const inrct_mlp* mlp) { return mlp->prec == INRCT_BF16; }
 
@@ -200,10 +230,13 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
     set_error("grad_step: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
     return INRCT_ERR_WORKSPACE;
   }
+  prof_step_begin();
+  prof_mark(kMarkStart, stream);
   // Algorithm 1, step 1: z = P E{f_theta} (no gradient tracking); loss epilogue
   INRCT_TRY(eval_dispatch(mlp, n, theta, grid->N, grid_points(grid), w.x, w.stage, w.stage_bytes,
                           stream));
   INRCT_TRY(project_impl(geom, grid, w.x, w.z, y, w.r, w.loss, w.stage, w.stage_bytes, stream));
+  prof_mark(kMarkProjDone, stream);
   // Algorithm 1, step 2: v = P^T dL/dz  (LS: z - y; FLS: F (z - y), Sec. 3)
   if (loss == INRCT_LOSS_FLS) {
     INRCT_TRY(ramp_filter_impl(geom, grid, w.r, w.z, w.loss, w.stage, w.stage_bytes, stream));
@@ -211,10 +244,12 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
   } else {
     INRCT_TRY(backproject_impl(geom, grid, w.r, w.v, w.stage, w.stage_bytes, stream));
   }
+  prof_mark(kMarkBackDone, stream);
   // steps 3-5: the index set is the caller's; gradient of the virtual loss (Eq. 3)
   double* g = grad_out ? grad_out : w.g;
   INRCT_TRY(vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, w.v, scale, g, nullptr, w.stage,
                          w.stage_bytes, stream));
+  prof_mark(kMarkVjpDone, stream);
   if (loss_out) {
     cudaError_t e = cudaMemcpyAsync(loss_out, w.loss, sizeof(double), cudaMemcpyDeviceToDevice, stream);
     if (e != cudaSuccess) {
@@ -223,6 +258,57 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
     }
   }
   if (adam) INRCT_TRY(adam_update(theta, g, adam_m, adam_s, n.p, adam, stream));
+  prof_mark(kMarkEnd, stream);
+  return INRCT_OK;
+}
+
+long long inrct_launch_count(void) { return g_launches.load(); }
+
+int inrct_profile_begin(int max_steps) {
+  clear_error();
+  INRCT_REQUIRE(max_steps > 0 && max_steps <= 4096, "max_steps=%d out of range", max_steps);
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  INRCT_REQUIRE(!g_prof.on, "a profile is already active");
+  g_prof.ev.assign((size_t)max_steps * kNumMarks, nullptr);
+  g_prof.hit.assign((size_t)max_steps * kNumMarks, 0);
+  for (auto& e : g_prof.ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      set_error("cudaEventCreate failed");
+      return INRCT_ERR_CUDA;
+    }
+  }
+  g_prof.max_steps = max_steps;
+  g_prof.step = -1;
+  g_prof.on = true;
+  return INRCT_OK;
+}
+
+int inrct_profile_end(double* stage_ms, int n_stages, int* steps_out) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  INRCT_REQUIRE(g_prof.on, "no active profile");
+  g_prof.on = false;
+  cudaDeviceSynchronize();
+  const int steps = std::min(g_prof.step + 1, g_prof.max_steps);
+  for (int k = 0; k < n_stages; ++k) stage_ms[k] = 0.0;
+  // stage k = time from the previous recorded mark to mark k+1
+  for (int s = 0; s < steps; ++s) {
+    int prev = -1;
+    for (int m = 0; m < kNumMarks; ++m) {
+      const size_t i = (size_t)s * kNumMarks + m;
+      if (!g_prof.hit[i]) continue;
+      if (prev >= 0 && m - 1 < n_stages) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g_prof.ev[(size_t)s * kNumMarks + prev], g_prof.ev[i]) == cudaSuccess)
+          stage_ms[m - 1] += ms;
+      }
+      prev = m;
+    }
+  }
+  for (auto& e : g_prof.ev) cudaEventDestroy(e);
+  g_prof.ev.clear();
+  g_prof.hit.clear();
+  if (steps_out) *steps_out = steps;
   return INRCT_OK;
 }
 

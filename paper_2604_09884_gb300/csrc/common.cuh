@@ -15,6 +15,25 @@ namespace inrct {
 void set_error(const char* fmt, ...);
 void clear_error();
 
+// Kernel launches issued by this library (all threads).
+void count_launch();
+
+// Optional stage marks of grad_step (a CUDA event recorded at each mark while a
+// profile is active; see inrct_profile_begin / inrct_profile_end).
+enum ProfMark {
+  kMarkStart = 0,    // grad_step entry
+  kMarkEvalKernel,   // before the grid-evaluation MLP kernel
+  kMarkEvalDone,     // after it
+  kMarkProjDone,     // after projection + loss
+  kMarkBackDone,     // after backprojection (and the ramp filter)
+  kMarkVjpKernel,    // before the VJP MLP kernel
+  kMarkVjpKernelDone,
+  kMarkVjpDone,      // after the weight-gradient GEMM and reductions
+  kMarkEnd,          // after Adam
+  kNumMarks
+};
+void prof_mark(int mark, cudaStream_t st);
+
 #define INRCT_REQUIRE(cond, ...)            \
   do {                                      \
     if (!(cond)) {                          \
@@ -23,8 +42,10 @@ void clear_error();
     }                                       \
   } while (0)
 
+// Checks the launch just issued and counts it (inrct_launch_count()).
 #define INRCT_CHECK_LAUNCH(what)                                                   \
   do {                                                                             \
+    ::inrct::count_launch();                                                       \
     cudaError_t e_ = cudaGetLastError();                                           \
     if (e_ != cudaSuccess) {                                                       \
       ::inrct::set_error("%s: %s", what, cudaGetErrorString(e_));                  \

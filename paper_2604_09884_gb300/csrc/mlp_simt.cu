@@ -345,8 +345,8 @@ int prep_wt(const Net& n, const float* theta, float* Wt, LayerOffs* lo, cudaStre
     const int64_t cnt = (int64_t)n.in_dim[l] * n.out_dim[l];
     transpose_w_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(theta, n.offW[l], n.out_dim[l],
                                                           n.in_dim[l], Wt + lo->Wt[l]);
+    INRCT_CHECK_LAUNCH("weight transpose");
   }
-  INRCT_CHECK_LAUNCH("weight transpose");
   return INRCT_OK;
 }
 
@@ -386,9 +386,11 @@ int simt_eval(const Net& n, const float* theta, int N, int64_t npts, float* imag
   float* Wt = static_cast<float*>(ws);
   INRCT_TRY(prep_wt(n, theta, Wt, &lo, st));
   INRCT_TRY(set_fwd_smem(n));
+  prof_mark(kMarkEvalKernel, st);
   simt_fwd_kernel<<<ceil_div(npts, TP), n.W, fwd_smem(n), st>>>(dev_of(n, N), lo, theta, Wt, npts,
                                                                nullptr, image, nullptr, nullptr);
   INRCT_CHECK_LAUNCH("simt forward");
+  prof_mark(kMarkEvalDone, st);
   return INRCT_OK;
 }
 
@@ -416,11 +418,13 @@ int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_
     const int64_t np = std::min(chunk, n_idx - c0);
     const int32_t* id = idx + c0;
     const unsigned nb = ceil_div(np, TP);
+    if (c0 == 0) prof_mark(kMarkVjpKernel, st);
     simt_fwd_kernel<<<nb, n.W, fwd_smem(n), st>>>(nd, lo, theta, w.Wt, np, id, nullptr, w.E, w.Z);
     INRCT_CHECK_LAUNCH("simt vjp forward");
     simt_bwd_kernel<<<nb, n.W, sizeof(float) * TP * n.W, st>>>(nd, lo, theta, np, id, v,
                                                                 (float)scale, w.Z, w.D, w.dout);
     INRCT_CHECK_LAUNCH("simt vjp backward");
+    if (c0 == 0) prof_mark(kMarkVjpKernelDone, st);
     const int S = splits_for(np);
     const int64_t per = (np + S - 1) / S;
     for (int l = 0; l <= n.L; ++l) {

@@ -94,7 +94,7 @@ int make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, u
   return INRCT_OK;
 }
 
-struct alignas(64) Maps {
+struct Maps {
   CUtensorMap m[kMaxJobs];
 };
 
@@ -375,14 +375,6 @@ __device__ __forceinline__ void load_row32_bf16(const __nv_bfloat16* src, float*
   }
 }
 
-// Phase B_f . x of Fourier feature f, rounded operation by operation in a fixed
-// order (products, then sums left to right), so that the value is reproducible.
-__device__ __forceinline__ float feat_phase(const float* Bf, const float* x, int d) {
-  float ph = __fadd_rn(__fmul_rn(Bf[0], x[0]), __fmul_rn(Bf[1], x[1]));
-  if (d == 3) ph = __fadd_rn(ph, __fmul_rn(Bf[2], x[2]));
-  return ph;
-}
-
 // cos or sin of 2 pi ph: ph is reduced to t in [-1/2, 1/2] exactly, then
 // sincospif(2t) (accurate to about an FP32 ulp).  The features feed ReLU mask
 // decisions downstream, so they are computed accurately rather than with the
@@ -394,20 +386,31 @@ __device__ __forceinline__ float four_feat(float ph, bool want_sin) {
   return want_sin ? s : c;
 }
 
+// Parameters staged in shared memory after the panels and the ring (FP32):
+// bias [L][W] (omega0 folded for SIREN), w_out [W], and the first-layer table:
+// SIREN float4 {w'_0, w'_1, w'_2, b'} per output, FFN float4 {B_0, B_1, B_2, 0} per feature.
+__host__ __device__ inline size_t param_floats(int L, int W, int F, int kind) {
+  return (size_t)L * W + W + 4 * (size_t)(kind == INRCT_SIREN ? W : F);
+}
+
+template <int MODE, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_tile_kernel(const __grid_constant__ Maps maps, const __grid_constant__ TileProg P,
                     int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t dsm[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  const int W = P.W;
   uint8_t* apan = smem;                      // 4 x 16 KB input panels
   uint8_t* ring = smem + 4 * kPanelBytes;    // kRing x (W x 128 B) weight chunks
+  float* bias_s = reinterpret_cast<float*>(ring + (size_t)kRing * W * 128);
+  float* wout_s = bias_s + (size_t)P.L * W;
+  float4* first_s = reinterpret_cast<float4*>(wout_s + W);
   __shared__ uint64_t w_full[kRing], w_empty[kRing], a_full[4], a_empty[4], acc_full[2], acc_empty[2],
       dot_bar, drain_bar;
   __shared__ float dotp[2][kTile];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int W = P.W;
   const uint32_t chunk_bytes = (uint32_t)W * 128;
   const int64_t n_tiles = (P.npts + kTile - 1) / kTile;
 
@@ -428,6 +431,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(&drain_bar, 1);
     abort_flag = 0;
     fence_mbar_init();
+  }
+  // stage the small parameters
+  for (int i = threadIdx.x; i < P.L * W; i += blockDim.x) bias_s[i] = P.bias[i];
+  for (int i = threadIdx.x; i < W; i += blockDim.x) wout_s[i] = P.theta[P.offWout + i];
+  if (KIND == INRCT_SIREN) {
+    for (int o = threadIdx.x; o < W; o += blockDim.x) {
+      const float* w1 = P.theta + P.offW0 + (int64_t)o * P.d;
+      first_s[o] = make_float4(P.omega0 * w1[0], P.omega0 * w1[1], P.d == 3 ? P.omega0 * w1[2] : 0.f,
+                               P.omega0 * P.theta[P.offb0 + o]);
+    }
+  } else {
+    for (int f = threadIdx.x; f < P.F; f += blockDim.x) {
+      const float* bf = P.B + (int64_t)f * P.d;
+      first_s[f] = make_float4(bf[0], bf[1], P.d == 3 ? bf[2] : 0.f, 0.f);
+    }
   }
   if (warp == 0) tmem_alloc(&tmem_base, 2 * W);
   tc_fence_before();
@@ -458,21 +476,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 9) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      uint32_t slot = 0, wf = 0, aep[2] = {1, 1}, acc_ctr = 0;
-      uint32_t ap[4] = {0, 0, 0, 0};
+      // phase parities of the barriers, one bit per slot
+      uint32_t slot = 0, wf = 0, aep = 3u, acc_ctr = 0, ap = 0u;
       const uint32_t idesc = idesc_bf16(128, W, false, false);
       bool issued = false;
       for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         for (int s = 0; s < P.n_stages; ++s) {
           const uint32_t b = acc_ctr & 1;
-          if (!mbar_wait(&acc_empty[b], aep[b], &abort_flag, err, 301)) goto mma_done;
-          aep[b] ^= 1;
+          if (!mbar_wait(&acc_empty[b], (aep >> b) & 1u, &abort_flag, err, 301)) goto mma_done;
+          aep ^= 1u << b;
           tc_fence_after();
           const uint32_t dcol = tmem + b * W;
           for (int c = 0; c < P.st_panels[s]; ++c) {
             const int as = c & 3;
-            if (!mbar_wait(&a_full[as], ap[as], &abort_flag, err, 302)) goto mma_done;
-            ap[as] ^= 1;
+            if (!mbar_wait(&a_full[as], (ap >> as) & 1u, &abort_flag, err, 302)) goto mma_done;
+            ap ^= 1u << as;
             if (!mbar_wait(&w_full[slot], wf, &abort_flag, err, 303)) goto mma_done;
             tc_fence_after();
             const uint32_t abase = smem_u32(apan + as * kPanelBytes);
@@ -506,8 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3, g = warp >> 2;
     const int r = q * 32 + lane;                 // row of the tile = TMEM lane
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    uint32_t ae[4] = {1, 1, 1, 1}, af[2] = {0, 0}, dotph = 0, acc_ctr = 0;
-    const float* wout = P.theta + P.offWout;
+    uint32_t ae = 0xFu, af = 0u, dotph = 0, acc_ctr = 0;  // phase parities, one bit per slot
     const float bout = P.theta[P.offbout];
     float v[32];
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -518,42 +535,46 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!in_range) gi = 0;
       float x[3];
       point_coords(gi, P.N, P.d, x);
-      const float sv = (P.mode == 1 && valid && in_range) ? P.scale * P.v[gi] : 0.f;
+      const float sv = (MODE == 1 && valid && in_range) ? P.scale * P.v[gi] : 0.f;
       const int64_t prow = t * kTile + r;        // scratch row (rows are padded to the tile)
       // ---- first stage input ----
       for (int c = 0; c < P.in_panels; ++c) {
         const int col0 = 64 * c + 32 * g;
-        if (P.kind == INRCT_FFN_RELU) {
+        if (KIND == INRCT_FFN_RELU) {
           const bool is_sin = col0 >= P.F;
           const int f0 = is_sin ? col0 - P.F : col0;
-#pragma unroll 4
+#pragma unroll
           for (int i = 0; i < 32; ++i) {
-            v[i] = four_feat(feat_phase(P.B + (int64_t)(f0 + i) * P.d, x, P.d), is_sin);
+            const float4 bf = first_s[f0 + i];
+            float ph = __fadd_rn(__fmul_rn(bf.x, x[0]), __fmul_rn(bf.y, x[1]));
+            if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, x[2]));
+            v[i] = four_feat(ph, is_sin);
           }
-          if (P.mode == 1) store_row32_bf16(P.E + prow * (2 * P.F) + col0, v);
+          if (MODE == 1) store_row32_bf16(P.E + prow * (2 * P.F) + col0, v);
         } else {
-          const float* W1 = P.theta + P.offW0;
-          const float* b1 = P.theta + P.offb0;
           float cs[32];
-#pragma unroll 4
+#pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const int o = col0 + i;
-            float z = b1[o] + W1[o * P.d] * x[0] + W1[o * P.d + 1] * x[1];
-            if (P.d == 3) z += W1[o * P.d + 2] * x[2];
-            z *= P.omega0;
-            __sincosf(z, &v[i], &cs[i]);
+            const float4 w1 = first_s[col0 + i];
+            const float z = fmaf(w1.x, x[0], fmaf(w1.y, x[1], fmaf(w1.z, x[2], w1.w)));
+            if (MODE == 1)
+              __sincosf(z, &v[i], &cs[i]);
+            else
+              v[i] = __sinf(z);
           }
-          if (P.mode == 1) {
+          if (MODE == 1) {
             store_row32_bf16(P.Act + prow * W + col0, v);
             store_row32_bf16(P.Cos + prow * W + col0, cs);
             if (c == 0 && g == 0) {
-              for (int k = 0; k < P.d; ++k) P.Y16c[(int64_t)k * P.npts_pad + prow] = __float2bfloat16_rn(x[k]);
+#pragma unroll
+              for (int k = 0; k < 3; ++k)
+                if (k < P.d) P.Y16c[(int64_t)k * P.npts_pad + prow] = __float2bfloat16_rn(x[k]);
             }
           }
         }
         const int as = c & 3;
-        if (!warp_wait(&a_empty[as], ae[as], &abort_flag, err, 401)) goto epi_done;
-        ae[as] ^= 1;
+        if (!warp_wait(&a_empty[as], (ae >> as) & 1u, &abort_flag, err, 401)) goto epi_done;
+        ae ^= 1u << as;
         st_panel_row32(apan + as * kPanelBytes, r, 4 * g, v);
         fence_async_smem();
         mbar_arrive(&a_full[as]);
@@ -561,19 +582,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- GEMM stages ----
       for (int s = 0; s < P.n_stages; ++s) {
         const uint32_t b = acc_ctr & 1;
-        if (!warp_wait(&acc_full[b], af[b], &abort_flag, err, 402)) goto epi_done;
-        af[b] ^= 1;
+        if (!warp_wait(&acc_full[b], (af >> b) & 1u, &abort_flag, err, 402)) goto epi_done;
+        af ^= 1u << b;
         tc_fence_after();
         const int kind = P.st_kind[s], l = P.st_layer[s];
+        const bool write_panel = s + 1 < P.n_stages;  // the next stage's input
         float dot = 0.f;
         for (int c = 0; c < W / 64; ++c) {
           const int col0 = 64 * c + 32 * g;
           tmem_ld32(tmem + lane_off + b * W + col0, v);
-          const bool write_panel = s + 1 < P.n_stages;  // the next stage's input
-          if (kind == kBwd) {
+          if (MODE == 1 && kind == kBwd) {
             // v = (W'_l^T delta_l) for layer l; delta_{l-1} = v * sigma'(u_{l-1})
             float sg[32];
-            if (P.kind == INRCT_FFN_RELU) {
+            if (KIND == INRCT_FFN_RELU) {
               load_row32_bf16(P.Act + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
 #pragma unroll
               for (int i = 0; i < 32; ++i) v[i] = sg[i] > 0.f ? v[i] : 0.f;
@@ -582,41 +603,62 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int i = 0; i < 32; ++i) v[i] *= sg[i];
             }
-            if (P.mode == 1) store_row32_bf16(P.Dlt + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, v);
+            store_row32_bf16(P.Dlt + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, v);
           } else {
-            const float* bl = P.bias + (int64_t)l * W + col0;
+            const float4* bl = reinterpret_cast<const float4*>(bias_s + (size_t)l * W + col0);
             float cs[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float z = v[i] + bl[i];
-              if (P.kind == INRCT_FFN_RELU) {
-                v[i] = fmaxf(z, 0.f);
-                cs[i] = z > 0.f ? 1.f : 0.f;
-              } else {
-                __sincosf(z, &v[i], &cs[i]);
+            for (int i4 = 0; i4 < 8; ++i4) {
+              const float4 bb = bl[i4];
+              const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const int i = 4 * i4 + k;
+                const float z = v[i] + bq[k];
+                if (KIND == INRCT_FFN_RELU) {
+                  v[i] = fmaxf(z, 0.f);
+                  if (MODE == 1) cs[i] = z > 0.f ? 1.f : 0.f;
+                } else if (MODE == 1) {
+                  __sincosf(z, &v[i], &cs[i]);
+                } else {
+                  v[i] = __sinf(z);
+                }
               }
             }
-            if (P.mode == 1) {
+            if (MODE == 1) {
               store_row32_bf16(P.Act + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
-              if (P.kind == INRCT_SIREN && kind == kFwdHidden)
+              if (KIND == INRCT_SIREN && kind == kFwdHidden)
                 store_row32_bf16(P.Cos + ((int64_t)l * P.npts_pad + prow) * W + col0, cs);
             }
             if (kind == kFwdLast) {
-              if (P.mode == 0) {
+              const float4* wo = reinterpret_cast<const float4*>(wout_s + col0);
+              if (MODE == 0) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) dot = fmaf(v[i], wout[col0 + i], dot);
+                for (int i4 = 0; i4 < 8; ++i4) {
+                  const float4 ww = wo[i4];
+                  dot = fmaf(v[4 * i4], ww.x, dot);
+                  dot = fmaf(v[4 * i4 + 1], ww.y, dot);
+                  dot = fmaf(v[4 * i4 + 2], ww.z, dot);
+                  dot = fmaf(v[4 * i4 + 3], ww.w, dot);
+                }
               } else {
                 // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = sv * wout[col0 + i] * cs[i];
+                for (int i4 = 0; i4 < 8; ++i4) {
+                  const float4 ww = wo[i4];
+                  v[4 * i4] = sv * ww.x * cs[4 * i4];
+                  v[4 * i4 + 1] = sv * ww.y * cs[4 * i4 + 1];
+                  v[4 * i4 + 2] = sv * ww.z * cs[4 * i4 + 2];
+                  v[4 * i4 + 3] = sv * ww.w * cs[4 * i4 + 3];
+                }
                 store_row32_bf16(P.Dlt + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
                 if (c == 0 && g == 0) P.Y16o[prow] = __float2bfloat16_rn(sv);
               }
             }
           }
           if (write_panel) {
-            if (!warp_wait(&a_empty[c], ae[c], &abort_flag, err, 403)) goto epi_done;
-            ae[c] ^= 1;
+            if (!warp_wait(&a_empty[c], (ae >> c) & 1u, &abort_flag, err, 403)) goto epi_done;
+            ae ^= 1u << c;
             st_panel_row32(apan + c * kPanelBytes, r, 4 * g, v);
             fence_async_smem();
             mbar_arrive(&a_full[c]);
@@ -625,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         mbar_arrive(&acc_empty[b]);
         ++acc_ctr;
-        if (kind == kFwdLast && P.mode == 0) {
+        if (MODE == 0 && kind == kFwdLast) {
           dotp[g][r] = dot;
           mbar_arrive(&dot_bar);
           if (!warp_wait(&dot_bar, dotph, &abort_flag, err, 404)) goto epi_done;
@@ -644,6 +686,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Launches the tile kernel instance for (mode, kind) with the needed shared memory.
+int launch_tile(int mode, const Net& n, const Maps& maps, const TileProg& P, int grid, int* err,
+                cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -658,7 +704,33 @@ int num_sms() {
   return n;
 }
 
-constexpr size_t kTileSmem = 4 * kPanelBytes + (size_t)kRing * 256 * 128 + 1024;
+size_t tile_smem(const Net& n) {
+  return 4 * (size_t)kPanelBytes + (size_t)kRing * n.W * 128 +
+         sizeof(float) * param_floats(n.L, n.W, n.F, n.kind) + 1024;
+}
+
+template <int MODE, int KIND>
+int launch_tile_t(const Net& n, const Maps& maps, const TileProg& P, int grid, int* err, cudaStream_t st) {
+  const size_t sm = tile_smem(n);
+  cudaError_t e = cudaFuncSetAttribute(mlp_tile_kernel<MODE, KIND>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) {
+    set_error("tile kernel shared memory (%zu bytes): %s", sm, cudaGetErrorString(e));
+    return INRCT_ERR_CUDA;
+  }
+  mlp_tile_kernel<MODE, KIND><<<grid, kThreads, sm, st>>>(maps, P, err);
+  INRCT_CHECK_LAUNCH("mlp tile kernel");
+  return INRCT_OK;
+}
+
+int launch_tile(int mode, const Net& n, const Maps& maps, const TileProg& P, int grid, int* err,
+                cudaStream_t st) {
+  if (mode == 0)
+    return n.kind == INRCT_SIREN ? launch_tile_t<0, INRCT_SIREN>(n, maps, P, grid, err, st)
+                                 : launch_tile_t<0, INRCT_FFN_RELU>(n, maps, P, grid, err, st);
+  return n.kind == INRCT_SIREN ? launch_tile_t<1, INRCT_SIREN>(n, maps, P, grid, err, st)
+                               : launch_tile_t<1, INRCT_FFN_RELU>(n, maps, P, grid, err, st);
+}
 constexpr size_t kGemmSmem = (size_t)kGemmStages * kGemmStageBytes + 2048 + 1024;
 
 struct TcWeights {
@@ -692,8 +764,8 @@ int prep_weights(const Net& n, const float* theta, Carver& c, bool transposed, T
     prep_weights_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(theta, n.offW[l], n.offb[l], n.out_dim[l],
                                                           n.in_dim[l], sc, w->Wb[l], w->WbT[l],
                                                           w->bias + (int64_t)l * n.W);
+    INRCT_CHECK_LAUNCH("weight preparation");
   }
-  INRCT_CHECK_LAUNCH("weight preparation");
   return INRCT_OK;
 }
 
@@ -764,6 +836,10 @@ bool tc_supported(const Net& n, char* why, size_t len) {
     snprintf(why, len, "n_feat=%d too large (<= 1024)", n.F);
     return false;
   }
+  if (tile_smem(n) + 4096 > 232448) {
+    snprintf(why, len, "network too large for the tile kernel's shared memory (%zu bytes)", tile_smem(n));
+    return false;
+  }
   return true;
 }
 
@@ -788,11 +864,11 @@ int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image,
   P.n_grid = npts;
   P.npts = npts;
   P.out = image;
-  INRCT_TRY(set_smem_attr((const void*)mlp_tile_kernel, kTileSmem));
   const int64_t tiles = (npts + kTile - 1) / kTile;
   const int grid = (int)std::min<int64_t>(tiles, num_sms());
-  mlp_tile_kernel<<<grid, kThreads, kTileSmem, st>>>(maps, P, err);
-  INRCT_CHECK_LAUNCH("mlp tile kernel (eval)");
+  prof_mark(kMarkEvalKernel, st);
+  INRCT_TRY(launch_tile(0, n, maps, P, grid, err, st));
+  prof_mark(kMarkEvalDone, st);
   return INRCT_OK;
 }
 
@@ -942,8 +1018,8 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
       prep_weights_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(theta, n.offW[l], n.offb[l], n.out_dim[l],
                                                             n.in_dim[l], sc, w.w.Wb[l], w.w.WbT[l],
                                                             w.w.bias + (int64_t)l * n.W);
+      INRCT_CHECK_LAUNCH("weight preparation");
     }
-    INRCT_CHECK_LAUNCH("weight preparation");
   }
   static Maps tmaps, gmaps;
   TileProg P;
@@ -962,7 +1038,6 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
   P.Y16c = w.Y16c;
   P.Y16o = w.Y16o;
   P.npts_pad = w.pad;
-  INRCT_TRY(set_smem_attr((const void*)mlp_tile_kernel, kTileSmem));
   INRCT_TRY(set_smem_attr((const void*)tn_gemm_kernel, kGemmSmem));
   for (int64_t c0 = 0; c0 < n_idx; c0 += chunk) {
     const int64_t np = std::min(chunk, n_idx - c0);
@@ -971,8 +1046,9 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     cudaMemsetAsync(w.Y16c, 0, sizeof(__nv_bfloat16) * 16 * w.pad, st);
     cudaMemsetAsync(w.Y16o, 0, sizeof(__nv_bfloat16) * 16 * w.pad, st);
     const int64_t tiles = (np + kTile - 1) / kTile;
-    mlp_tile_kernel<<<(int)std::min<int64_t>(tiles, num_sms()), kThreads, kTileSmem, st>>>(tmaps, P, w.err);
-    INRCT_CHECK_LAUNCH("mlp tile kernel (vjp)");
+    if (c0 == 0) prof_mark(kMarkVjpKernel, st);
+    INRCT_TRY(launch_tile(1, n, tmaps, P, (int)std::min<int64_t>(tiles, num_sms()), w.err, st));
+    if (c0 == 0) prof_mark(kMarkVjpKernelDone, st);
     // split-K weight-gradient GEMMs over this chunk's points
     int64_t pf;
     GemmPlan G = plan_gemm(n, np, &pf);

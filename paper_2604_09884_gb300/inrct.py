@@ -88,6 +88,10 @@ def lib():
         "inr_weighted_vjp": ([m, _P, gr, _P, _I64, _P, ctypes.c_double, _P, _P, _P, _SZ, _P],
                              ctypes.c_int),
         "inrct_step_ws_bytes": ([g, gr, m, _I64], _SZ),
+        "inrct_launch_count": ([], ctypes.c_longlong),
+        "inrct_profile_begin": ([ctypes.c_int], ctypes.c_int),
+        "inrct_profile_end": ([ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "inrct_gemm_tn_ws_bytes": ([_I64, ctypes.c_int, ctypes.c_int], _SZ),
         "inrct_gemm_tn": ([_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, _P, _P, _SZ, _P], ctypes.c_int),
         "grad_step": ([g, gr, m, ctypes.c_int, _P, _P, _P, _I64, ctypes.c_double,
@@ -273,6 +277,26 @@ def gemm_tn(X: torch.Tensor, Y: torch.Tensor | None, Y16: torch.Tensor | None, s
     _check(L.inrct_gemm_tn(_ptr(X, torch.bfloat16), _ptr(Y, torch.bfloat16), _ptr(Y16, torch.bfloat16),
                            K, M, N, _ptr(C), _ptr(ws), nb, _stream(stream)))
     return C
+
+
+STAGES = ["eval_prep", "eval_mlp_kernel", "project_loss", "backproject", "vjp_prep",
+          "vjp_mlp_kernel", "vjp_dw_gemm_reduce", "adam"]
+
+
+def launch_count() -> int:
+    return int(lib().inrct_launch_count())
+
+
+def profile_begin(max_steps: int):
+    _check(lib().inrct_profile_begin(max_steps))
+
+
+def profile_end() -> tuple[dict, int]:
+    """Summed milliseconds per grad_step stage over the recorded steps, and the step count."""
+    arr = (ctypes.c_double * len(STAGES))()
+    steps = ctypes.c_int(0)
+    _check(lib().inrct_profile_end(arr, len(STAGES), ctypes.byref(steps)))
+    return dict(zip(STAGES, list(arr))), steps.value
 
 
 def adam(lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, t=1) -> Adam:
