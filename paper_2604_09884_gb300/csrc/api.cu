@@ -71,15 +71,17 @@ static int check_tc(const inrct_mlp* mlp, const Net& n) {
 }
 
 static int eval_dispatch(const inrct_mlp* mlp, const Net& n, const float* theta, int N, int64_t npts,
-                         float* image, void* ws, size_t ws_bytes, cudaStream_t st) {
-  return use_tc(mlp) ? tc_eval(n, theta, N, npts, image, ws, ws_bytes, st)
+                         float* image, void* ws, size_t ws_bytes, cudaStream_t st,
+                         const void* prepared = nullptr) {
+  return use_tc(mlp) ? tc_eval(n, theta, N, npts, image, ws, ws_bytes, st, prepared)
                      : simt_eval(n, theta, N, npts, image, ws, ws_bytes, st);
 }
 
 static int vjp_dispatch(const inrct_mlp* mlp, const Net& n, const float* theta, int N,
                         const int32_t* idx, int64_t n_idx, const float* v, double scale,
-                        double* g64, float* g32, void* ws, size_t ws_bytes, cudaStream_t st) {
-  return use_tc(mlp) ? tc_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, ws, ws_bytes, st)
+                        double* g64, float* g32, void* ws, size_t ws_bytes, cudaStream_t st,
+                        const void* prepared = nullptr) {
+  return use_tc(mlp) ? tc_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, ws, ws_bytes, st, prepared)
                      : simt_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, ws, ws_bytes, st);
 }
 
@@ -175,6 +177,10 @@ int inr_weighted_vjp(const inrct_mlp* mlp, const float* theta, const inrct_grid*
 struct StepWs {
   float *x, *z, *r, *v;
   double *g, *loss;
+  void* tables;  // ray tables, built once per step and shared by P and P^T
+  size_t tables_bytes;
+  void* wprep;   // BF16 weights, converted once per step (tensor-core path)
+  size_t wprep_bytes;
   void* stage;
   size_t stage_bytes;
 };
@@ -191,8 +197,12 @@ static size_t step_layout(const inrct_geom* geom, const inrct_grid* grid, const 
   w.v = c.take<float>(npix);
   w.g = c.take<double>(n.p);
   w.loss = c.take<double>(1);
-  size_t st = project_ws_bytes(geom, grid);
-  st = std::max(st, backproject_ws_bytes(geom, grid));
+  w.tables_bytes = tables_bytes(geom);
+  w.tables = c.take<char>(w.tables_bytes);
+  w.wprep_bytes = use_tc(mlp) ? tc_weights_bytes(n) : 0;
+  w.wprep = use_tc(mlp) ? c.take<char>(w.wprep_bytes) : nullptr;
+  size_t st = project_ws_bytes(geom, grid, false);
+  st = std::max(st, backproject_ws_bytes(geom, grid, false));
   st = std::max(st, eval_ws(mlp, n));
   st = std::max(st, vjp_ws(mlp, n, n_idx));
   if (loss == INRCT_LOSS_FLS) st = std::max(st, ramp_ws_bytes(geom));
@@ -232,23 +242,26 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
   }
   prof_step_begin();
   prof_mark(kMarkStart, stream);
+  if (w.wprep) INRCT_TRY(tc_prepare(n, theta, w.wprep, w.wprep_bytes, stream));
   // Algorithm 1, step 1: z = P E{f_theta} (no gradient tracking); loss epilogue
   INRCT_TRY(eval_dispatch(mlp, n, theta, grid->N, grid_points(grid), w.x, w.stage, w.stage_bytes,
-                          stream));
-  INRCT_TRY(project_impl(geom, grid, w.x, w.z, y, w.r, w.loss, w.stage, w.stage_bytes, stream));
+                          stream, w.wprep));
+  ProjTables tabs;
+  INRCT_TRY(build_tables(geom, grid, w.tables, w.tables_bytes, &tabs, stream));
+  INRCT_TRY(project_impl(geom, grid, w.x, w.z, y, w.r, w.loss, w.stage, w.stage_bytes, stream, &tabs));
   prof_mark(kMarkProjDone, stream);
   // Algorithm 1, step 2: v = P^T dL/dz  (LS: z - y; FLS: F (z - y), Sec. 3)
   if (loss == INRCT_LOSS_FLS) {
     INRCT_TRY(ramp_filter_impl(geom, grid, w.r, w.z, w.loss, w.stage, w.stage_bytes, stream));
-    INRCT_TRY(backproject_impl(geom, grid, w.z, w.v, w.stage, w.stage_bytes, stream));
+    INRCT_TRY(backproject_impl(geom, grid, w.z, w.v, w.stage, w.stage_bytes, stream, &tabs));
   } else {
-    INRCT_TRY(backproject_impl(geom, grid, w.r, w.v, w.stage, w.stage_bytes, stream));
+    INRCT_TRY(backproject_impl(geom, grid, w.r, w.v, w.stage, w.stage_bytes, stream, &tabs));
   }
   prof_mark(kMarkBackDone, stream);
   // steps 3-5: the index set is the caller's; gradient of the virtual loss (Eq. 3)
   double* g = grad_out ? grad_out : w.g;
   INRCT_TRY(vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, w.v, scale, g, nullptr, w.stage,
-                         w.stage_bytes, stream));
+                         w.stage_bytes, stream, w.wprep));
   prof_mark(kMarkVjpDone, stream);
   if (loss_out) {
     cudaError_t e = cudaMemcpyAsync(loss_out, w.loss, sizeof(double), cudaMemcpyDeviceToDevice, stream);

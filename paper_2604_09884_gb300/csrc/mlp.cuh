@@ -44,13 +44,17 @@ int simt_vjp(const Net& net, const float* theta, int N, const int32_t* idx, int6
 
 // BF16 tcgen05 path
 bool tc_supported(const Net& net, char* why, size_t why_len);
+// BF16 weights prepared once (grad_step shares them between evaluation and VJP);
+// `prepared` may be NULL, then each call converts theta itself.
+size_t tc_weights_bytes(const Net& net);
+int tc_prepare(const Net& net, const float* theta, void* buf, size_t bytes, cudaStream_t st);
 size_t tc_eval_ws_bytes(const Net& net);
 int tc_eval(const Net& net, const float* theta, int N, int64_t n, float* image, void* ws,
-            size_t ws_bytes, cudaStream_t st);
+            size_t ws_bytes, cudaStream_t st, const void* prepared = nullptr);
 size_t tc_vjp_ws_bytes(const Net& net, int64_t n_idx);
 int tc_vjp(const Net& net, const float* theta, int N, const int32_t* idx, int64_t n_idx,
            const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
-           size_t ws_bytes, cudaStream_t st);
+           size_t ws_bytes, cudaStream_t st, const void* prepared = nullptr);
 
 // split-K TN GEMM of the weight gradients, exposed for diagnostics
 size_t gemm_tn_ws_bytes(int64_t K, int M, int N);

@@ -50,8 +50,6 @@ constexpr int kTile = 128;       // points per tile (MMA M)
 constexpr int kRing = 4;         // weight ring slots
 constexpr int kPanelBytes = kTile * 128;  // one 64-column BF16 panel of 128 rows
 constexpr int kMaxStages = 2 * kMaxLayers;
-constexpr int kEpiThreads = 256;
-constexpr int kThreads = kEpiThreads + 64;
 constexpr int kMaxJobs = 24;
 
 // ---------------------------------------------------------------------------
@@ -101,17 +99,29 @@ struct Maps {
 // ---------------------------------------------------------------------------
 // weight preparation: BF16 (W' = scale W) row-major and transposed, FP32 biases
 // ---------------------------------------------------------------------------
-__global__ void prep_weights_kernel(const float* __restrict__ theta, int64_t offW, int64_t offb,
-                                    int out, int in, float scale, __nv_bfloat16* __restrict__ Wb,
-                                    __nv_bfloat16* __restrict__ WbT, float* __restrict__ bias) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (int64_t)out * in) {
+struct PrepTable {
+  int n;
+  int out[kMaxLayers], in[kMaxLayers];
+  int64_t offW[kMaxLayers], offb[kMaxLayers];
+  __nv_bfloat16* Wb[kMaxLayers];
+  __nv_bfloat16* WbT[kMaxLayers];
+  float* bias[kMaxLayers];
+};
+
+// All MMA layers in one launch: blockIdx.y selects the layer.
+__global__ void prep_all_kernel(const float* __restrict__ theta, const __grid_constant__ PrepTable T,
+                                float scale) {
+  const int l = blockIdx.y;
+  const int out = T.out[l], in = T.in[l];
+  const int64_t cnt = (int64_t)out * in;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
+       t += (int64_t)gridDim.x * blockDim.x) {
     const int o = (int)(t / in), k = (int)(t % in);
-    const __nv_bfloat16 w = __float2bfloat16_rn(scale * theta[offW + t]);
-    Wb[t] = w;
-    if (WbT) WbT[(int64_t)k * out + o] = w;
+    const __nv_bfloat16 w = __float2bfloat16_rn(scale * theta[T.offW[l] + t]);
+    T.Wb[l][t] = w;
+    if (T.WbT[l]) T.WbT[l][(int64_t)k * out + o] = w;
+    if (t < out) T.bias[l][t] = scale * theta[T.offb[l] + t];
   }
-  if (t < out) bias[t] = scale * theta[offb + t];
 }
 
 // ---------------------------------------------------------------------------
@@ -301,17 +311,32 @@ __global__ void gemm_reduce_kernel(const __grid_constant__ GemmPlan plan, const 
   grad[dst] = accumulate ? grad[dst] + s : s;
 }
 
-// Output-layer bias gradient: grad[off] (+)= sum_k scale * v[idx[k]] (FP64, one block, fixed order).
-__global__ void out_bias_grad_kernel(const int32_t* __restrict__ idx, int64_t npts,
-                                     const float* __restrict__ v, int64_t n_grid, float scale,
-                                     int accumulate, double* __restrict__ grad) {
-  __shared__ double sh[1024];
+// Output-layer bias gradient: grad[off] (+)= sum_k scale * v[idx[k]] (FP64).  Pass 1: one
+// partial per block (fixed order); pass 2: one block sums the partials in order.
+constexpr int kBiasBlocks = 128;
+__global__ void out_bias_partial_kernel(const int32_t* __restrict__ idx, int64_t npts,
+                                        const float* __restrict__ v, int64_t n_grid, float scale,
+                                        double* __restrict__ part) {
+  __shared__ double sh[256];
   double s = 0.0;
-  for (int64_t k = threadIdx.x; k < npts; k += blockDim.x) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npts;
+       k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx[k];
     if (i >= 0 && i < n_grid) s += (double)(scale * v[i]);
   }
   sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void out_bias_final_kernel(const double* __restrict__ part, int n, int accumulate,
+                                      double* __restrict__ grad) {
+  __shared__ double sh[kBiasBlocks];
+  sh[threadIdx.x] = threadIdx.x < n ? part[threadIdx.x] : 0.0;
   __syncthreads();
   for (int o = blockDim.x / 2; o; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
@@ -353,18 +378,20 @@ struct TileProg {
   int stall;            // diagnostic: the producer issues nothing (tests bounded waits)
 };
 
-__device__ __forceinline__ void store_row32_bf16(__nv_bfloat16* dst, const float* v) {
+template <int CW>
+__device__ __forceinline__ void store_row_bf16(__nv_bfloat16* dst, const float* v) {
   uint4* d4 = reinterpret_cast<uint4*>(dst);
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < CW / 8; ++q)
     d4[q] = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
                        pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
 }
 
-__device__ __forceinline__ void load_row32_bf16(const __nv_bfloat16* src, float* v) {
+template <int CW>
+__device__ __forceinline__ void load_row_bf16(const __nv_bfloat16* src, float* v) {
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < CW / 8; ++q) {
     const uint4 w = s4[q];
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -393,8 +420,10 @@ __host__ __device__ inline size_t param_floats(int L, int W, int F, int kind) {
   return (size_t)L * W + W + 4 * (size_t)(kind == INRCT_SIREN ? W : F);
 }
 
-template <int MODE, int KIND>
-__global__ void __launch_bounds__(kThreads, 1)
+// NWG epilogue warpgroups; each thread of warpgroup g owns CW = 64/NWG columns of
+// every 64-column chunk of its TMEM lane (row).
+template <int MODE, int KIND, int NWG>
+__global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     mlp_tile_kernel(const __grid_constant__ Maps maps, const __grid_constant__ TileProg P,
                     int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t dsm[];
@@ -407,7 +436,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float4* first_s = reinterpret_cast<float4*>(wout_s + W);
   __shared__ uint64_t w_full[kRing], w_empty[kRing], a_full[4], a_empty[4], acc_full[2], acc_empty[2],
       dot_bar, drain_bar;
-  __shared__ float dotp[2][kTile];
+  constexpr int CW = 64 / NWG, EPI = 128 * NWG;
+  __shared__ float dotp[NWG][kTile];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -420,14 +450,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&w_empty[s], 1);
     }
     for (int s = 0; s < 4; ++s) {
-      mbar_init(&a_full[s], kEpiThreads);
+      mbar_init(&a_full[s], EPI);
       mbar_init(&a_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], kEpiThreads);
+      mbar_init(&acc_empty[s], EPI);
     }
-    mbar_init(&dot_bar, kEpiThreads);
+    mbar_init(&dot_bar, EPI);
     mbar_init(&drain_bar, 1);
     abort_flag = 0;
     fence_mbar_init();
@@ -453,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  if (warp == 8) {
+  if (warp == 4 * NWG) {
     // ---------------- TMA producer ----------------
     if (lane == 0 && !P.stall) {
       for (int s = 0; s < P.n_stages; ++s) prefetch_map(&maps.m[P.st_map[s]]);
@@ -473,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   producer_done:;
-  } else if (warp == 9) {
+  } else if (warp == 4 * NWG + 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       // phase parities of the barriers, one bit per slot
@@ -520,13 +550,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue warps 0..7 ----------------
+    // ---------------- epilogue warps 0 .. 4*NWG-1 ----------------
     const int q = warp & 3, g = warp >> 2;
     const int r = q * 32 + lane;                 // row of the tile = TMEM lane
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     uint32_t ae = 0xFu, af = 0u, dotph = 0, acc_ctr = 0;  // phase parities, one bit per slot
     const float bout = P.theta[P.offbout];
-    float v[32];
+    float v[CW];
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
       const int64_t pt = t * kTile + r;
       const bool valid = pt < P.npts;
@@ -539,22 +569,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t prow = t * kTile + r;        // scratch row (rows are padded to the tile)
       // ---- first stage input ----
       for (int c = 0; c < P.in_panels; ++c) {
-        const int col0 = 64 * c + 32 * g;
+        const int col0 = 64 * c + CW * g;
         if (KIND == INRCT_FFN_RELU) {
           const bool is_sin = col0 >= P.F;
           const int f0 = is_sin ? col0 - P.F : col0;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < CW; ++i) {
             const float4 bf = first_s[f0 + i];
             float ph = __fadd_rn(__fmul_rn(bf.x, x[0]), __fmul_rn(bf.y, x[1]));
             if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, x[2]));
             v[i] = four_feat(ph, is_sin);
           }
-          if (MODE == 1) store_row32_bf16(P.E + prow * (2 * P.F) + col0, v);
+          if (MODE == 1) store_row_bf16<CW>(P.E + prow * (2 * P.F) + col0, v);
         } else {
-          float cs[32];
+          float cs[CW];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < CW; ++i) {
             const float4 w1 = first_s[col0 + i];
             const float z = fmaf(w1.x, x[0], fmaf(w1.y, x[1], fmaf(w1.z, x[2], w1.w)));
             if (MODE == 1)
@@ -563,8 +593,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               v[i] = __sinf(z);
           }
           if (MODE == 1) {
-            store_row32_bf16(P.Act + prow * W + col0, v);
-            store_row32_bf16(P.Cos + prow * W + col0, cs);
+            store_row_bf16<CW>(P.Act + prow * W + col0, v);
+            store_row_bf16<CW>(P.Cos + prow * W + col0, cs);
             if (c == 0 && g == 0) {
 #pragma unroll
               for (int k = 0; k < 3; ++k)
@@ -575,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int as = c & 3;
         if (!warp_wait(&a_empty[as], (ae >> as) & 1u, &abort_flag, err, 401)) goto epi_done;
         ae ^= 1u << as;
-        st_panel_row32(apan + as * kPanelBytes, r, 4 * g, v);
+        st_panel_row<CW>(apan + as * kPanelBytes, r, (CW / 8) * g, v);
         fence_async_smem();
         mbar_arrive(&a_full[as]);
       }
@@ -589,26 +619,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool write_panel = s + 1 < P.n_stages;  // the next stage's input
         float dot = 0.f;
         for (int c = 0; c < W / 64; ++c) {
-          const int col0 = 64 * c + 32 * g;
-          tmem_ld32(tmem + lane_off + b * W + col0, v);
+          const int col0 = 64 * c + CW * g;
+          tmem_ld<CW>(tmem + lane_off + b * W + col0, v);
           if (MODE == 1 && kind == kBwd) {
             // v = (W'_l^T delta_l) for layer l; delta_{l-1} = v * sigma'(u_{l-1})
-            float sg[32];
+            float sg[CW];
             if (KIND == INRCT_FFN_RELU) {
-              load_row32_bf16(P.Act + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
+              load_row_bf16<CW>(P.Act + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
 #pragma unroll
-              for (int i = 0; i < 32; ++i) v[i] = sg[i] > 0.f ? v[i] : 0.f;
+              for (int i = 0; i < CW; ++i) v[i] = sg[i] > 0.f ? v[i] : 0.f;
             } else {
-              load_row32_bf16(P.Cos + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
+              load_row_bf16<CW>(P.Cos + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
 #pragma unroll
-              for (int i = 0; i < 32; ++i) v[i] *= sg[i];
+              for (int i = 0; i < CW; ++i) v[i] *= sg[i];
             }
-            store_row32_bf16(P.Dlt + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, v);
+            store_row_bf16<CW>(P.Dlt + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, v);
           } else {
             const float4* bl = reinterpret_cast<const float4*>(bias_s + (size_t)l * W + col0);
-            float cs[32];
+            float cs[CW];
 #pragma unroll
-            for (int i4 = 0; i4 < 8; ++i4) {
+            for (int i4 = 0; i4 < CW / 4; ++i4) {
               const float4 bb = bl[i4];
               const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
@@ -626,15 +656,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
             if (MODE == 1) {
-              store_row32_bf16(P.Act + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
+              store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
               if (KIND == INRCT_SIREN && kind == kFwdHidden)
-                store_row32_bf16(P.Cos + ((int64_t)l * P.npts_pad + prow) * W + col0, cs);
+                store_row_bf16<CW>(P.Cos + ((int64_t)l * P.npts_pad + prow) * W + col0, cs);
             }
             if (kind == kFwdLast) {
               const float4* wo = reinterpret_cast<const float4*>(wout_s + col0);
               if (MODE == 0) {
 #pragma unroll
-                for (int i4 = 0; i4 < 8; ++i4) {
+                for (int i4 = 0; i4 < CW / 4; ++i4) {
                   const float4 ww = wo[i4];
                   dot = fmaf(v[4 * i4], ww.x, dot);
                   dot = fmaf(v[4 * i4 + 1], ww.y, dot);
@@ -644,14 +674,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               } else {
                 // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
 #pragma unroll
-                for (int i4 = 0; i4 < 8; ++i4) {
+                for (int i4 = 0; i4 < CW / 4; ++i4) {
                   const float4 ww = wo[i4];
                   v[4 * i4] = sv * ww.x * cs[4 * i4];
                   v[4 * i4 + 1] = sv * ww.y * cs[4 * i4 + 1];
                   v[4 * i4 + 2] = sv * ww.z * cs[4 * i4 + 2];
                   v[4 * i4 + 3] = sv * ww.w * cs[4 * i4 + 3];
                 }
-                store_row32_bf16(P.Dlt + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
+                store_row_bf16<CW>(P.Dlt + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
                 if (c == 0 && g == 0) P.Y16o[prow] = __float2bfloat16_rn(sv);
               }
             }
@@ -659,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (write_panel) {
             if (!warp_wait(&a_empty[c], (ae >> c) & 1u, &abort_flag, err, 403)) goto epi_done;
             ae ^= 1u << c;
-            st_panel_row32(apan + c * kPanelBytes, r, 4 * g, v);
+            st_panel_row<CW>(apan + c * kPanelBytes, r, (CW / 8) * g, v);
             fence_async_smem();
             mbar_arrive(&a_full[c]);
           }
@@ -672,7 +702,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_arrive(&dot_bar);
           if (!warp_wait(&dot_bar, dotph, &abort_flag, err, 404)) goto epi_done;
           dotph ^= 1;
-          if (g == 0 && valid) P.out[pt] = bout + dotp[0][r] + dotp[1][r];
+          if (g == 0 && valid) {
+            float f = bout;
+#pragma unroll
+            for (int q2 = 0; q2 < NWG; ++q2) f += dotp[q2][r];
+            P.out[pt] = f;
+          }
         }
       }
     }
@@ -709,16 +744,18 @@ size_t tile_smem(const Net& n) {
          sizeof(float) * param_floats(n.L, n.W, n.F, n.kind) + 1024;
 }
 
+constexpr int kTileNWG = 4;  // epilogue warpgroups of the tile kernel
+
 template <int MODE, int KIND>
 int launch_tile_t(const Net& n, const Maps& maps, const TileProg& P, int grid, int* err, cudaStream_t st) {
   const size_t sm = tile_smem(n);
-  cudaError_t e = cudaFuncSetAttribute(mlp_tile_kernel<MODE, KIND>,
+  cudaError_t e = cudaFuncSetAttribute(mlp_tile_kernel<MODE, KIND, kTileNWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
     set_error("tile kernel shared memory (%zu bytes): %s", sm, cudaGetErrorString(e));
     return INRCT_ERR_CUDA;
   }
-  mlp_tile_kernel<MODE, KIND><<<grid, kThreads, sm, st>>>(maps, P, err);
+  mlp_tile_kernel<MODE, KIND, kTileNWG><<<grid, 32 * (4 * kTileNWG + 2), sm, st>>>(maps, P, err);
   INRCT_CHECK_LAUNCH("mlp tile kernel");
   return INRCT_OK;
 }
@@ -742,30 +779,44 @@ struct TcWeights {
 // Layers handled by the MMA stages: FFN 0..L-1, SIREN 1..L-1 (the SIREN first layer is FP32).
 int first_mma_layer(const Net& n) { return n.kind == INRCT_SIREN ? 1 : 0; }
 
-size_t weights_bytes(const Net& n, bool transposed) {
-  size_t b = 0;
-  for (int l = first_mma_layer(n); l < n.L; ++l)
-    b += align_up(sizeof(__nv_bfloat16) * n.in_dim[l] * n.out_dim[l], 256) * (transposed ? 2 : 1);
-  return b + align_up(sizeof(float) * n.L * n.W, 256) + 256;
-}
-
-int prep_weights(const Net& n, const float* theta, Carver& c, bool transposed, TcWeights* w,
-                 cudaStream_t st) {
+// BF16 weights (and their transposes) plus FP32 biases, laid out in order.
+void weights_layout(const Net& n, Carver& c, TcWeights* w) {
   w->bias = c.take<float>((size_t)n.L * n.W);
   for (int l = 0; l < kMaxLayers; ++l) w->Wb[l] = w->WbT[l] = nullptr;
   for (int l = first_mma_layer(n); l < n.L; ++l) {
     w->Wb[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
-    if (transposed) w->WbT[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
+    w->WbT[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
   }
-  if (!c.ok) return INRCT_ERR_WORKSPACE;
-  const float sc = n.kind == INRCT_SIREN ? n.omega0 : 1.f;
+}
+
+size_t weights_bytes(const Net& n) {
+  Carver c(nullptr, 0);
+  TcWeights w;
+  weights_layout(n, c, &w);
+  return c.off + 256;
+}
+
+// One launch converts every MMA layer of theta (omega0 folded for SIREN).
+int prep_weights(const Net& n, const float* theta, const TcWeights& w, cudaStream_t st) {
+  PrepTable T;
+  memset(&T, 0, sizeof(T));
+  int64_t most = 0;
   for (int l = first_mma_layer(n); l < n.L; ++l) {
-    const int64_t cnt = (int64_t)n.in_dim[l] * n.out_dim[l];
-    prep_weights_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(theta, n.offW[l], n.offb[l], n.out_dim[l],
-                                                          n.in_dim[l], sc, w->Wb[l], w->WbT[l],
-                                                          w->bias + (int64_t)l * n.W);
-    INRCT_CHECK_LAUNCH("weight preparation");
+    const int i = T.n++;
+    T.out[i] = n.out_dim[l];
+    T.in[i] = n.in_dim[l];
+    T.offW[i] = n.offW[l];
+    T.offb[i] = n.offb[l];
+    T.Wb[i] = w.Wb[l];
+    T.WbT[i] = w.WbT[l];
+    T.bias[i] = w.bias + (int64_t)l * n.W;
+    most = std::max<int64_t>(most, (int64_t)n.in_dim[l] * n.out_dim[l]);
   }
+  if (T.n == 0) return INRCT_OK;
+  const float sc = n.kind == INRCT_SIREN ? n.omega0 : 1.f;
+  dim3 grd((unsigned)std::min<int64_t>(ceil_div(most, 256), 512), T.n);
+  prep_all_kernel<<<grd, 256, 0, st>>>(theta, T, sc);
+  INRCT_CHECK_LAUNCH("weight preparation");
   return INRCT_OK;
 }
 
@@ -843,17 +894,37 @@ bool tc_supported(const Net& n, char* why, size_t len) {
   return true;
 }
 
-size_t tc_eval_ws_bytes(const Net& n) { return 256 + weights_bytes(n, false) + 256; }
+size_t tc_weights_bytes(const Net& n) { return weights_bytes(n); }
+
+int tc_prepare(const Net& n, const float* theta, void* buf, size_t bytes, cudaStream_t st) {
+  Carver c(buf, bytes);
+  TcWeights w;
+  weights_layout(n, c, &w);
+  if (!buf || !c.ok) {
+    set_error("tensor-core weights: buffer of %zu bytes too small (need %zu)", bytes, weights_bytes(n));
+    return INRCT_ERR_WORKSPACE;
+  }
+  return prep_weights(n, theta, w, st);
+}
+
+size_t tc_eval_ws_bytes(const Net& n) { return 256 + weights_bytes(n) + 256; }
 
 int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image, void* ws, size_t ws_bytes,
-            cudaStream_t st) {
+            cudaStream_t st, const void* prepared) {
   Carver c(ws, ws_bytes);
   int* err = c.take<int>(64);
   TcWeights w;
-  if (!ws || prep_weights(n, theta, c, false, &w, st) != INRCT_OK || !c.ok) {
+  weights_layout(n, c, &w);
+  if (!ws || !c.ok) {
     set_error("inr_eval_grid (bf16): workspace of %zu bytes too small (need %zu)", ws_bytes,
               tc_eval_ws_bytes(n));
     return INRCT_ERR_WORKSPACE;
+  }
+  if (prepared) {
+    Carver pc(const_cast<void*>(prepared), SIZE_MAX);
+    weights_layout(n, pc, &w);
+  } else {
+    INRCT_TRY(prep_weights(n, theta, w, st));
   }
   cudaMemsetAsync(err, 0, sizeof(int), st);
   static Maps maps;
@@ -879,6 +950,7 @@ struct TcVjpWs {
   TcWeights w;
   __nv_bfloat16 *E, *Act, *Dlt, *Cos, *Y16c, *Y16o;
   float* part;
+  double* bias_part;
   int64_t pad;
   size_t part_floats;
 };
@@ -969,13 +1041,7 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* ou
   Carver c(ws, cap);
   TcVjpWs w;
   w.err = c.take<int>(64);
-  // weights
-  w.w.bias = c.take<float>((size_t)n.L * n.W);
-  for (int l = 0; l < kMaxLayers; ++l) w.w.Wb[l] = w.w.WbT[l] = nullptr;
-  for (int l = first_mma_layer(n); l < n.L; ++l) {
-    w.w.Wb[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
-    w.w.WbT[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
-  }
+  weights_layout(n, c, &w.w);
   const int64_t pad = (chunk + kTile - 1) / kTile * kTile;
   w.pad = pad;
   w.E = n.kind == INRCT_FFN_RELU ? c.take<__nv_bfloat16>((size_t)pad * n.K0) : nullptr;
@@ -988,6 +1054,7 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* ou
   plan_gemm(n, chunk, &pf);
   w.part_floats = (size_t)pf;
   w.part = c.take<float>((size_t)pf);
+  w.bias_part = c.take<double>(kBiasBlocks);
   if (out) *out = w;
   if (ok) *ok = c.ok;
   return c.off + 256;
@@ -1001,7 +1068,8 @@ size_t tc_vjp_ws_bytes(const Net& n, int64_t n_idx) {
 }
 
 int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t n_idx, const float* v,
-           double scale, double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes, cudaStream_t st) {
+           double scale, double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes, cudaStream_t st,
+           const void* prepared) {
   const int64_t chunk = n_idx < kVjpChunk ? n_idx : kVjpChunk;
   TcVjpWs w;
   bool ok;
@@ -1011,15 +1079,11 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     return INRCT_ERR_WORKSPACE;
   }
   cudaMemsetAsync(w.err, 0, sizeof(int), st);
-  {  // the weight buffers were carved by vjp_layout; convert theta into them
-    const float sc = n.kind == INRCT_SIREN ? n.omega0 : 1.f;
-    for (int l = first_mma_layer(n); l < n.L; ++l) {
-      const int64_t cnt = (int64_t)n.in_dim[l] * n.out_dim[l];
-      prep_weights_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(theta, n.offW[l], n.offb[l], n.out_dim[l],
-                                                            n.in_dim[l], sc, w.w.Wb[l], w.w.WbT[l],
-                                                            w.w.bias + (int64_t)l * n.W);
-      INRCT_CHECK_LAUNCH("weight preparation");
-    }
+  if (prepared) {  // weights converted once by the caller (grad_step)
+    Carver pc(const_cast<void*>(prepared), SIZE_MAX);
+    weights_layout(n, pc, &w.w);
+  } else {
+    INRCT_TRY(prep_weights(n, theta, w.w, st));
   }
   static Maps tmaps, gmaps;
   TileProg P;
@@ -1071,9 +1135,11 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
       maxe = std::max(maxe, G.job[q].M * (G.job[q].w_cols + 1));
     gemm_reduce_kernel<<<dim3(ceil_div(maxe, 256), G.n_jobs), 256, 0, st>>>(G, w.part, c0 > 0, grad_f64);
     INRCT_CHECK_LAUNCH("gemm reduce");
-    out_bias_grad_kernel<<<1, 1024, 0, st>>>(idx + c0, np, v, ng, (float)scale, c0 > 0,
-                                             grad_f64 + n.offb[n.L]);
+    out_bias_partial_kernel<<<kBiasBlocks, 256, 0, st>>>(idx + c0, np, v, ng, (float)scale, w.bias_part);
     INRCT_CHECK_LAUNCH("output bias gradient");
+    out_bias_final_kernel<<<1, kBiasBlocks, 0, st>>>(w.bias_part, kBiasBlocks, c0 > 0,
+                                                     grad_f64 + n.offb[n.L]);
+    INRCT_CHECK_LAUNCH("output bias gradient (final)");
   }
   if (grad_f32) INRCT_TRY(f64_to_f32(grad_f64, grad_f32, n.p, st));
   return INRCT_OK;

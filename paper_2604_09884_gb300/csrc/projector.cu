@@ -63,21 +63,33 @@ __device__ __forceinline__ int64_t ray_U0(const int4& t) {
   return ((int64_t)t.y << 32) | (int64_t)(uint32_t)t.x;
 }
 
-__global__ void build_rays2d_kernel(GeomDev g, int4* __restrict__ tab, float2* __restrict__ views) {
-  const int64_t m = (int64_t)g.V * g.A;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < g.V) {
-    const double ang = g.angle0 + g.span * (double)r / (double)g.V;
+// FP64 cos/sin of every view angle and (fan) every bin's fan angle.
+__global__ void trig_kernel(GeomDev g, double2* __restrict__ vtrig, double2* __restrict__ btrig) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < g.V) {
+    const double ang = g.angle0 + g.span * (double)i / (double)g.V;
     double s, c;
     sincos(ang, &s, &c);
-    views[r] = make_float2((float)c, (float)s);
+    vtrig[i] = make_double2(c, s);
   }
+  if (btrig && i < g.A) {
+    const double gam = ((double)i - 0.5 * (g.A - 1)) * g.du / g.sod;
+    double s, c;
+    sincos(gam, &s, &c);
+    btrig[i] = make_double2(c, s);
+  }
+}
+
+__global__ void build_rays2d_kernel(GeomDev g, const double2* __restrict__ vtrig,
+                                    const double2* __restrict__ btrig, int4* __restrict__ tab,
+                                    float2* __restrict__ views) {
+  const int64_t m = (int64_t)g.V * g.A;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < g.V) views[r] = make_float2((float)vtrig[r].x, (float)vtrig[r].y);
   if (r >= m) return;
   const int k = (int)(r / g.A), b = (int)(r % g.A);
   const double D = 2.0 / g.N;
-  const double ang = g.angle0 + g.span * (double)k / (double)g.V;
-  double sb, cb;
-  sincos(ang, &sb, &cb);
+  const double cb = vtrig[k].x, sb = vtrig[k].y;
   double px, py, ex, ey;
   if (g.kind == INRCT_PAR2D) {
     const double t = ((double)b - 0.5 * (g.A - 1)) * g.du * D;
@@ -87,9 +99,7 @@ __global__ void build_rays2d_kernel(GeomDev g, int4* __restrict__ tab, float2* _
     ey = cb;
   } else {
     const double R = g.sod * D;
-    const double gam = ((double)b - 0.5 * (g.A - 1)) * g.du / g.sod;
-    double sg, cg;
-    sincos(gam, &sg, &cg);
+    const double cg = btrig[b].x, sg = btrig[b].y;
     ex = -(cb * cg - sb * sg);
     ey = -(sb * cg + cb * sg);
     const double Sx = R * cb, Sy = R * sb;
@@ -108,22 +118,16 @@ __global__ void build_rays2d_kernel(GeomDev g, int4* __restrict__ tab, float2* _
   tab[r] = pack_ray(uref, slope, xd ? sc : -sc);
 }
 
-__global__ void build_cols3d_kernel(GeomDev g, int4* __restrict__ t0, int4* __restrict__ t1,
-                                    float* __restrict__ t2, float2* __restrict__ views) {
+__global__ void build_cols3d_kernel(GeomDev g, const double2* __restrict__ vtrig, int4* __restrict__ t0,
+                                    int4* __restrict__ t1, float* __restrict__ t2,
+                                    float2* __restrict__ views) {
   const int64_t cnt = (int64_t)g.V * g.A;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < g.V) {
-    const double ang = g.angle0 + g.span * (double)r / (double)g.V;
-    double s, c;
-    sincos(ang, &s, &c);
-    views[r] = make_float2((float)c, (float)s);
-  }
+  if (r < g.V) views[r] = make_float2((float)vtrig[r].x, (float)vtrig[r].y);
   if (r >= cnt) return;
   const int k = (int)(r / g.A), a = (int)(r % g.A);
   const double D = 2.0 / g.N;
-  const double ang = g.angle0 + g.span * (double)k / (double)g.V;
-  double sb, cb;
-  sincos(ang, &sb, &cb);
+  const double cb = vtrig[k].x, sb = vtrig[k].y;
   const double R = g.sod * D;
   const double pu = g.du * D * g.sdd / g.sod;
   const double pv = g.dv * D * g.sdd / g.sod;
@@ -577,56 +581,79 @@ int64_t num_rays(const inrct_geom* geom) {
   return (int64_t)geom->n_views * rows * geom->n_bins_u;
 }
 
-// Workspace: ray tables, view table, transposed image, loss partials.
+// Ray tables of one geometry (built per call, or once per grad_step and shared
+// by the projection and the adjoint).
+static void tables_layout(const inrct_geom* geom, Carver& c, ProjTables* t) {
+  const bool cone = geom->kind == INRCT_CONE3D;
+  const int64_t entries = cone ? (int64_t)geom->n_views * geom->n_bins_u : num_rays(geom);
+  t->tab0 = c.take<int4>(entries);
+  t->tab1 = cone ? c.take<int4>(entries) : nullptr;
+  t->tab2 = cone ? c.take<float>(entries) : nullptr;
+  t->views = c.take<float2>(geom->n_views);
+  t->vtrig = c.take<double2>(geom->n_views);
+  t->btrig = geom->kind == INRCT_FAN2D ? c.take<double2>(geom->n_bins_u) : nullptr;
+}
+
+size_t tables_bytes(const inrct_geom* geom) {
+  Carver c(nullptr, 0);
+  ProjTables t;
+  tables_layout(geom, c, &t);
+  return c.off + 256;
+}
+
+int build_tables(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes,
+                 ProjTables* t, cudaStream_t st) {
+  INRCT_TRY(check_geom(geom, grid));
+  Carver c(ws, ws_bytes);
+  tables_layout(geom, c, t);
+  if (!ws || !c.ok) {
+    set_error("ray tables: workspace of %zu bytes too small", ws_bytes);
+    return INRCT_ERR_WORKSPACE;
+  }
+  const GeomDev g = to_dev(geom, grid);
+  trig_kernel<<<ceil_div(std::max(g.V, g.A), 256), 256, 0, st>>>(g, t->vtrig, t->btrig);
+  INRCT_CHECK_LAUNCH("trig table");
+  const int64_t cnt = (int64_t)g.V * g.A;
+  if (g.kind == INRCT_CONE3D) {
+    build_cols3d_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(g, t->vtrig, t->tab0, t->tab1, t->tab2,
+                                                           t->views);
+  } else {
+    build_rays2d_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(g, t->vtrig, t->btrig, t->tab0, t->views);
+  }
+  INRCT_CHECK_LAUNCH("ray table");
+  return INRCT_OK;
+}
+
+// Per-call workspace: [ray tables unless given], transposed image (P only), loss partials (P only).
 struct ProjWs {
-  int4* tab0;
-  int4* tab1;
-  float* tab2;
-  float2* views;
+  ProjTables t;
   float* imgT;
   double* loss_part;
 };
 
 static size_t proj_layout(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t cap,
-                          ProjWs* out, bool want_transpose, bool* ok) {
+                          ProjWs* out, bool forward, bool with_tables, bool* ok) {
   Carver c(ws, cap);
   const bool cone = geom->kind == INRCT_CONE3D;
-  const int64_t entries = cone ? (int64_t)geom->n_views * geom->n_bins_u : num_rays(geom);
   ProjWs w;
-  w.tab0 = c.take<int4>(entries);
-  w.tab1 = cone ? c.take<int4>(entries) : nullptr;
-  w.tab2 = cone ? c.take<float>(entries) : nullptr;
-  w.views = c.take<float2>(geom->n_views);
-  w.imgT = want_transpose ? c.take<float>(grid_points(grid)) : nullptr;
+  if (with_tables) tables_layout(geom, c, &w.t);
+  w.imgT = forward ? c.take<float>(grid_points(grid)) : nullptr;
   const int64_t blocks = cone ? (int64_t)ceil_div(geom->n_bins_u, 32) * geom->n_bins_v * geom->n_views
                               : (int64_t)ceil_div(num_rays(geom), 32);
-  w.loss_part = c.take<double>(blocks);
+  w.loss_part = forward ? c.take<double>(blocks) : nullptr;
   if (out) *out = w;
   if (ok) *ok = c.ok;
   return c.off + 256;
 }
 
-size_t project_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
+size_t project_ws_bytes(const inrct_geom* geom, const inrct_grid* grid, bool with_tables) {
   if (check_geom(geom, grid) != INRCT_OK) return 0;
-  return proj_layout(geom, grid, nullptr, 0, nullptr, true, nullptr);
+  return proj_layout(geom, grid, nullptr, 0, nullptr, true, with_tables, nullptr);
 }
 
-size_t backproject_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
+size_t backproject_ws_bytes(const inrct_geom* geom, const inrct_grid* grid, bool with_tables) {
   if (check_geom(geom, grid) != INRCT_OK) return 0;
-  return proj_layout(geom, grid, nullptr, 0, nullptr, false, nullptr);
-}
-
-static int build_tables(const GeomDev& g, const ProjWs& w, cudaStream_t st) {
-  if (g.kind == INRCT_CONE3D) {
-    const int64_t cnt = (int64_t)g.V * g.A;
-    build_cols3d_kernel<<<ceil_div(cnt > g.V ? cnt : g.V, 256), 256, 0, st>>>(g, w.tab0, w.tab1,
-                                                                             w.tab2, w.views);
-  } else {
-    const int64_t cnt = (int64_t)g.V * g.A;
-    build_rays2d_kernel<<<ceil_div(cnt > g.V ? cnt : g.V, 256), 256, 0, st>>>(g, w.tab0, w.views);
-  }
-  INRCT_CHECK_LAUNCH("ray table");
-  return INRCT_OK;
+  return proj_layout(geom, grid, nullptr, 0, nullptr, false, with_tables, nullptr);
 }
 
 // Per-geometry cone constants shared by P and P^T: half the row pitch (world
@@ -639,19 +666,23 @@ static void cone_consts(const GeomDev& g, float* pv_half, int64_t* CzF) {
 
 int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
                  const float* y, float* resid, double* loss_out, void* ws, size_t ws_bytes,
-                 cudaStream_t st) {
+                 cudaStream_t st, const ProjTables* pre) {
   INRCT_TRY(check_geom(geom, grid));
   INRCT_REQUIRE(image && sino, "image and sino must not be NULL");
   INRCT_REQUIRE(!y || (resid && loss_out), "y given: resid and loss_out must not be NULL");
   ProjWs w;
   bool ok;
-  const size_t need = proj_layout(geom, grid, ws, ws_bytes, &w, true, &ok);
+  const size_t need = proj_layout(geom, grid, ws, ws_bytes, &w, true, pre == nullptr, &ok);
   if (!ws || !ok) {
     set_error("project: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
     return INRCT_ERR_WORKSPACE;
   }
   const GeomDev g = to_dev(geom, grid);
-  INRCT_TRY(build_tables(g, w, st));
+  if (pre) {
+    w.t = *pre;
+  } else {
+    INRCT_TRY(build_tables(geom, grid, ws, ws_bytes, &w.t, st));  // same offsets as the layout
+  }
   const int N = g.N;
   dim3 tb(32, 8);
   dim3 tg(ceil_div(N, 32), ceil_div(N, 32), g.kind == INRCT_CONE3D ? N : 1);
@@ -663,7 +694,7 @@ int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* im
     cone_consts(g, &pvh, &CzF);
     constexpr int SEG = 4;
     dim3 grd(ceil_div(g.A, 32), g.B, g.V);
-    project3d_kernel<SEG><<<grd, dim3(32, SEG), 0, st>>>(w.tab0, w.tab1, w.tab2, g.A, g.B, N, pvh,
+    project3d_kernel<SEG><<<grd, dim3(32, SEG), 0, st>>>(w.t.tab0, w.t.tab1, w.t.tab2, g.A, g.B, N, pvh,
                                                          CzF, image, w.imgT, sino, y, resid,
                                                          w.loss_part);
     INRCT_CHECK_LAUNCH("project3d");
@@ -675,7 +706,7 @@ int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* im
     constexpr int SEG = 8;
     const int64_t m = num_rays(geom);
     const unsigned nb = ceil_div(m, 32);
-    project2d_kernel<SEG><<<nb, dim3(32, SEG), 0, st>>>(w.tab0, (int)m, N, image, w.imgT, sino, y,
+    project2d_kernel<SEG><<<nb, dim3(32, SEG), 0, st>>>(w.t.tab0, (int)m, N, image, w.imgT, sino, y,
                                                         resid, w.loss_part);
     INRCT_CHECK_LAUNCH("project2d");
     if (y) {
@@ -687,18 +718,22 @@ int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* im
 }
 
 int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
-                     void* ws, size_t ws_bytes, cudaStream_t st) {
+                     void* ws, size_t ws_bytes, cudaStream_t st, const ProjTables* pre) {
   INRCT_TRY(check_geom(geom, grid));
   INRCT_REQUIRE(image && sino, "image and sino must not be NULL");
   ProjWs w;
   bool ok;
-  const size_t need = proj_layout(geom, grid, ws, ws_bytes, &w, false, &ok);
+  const size_t need = proj_layout(geom, grid, ws, ws_bytes, &w, false, pre == nullptr, &ok);
   if (!ws || !ok) {
     set_error("backproject: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
     return INRCT_ERR_WORKSPACE;
   }
   const GeomDev g = to_dev(geom, grid);
-  INRCT_TRY(build_tables(g, w, st));
+  if (pre) {
+    w.t = *pre;
+  } else {
+    INRCT_TRY(build_tables(geom, grid, ws, ws_bytes, &w.t, st));  // same offsets as the layout
+  }
   const size_t shm = sizeof(float2) * g.V;
   if (g.kind == INRCT_CONE3D) {
     float pvh;
@@ -707,13 +742,13 @@ int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float
     constexpr int ZC = 8;
     dim3 blk(32, 4);
     dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, ZC));
-    backproject3d_kernel<ZC><<<grd, blk, shm, st>>>(g, w.tab0, w.tab1, w.tab2, w.views, pvh, CzF,
+    backproject3d_kernel<ZC><<<grd, blk, shm, st>>>(g, w.t.tab0, w.t.tab1, w.t.tab2, w.t.views, pvh, CzF,
                                                     sino, image);
     INRCT_CHECK_LAUNCH("backproject3d");
   } else {
     dim3 blk(32, 8);
     dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 8));
-    backproject2d_kernel<<<grd, blk, shm, st>>>(g, w.tab0, w.views, sino, image);
+    backproject2d_kernel<<<grd, blk, shm, st>>>(g, w.t.tab0, w.t.views, sino, image);
     INRCT_CHECK_LAUNCH("backproject2d");
   }
   return INRCT_OK;

@@ -10,14 +10,28 @@ struct GeomDev {
   double du, dv, sod, sdd, angle0, span;
 };
 
+// Ray tables of one geometry (see projector.cu).
+struct ProjTables {
+  int4* tab0;
+  int4* tab1;
+  float* tab2;
+  float2* views;
+  double2* vtrig;
+  double2* btrig;
+};
+
 int check_geom(const inrct_geom* geom, const inrct_grid* grid);
+size_t tables_bytes(const inrct_geom* geom);
+int build_tables(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes,
+                 ProjTables* t, cudaStream_t st);
 int64_t num_rays(const inrct_geom* geom);
-size_t project_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
-size_t backproject_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
+// Workspace of one call; with_tables = false when the caller passes prebuilt tables.
+size_t project_ws_bytes(const inrct_geom* geom, const inrct_grid* grid, bool with_tables = true);
+size_t backproject_ws_bytes(const inrct_geom* geom, const inrct_grid* grid, bool with_tables = true);
 int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
                  const float* y, float* resid, double* loss_out, void* ws, size_t ws_bytes,
-                 cudaStream_t st);
+                 cudaStream_t st, const ProjTables* pre = nullptr);
 int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
-                     void* ws, size_t ws_bytes, cudaStream_t st);
+                     void* ws, size_t ws_bytes, cudaStream_t st, const ProjTables* pre = nullptr);
 
 }  // namespace inrct

@@ -181,16 +181,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+  if constexpr (CW == 32) {
+    tmem_ld32(taddr, v);
+  } else {
+    static_assert(CW == 16, "16 or 32 columns");
+    tmem_ld16(taddr, v);
+  }
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
 }
 
-// Writes 32 BF16 values (columns 8*j0 .. 8*j0+31 of a 64-column K-major panel row r).
-__device__ __forceinline__ void st_panel_row32(uint8_t* panel, int r, int j0, const float* v) {
+// Writes CW BF16 values (columns 8*j0 .. 8*j0+CW-1 of a 64-column K-major panel row r).
+template <int CW>
+__device__ __forceinline__ void st_panel_row(uint8_t* panel, int r, int j0, const float* v) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < CW / 8; ++q) {
     const int j = j0 + q;
     uint4 w;
     w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
