@@ -141,6 +141,32 @@ int project(const inrct_geom* geom, const inrct_grid* grid, const float* image, 
             cudaStream_t stream);
 
 /*
+ * project_noalloc -- the same projection and optional LS-loss epilogue as
+ * project(), for callers that cannot allocate device memory: for example an
+ * application whose device memory belongs to another framework's pool
+ * allocator, or a scanner-side loop that reserves all memory at start-up and
+ * may not allocate afterwards.  The paper has no counterpart; this is a
+ * calling convention of this library only.
+ *   The scratch lives in one static device array of INRCT_NOALLOC_SCRATCH_BYTES
+ *   bytes inside the library, which every GPU that loads the library keeps
+ *   until the process exits.  The call allocates nothing: the caller passes
+ *   image, sino (and y, resid, loss_out) exactly as for project().
+ *   A geometry whose scratch (inrct_project_ws_bytes) exceeds the array is
+ *   rejected with INRCT_ERR_WORKSPACE before anything is launched (2-D
+ *   geometries up to about 1400^2 pixels fit; most 3-D ones do not).
+ *   The first call on a device looks up the array's device address on that
+ *   device (the device that is current at the call); make that first call
+ *   before any stream capture.  All calls on a device share the one array:
+ *   calls whose work overlaps on the GPU (different streams, or host threads
+ *   without ordering) race on it and must be serialised by the caller.  The
+ *   array keeps the last call's contents; each call writes every scratch byte
+ *   it later reads, so no clearing is needed.
+ */
+#define INRCT_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int project_noalloc(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
+                    const float* y, float* resid, double* loss_out, cudaStream_t stream);
+
+/*
  * backproject -- v = P^T r (Sec. 3, v = P^T r; Algorithm 1, step 2), the exact
  * adjoint of project (same interpolation weights), in gather form: every
  * pixel sums its own contributions, so the result is deterministic.

@@ -112,6 +112,12 @@ int project(const inrct_geom* geom, const inrct_grid* grid, const float* image, 
   return project_impl(geom, grid, image, sino, y, resid, loss_out, ws, ws_bytes, stream);
 }
 
+int project_noalloc(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
+                    const float* y, float* resid, double* loss_out, cudaStream_t stream) {
+  clear_error();
+  return project_noalloc_impl(geom, grid, image, sino, y, resid, loss_out, stream);
+}
+
 size_t inrct_backproject_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
   return backproject_ws_bytes(geom, grid);
 }

@@ -27,6 +27,8 @@
 //   table and sums locally: deterministic, no atomics.
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "projector.cuh"
 
@@ -752,6 +754,65 @@ int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float
     INRCT_CHECK_LAUNCH("backproject2d");
   }
   return INRCT_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free projection
+//
+// For callers that must not allocate device memory themselves: for example a
+// host application whose device memory is owned by another framework's pool
+// (a cudaMalloc behind its back would break its budget or fragment it), or a
+// reconstruction loop on a scanner that reserves all memory once at start-up
+// and allows no allocation afterwards.  The projection's scratch (ray tables,
+// transposed image, loss partials) then lives in one file-scope device array
+// of fixed size, which every GPU that loads this library holds until the
+// process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_project_scratch[INRCT_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_project_scratch_mu;
+static void* g_project_scratch_addr[256] = {};  // device address of the array, per device ordinal
+
+// Device address of the array on the current device, looked up once per device
+// (host code cannot use the array's name as a device pointer).
+static int project_scratch_address(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    set_error("project_noalloc: no usable current device (%s)", cudaGetErrorString(e));
+    return INRCT_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_project_scratch_mu);
+  if (!g_project_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_project_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("project_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return INRCT_ERR_CUDA;
+    }
+    g_project_scratch_addr[dev] = p;
+  }
+  *out = g_project_scratch_addr[dev];
+  return INRCT_OK;
+}
+
+int project_noalloc_impl(const inrct_geom* geom, const inrct_grid* grid, const float* image,
+                         float* sino, const float* y, float* resid, double* loss_out, cudaStream_t st) {
+  INRCT_TRY(check_geom(geom, grid));
+  const size_t need = project_ws_bytes(geom, grid);
+  if (need > (size_t)INRCT_NOALLOC_SCRATCH_BYTES) {
+    set_error("project_noalloc: this geometry needs %zu bytes of scratch, more than the %zu-byte "
+              "static buffer; use project() with a caller-provided workspace",
+              need, (size_t)INRCT_NOALLOC_SCRATCH_BYTES);
+    return INRCT_ERR_WORKSPACE;
+  }
+  void* ws = nullptr;
+  INRCT_TRY(project_scratch_address(&ws));
+  // every byte of scratch the projection reads is written earlier in the same call
+  // (tables, transposed image, loss partials), so nothing needs clearing
+  return project_impl(geom, grid, image, sino, y, resid, loss_out, ws,
+                      (size_t)INRCT_NOALLOC_SCRATCH_BYTES, st);
 }
 
 }  // namespace inrct

@@ -33,5 +33,7 @@ int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* im
                  cudaStream_t st, const ProjTables* pre = nullptr);
 int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
                      void* ws, size_t ws_bytes, cudaStream_t st, const ProjTables* pre = nullptr);
+int project_noalloc_impl(const inrct_geom* geom, const inrct_grid* grid, const float* image,
+                         float* sino, const float* y, float* resid, double* loss_out, cudaStream_t st);
 
 }  // namespace inrct

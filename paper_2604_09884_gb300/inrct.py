@@ -78,6 +78,7 @@ def lib():
         "inrct_num_rays": ([g], _I64),
         "inrct_project_ws_bytes": ([g, gr], _SZ),
         "project": ([g, gr, _P, _P, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+        "project_noalloc": ([g, gr, _P, _P, _P, _P, _P, _P], ctypes.c_int),
         "inrct_backproject_ws_bytes": ([g, gr], _SZ),
         "backproject": ([g, gr, _P, _P, _P, _SZ, _P], ctypes.c_int),
         "inrct_ramp_ws_bytes": ([g, gr], _SZ),
@@ -186,6 +187,21 @@ def project(g: synth.GeomSpec, image: torch.Tensor, y: torch.Tensor | None = Non
     ws = _ws(nb, dev)
     _check(L.project(ctypes.byref(gd), ctypes.byref(grd), _ptr(image, torch.float32), _ptr(z),
                      _ptr(y, torch.float32), _ptr(r), _ptr(loss), _ptr(ws), nb, _stream(stream)))
+    return z if y is None else (z, r, loss)
+
+
+def project_noalloc(g: synth.GeomSpec, image: torch.Tensor, y: torch.Tensor | None = None,
+                    stream=None):
+    """project() without a caller workspace: the library's fixed static scratch is used.
+    For callers that may not allocate device scratch; the outputs are still the caller's."""
+    L = lib()
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    dev = image.device
+    z = torch.empty(g.m, dtype=torch.float32, device=dev)
+    r = torch.empty(g.m, dtype=torch.float32, device=dev) if y is not None else None
+    loss = torch.empty(1, dtype=torch.float64, device=dev) if y is not None else None
+    _check(L.project_noalloc(ctypes.byref(gd), ctypes.byref(grd), _ptr(image, torch.float32), _ptr(z),
+                             _ptr(y, torch.float32), _ptr(r), _ptr(loss), _stream(stream)))
     return z if y is None else (z, r, loss)
 
 
