@@ -47,7 +47,9 @@ using namespace tc;
 namespace {
 
 constexpr int kTile = 128;       // points per tile (MMA M)
-constexpr int kRing = 4;         // weight ring slots
+constexpr int kNSplit = 1;       // MMA N-groups per weight K-panel: N = W / kNSplit
+constexpr int kRingBytes = 64 * 1024;  // weight ring: kRingBytes / (W / kNSplit * 128 B) slots
+constexpr int kRingMax = 8;
 constexpr int kPanelBytes = kTile * 128;  // one 64-column BF16 panel of 128 rows
 constexpr int kMaxStages = 2 * kMaxLayers;
 constexpr int kMaxJobs = 24;
@@ -420,6 +422,24 @@ __host__ __device__ inline size_t param_floats(int L, int W, int F, int kind) {
   return (size_t)L * W + W + 4 * (size_t)(kind == INRCT_SIREN ? W : F);
 }
 
+// Two tiles are in flight per CTA (slots 0 and 1), each with one FP32 accumulator of
+// W TMEM columns and its own four input panels.  The MMA issuer alternates the slots
+// stage by stage, (slot 0, stage s), (slot 1, stage s), (slot 0, stage s+1), ..., so
+// that while the epilogue works on one slot the tensor core works on the other.
+// Weights go through a ring of chunks of NW = W / kNSplit rows x 64 K (128B swizzle);
+// each K-panel of a stage is kNSplit MMA groups of N = NW.  N = W = 256 runs the tensor
+// core at its peak; N = 128 needs twice the MMA instructions from the single issuing
+// thread and falls behind when the epilogue warps keep its SMSP busy.
+//
+// Hand-off per slot and stage: the epilogue waits for acc_full[t] (every MMA of the
+// stage has completed, so the slot's input panels are free as well), reads the
+// accumulator, writes the next stage's input panels and arrives once per warp on
+// in_ready[t], which the MMA issuer waits for before the slot's next stage: one
+// arrival means both "accumulator drained" and "next input written".  Only the
+// first stage may have more than four input panels (Fourier features, 2F > 256);
+// those are streamed through the four panel buffers with per-panel barriers
+// (a_full: written, a_empty: read by the MMA).
+//
 // NWG epilogue warpgroups; each thread of warpgroup g owns CW = 64/NWG columns of
 // every 64-column chunk of its TMEM lane (row).
 template <int MODE, int KIND, int NWG>
@@ -429,35 +449,40 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   extern __shared__ __align__(1024) uint8_t dsm[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
   const int W = P.W;
-  uint8_t* apan = smem;                      // 4 x 16 KB input panels
-  uint8_t* ring = smem + 4 * kPanelBytes;    // kRing x (W x 128 B) weight chunks
-  float* bias_s = reinterpret_cast<float*>(ring + (size_t)kRing * W * 128);
+  uint8_t* apan = smem;                          // 2 slots x 4 x 16 KB input panels
+  const int NW = W / kNSplit;                    // MMA N and weight rows per ring slot
+  uint8_t* ring = smem + 8 * kPanelBytes;        // n_ring x (NW x 128 B) weight chunks
+  const uint32_t chunk_bytes = (uint32_t)NW * 128;
+  const int n_ring = kRingBytes / (int)chunk_bytes;
+  float* bias_s = reinterpret_cast<float*>(ring + kRingBytes);
   float* wout_s = bias_s + (size_t)P.L * W;
   float4* first_s = reinterpret_cast<float4*>(wout_s + W);
-  __shared__ uint64_t w_full[kRing], w_empty[kRing], a_full[4], a_empty[4], acc_full[2], acc_empty[2],
-      dot_bar, drain_bar;
-  constexpr int CW = 64 / NWG, EPI = 128 * NWG;
-  __shared__ float dotp[NWG][kTile];
+  constexpr int CW = 64 / NWG, EPI_WARPS = 4 * NWG;  // one arrival per epilogue warp
+  __shared__ uint64_t w_full[kRingMax], w_empty[kRingMax], in_ready[2], acc_full[2], a_full[2][4],
+      a_empty[2][4], dot_bar[2][4], drain_bar;
+  __shared__ float dotp[2][NWG][kTile];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t chunk_bytes = (uint32_t)W * 128;
   const int64_t n_tiles = (P.npts + kTile - 1) / kTile;
+  // this CTA's tiles are blockIdx.x + j * gridDim.x; they are taken in pairs (slot 0, slot 1)
+  const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t n_pairs = (my_tiles + 1) / 2;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kRing; ++s) {
+    for (int s = 0; s < n_ring; ++s) {
       mbar_init(&w_full[s], 1);
       mbar_init(&w_empty[s], 1);
     }
-    for (int s = 0; s < 4; ++s) {
-      mbar_init(&a_full[s], EPI);
-      mbar_init(&a_empty[s], 1);
+    for (int t = 0; t < 2; ++t) {
+      mbar_init(&in_ready[t], EPI_WARPS);
+      mbar_init(&acc_full[t], 1);
+      for (int s = 0; s < 4; ++s) {
+        mbar_init(&a_full[t][s], EPI_WARPS);
+        mbar_init(&a_empty[t][s], 1);
+        mbar_init(&dot_bar[t][s], NWG);
+      }
     }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], EPI);
-    }
-    mbar_init(&dot_bar, EPI);
     mbar_init(&drain_bar, 1);
     abort_flag = 0;
     fence_mbar_init();
@@ -488,15 +513,19 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     if (lane == 0 && !P.stall) {
       for (int s = 0; s < P.n_stages; ++s) prefetch_map(&maps.m[P.st_map[s]]);
       uint32_t slot = 0, ep = 1;
-      for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      for (int64_t pr = 0; pr < n_pairs; ++pr) {
         for (int s = 0; s < P.n_stages; ++s) {
-          for (int c = 0; c < P.st_panels[s]; ++c) {
-            if (!mbar_wait(&w_empty[slot], ep, &abort_flag, err, 201)) goto producer_done;
-            mbar_arrive_expect_tx(&w_full[slot], chunk_bytes);
-            tma_load_2d(ring + slot * chunk_bytes, &maps.m[P.st_map[s]], &w_full[slot], 64 * c, 0);
-            if (++slot == kRing) {
-              slot = 0;
-              ep ^= 1;
+          for (int t = 0; t < 2; ++t) {
+            for (int c = 0; c < P.st_panels[s]; ++c) {
+              for (int h = 0; h < kNSplit; ++h) {
+                if (!mbar_wait(&w_empty[slot], ep, &abort_flag, err, 201)) goto producer_done;
+                mbar_arrive_expect_tx(&w_full[slot], chunk_bytes);
+                tma_load_2d(ring + slot * chunk_bytes, &maps.m[P.st_map[s]], &w_full[slot], 64 * c, h * NW);
+                if (++slot == n_ring) {
+                  slot = 0;
+                  ep ^= 1;
+                }
+              }
             }
           }
         }
@@ -506,39 +535,46 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   } else if (warp == 4 * NWG + 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      // phase parities of the barriers, one bit per slot
-      uint32_t slot = 0, wf = 0, aep = 3u, acc_ctr = 0, ap = 0u;
-      const uint32_t idesc = idesc_bf16(128, W, false, false);
+      // phase parities: ring, in_ready (one bit per slot), a_full (one bit per slot and buffer)
+      uint32_t slot = 0, wf = 0, irp = 0u, ap = 0u;
+      const uint32_t idesc = idesc_bf16(128, NW, false, false);
       bool issued = false;
-      for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      for (int64_t pr = 0; pr < n_pairs; ++pr) {
         for (int s = 0; s < P.n_stages; ++s) {
-          const uint32_t b = acc_ctr & 1;
-          if (!mbar_wait(&acc_empty[b], (aep >> b) & 1u, &abort_flag, err, 301)) goto mma_done;
-          aep ^= 1u << b;
-          tc_fence_after();
-          const uint32_t dcol = tmem + b * W;
-          for (int c = 0; c < P.st_panels[s]; ++c) {
-            const int as = c & 3;
-            if (!mbar_wait(&a_full[as], (ap >> as) & 1u, &abort_flag, err, 302)) goto mma_done;
-            ap ^= 1u << as;
-            if (!mbar_wait(&w_full[slot], wf, &abort_flag, err, 303)) goto mma_done;
+          for (int t = 0; t < 2; ++t) {
+            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, &abort_flag, err, 301)) goto mma_done;
+            irp ^= 1u << t;
             tc_fence_after();
-            const uint32_t abase = smem_u32(apan + as * kPanelBytes);
-            const uint32_t bbase = smem_u32(ring + slot * chunk_bytes);
+            const int np = P.st_panels[s];
+            for (int c = 0; c < np; ++c) {
+              const int as = c & 3;
+              if (c >= 4) {  // a streamed input panel (first stage only)
+                const int bit = 4 * t + as;
+                if (!mbar_wait(&a_full[t][as], (ap >> bit) & 1u, &abort_flag, err, 302)) goto mma_done;
+                ap ^= 1u << bit;
+                tc_fence_after();
+              }
+              const uint32_t abase = smem_u32(apan + (4 * t + as) * kPanelBytes);
+              for (int h = 0; h < kNSplit; ++h) {
+                if (!mbar_wait(&w_full[slot], wf, &abort_flag, err, 303)) goto mma_done;
+                tc_fence_after();
+                const uint32_t bbase = smem_u32(ring + slot * chunk_bytes);
+                const uint32_t dcol = tmem + t * W + h * NW;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              mma_bf16(dcol, desc_sw128(abase + 32 * j, 16, 1024), desc_sw128(bbase + 32 * j, 16, 1024),
-                       idesc, (c > 0 || j > 0) ? 1u : 0u);
-            issued = true;
-            mma_commit(&w_empty[slot]);
-            mma_commit(&a_empty[as]);
-            if (++slot == kRing) {
-              slot = 0;
-              wf ^= 1;
+                for (int j = 0; j < 4; ++j)
+                  mma_bf16(dcol, desc_sw128(abase + 32 * j, 16, 1024),
+                           desc_sw128(bbase + 32 * j, 16, 1024), idesc, (c > 0 || j > 0) ? 1u : 0u);
+                issued = true;
+                mma_commit(&w_empty[slot]);
+                if (++slot == n_ring) {
+                  slot = 0;
+                  wf ^= 1;
+                }
+              }
+              if (c + 4 < np) mma_commit(&a_empty[t][as]);  // the buffer takes panel c + 4 next
             }
+            mma_commit(&acc_full[t]);
           }
-          mma_commit(&acc_full[b]);
-          ++acc_ctr;
         }
       }
     mma_done:
@@ -554,159 +590,217 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     const int q = warp & 3, g = warp >> 2;
     const int r = q * 32 + lane;                 // row of the tile = TMEM lane
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    uint32_t ae = 0xFu, af = 0u, dotph = 0, acc_ctr = 0;  // phase parities, one bit per slot
+    uint32_t ae = 0u, af = 0u, dotph = 0u;       // phase parities (a_empty per slot and buffer; per slot)
     const float bout = P.theta[P.offbout];
+    const int n0 = P.in_panels < 4 ? P.in_panels : 4;  // first-stage panels published together
     float v[CW];
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-      const int64_t pt = t * kTile + r;
-      const bool valid = pt < P.npts;
-      int64_t gi = valid ? (P.idx ? (int64_t)P.idx[pt] : pt) : 0;
-      const bool in_range = gi >= 0 && gi < P.n_grid;
-      if (!in_range) gi = 0;
-      float x[3];
-      point_coords(gi, P.N, P.d, x);
-      const float sv = (MODE == 1 && valid && in_range) ? P.scale * P.v[gi] : 0.f;
-      const int64_t prow = t * kTile + r;        // scratch row (rows are padded to the tile)
-      // ---- first stage input ----
-      for (int c = 0; c < P.in_panels; ++c) {
-        const int col0 = 64 * c + CW * g;
-        if (KIND == INRCT_FFN_RELU) {
-          const bool is_sin = col0 >= P.F;
-          const int f0 = is_sin ? col0 - P.F : col0;
-#pragma unroll
-          for (int i = 0; i < CW; ++i) {
-            const float4 bf = first_s[f0 + i];
-            float ph = __fadd_rn(__fmul_rn(bf.x, x[0]), __fmul_rn(bf.y, x[1]));
-            if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, x[2]));
-            v[i] = four_feat(ph, is_sin);
-          }
-          if (MODE == 1) store_row_bf16<CW>(P.E + prow * (2 * P.F) + col0, v);
-        } else {
-          float cs[CW];
-#pragma unroll
-          for (int i = 0; i < CW; ++i) {
-            const float4 w1 = first_s[col0 + i];
-            const float z = fmaf(w1.x, x[0], fmaf(w1.y, x[1], fmaf(w1.z, x[2], w1.w)));
-            if (MODE == 1)
-              __sincosf(z, &v[i], &cs[i]);
-            else
-              v[i] = __sinf(z);
-          }
-          if (MODE == 1) {
-            store_row_bf16<CW>(P.Act + prow * W + col0, v);
-            store_row_bf16<CW>(P.Cos + prow * W + col0, cs);
-            if (c == 0 && g == 0) {
-#pragma unroll
-              for (int k = 0; k < 3; ++k)
-                if (k < P.d) P.Y16c[(int64_t)k * P.npts_pad + prow] = __float2bfloat16_rn(x[k]);
-            }
-          }
-        }
-        const int as = c & 3;
-        if (!warp_wait(&a_empty[as], (ae >> as) & 1u, &abort_flag, err, 401)) goto epi_done;
-        ae ^= 1u << as;
-        st_panel_row<CW>(apan + as * kPanelBytes, r, (CW / 8) * g, v);
-        fence_async_smem();
-        mbar_arrive(&a_full[as]);
+    for (int64_t pr = 0; pr < n_pairs; ++pr) {
+      // per-slot point data, kept in scalars (slot t selects with a conditional)
+      const int64_t tile0 = blockIdx.x + (2 * pr) * (int64_t)gridDim.x;
+      const int64_t tile1 = tile0 + gridDim.x;  // may be past the end: a dummy tile
+      float x0[3], x1[3], sv0, sv1;
+      bool valid0, valid1;
+      {
+        auto setup = [&](int64_t tile, float* x, float& sv, bool& valid) {
+          const int64_t pt = tile * kTile + r;
+          valid = pt < P.npts;
+          int64_t gi = valid ? (P.idx ? (int64_t)P.idx[pt] : pt) : 0;
+          const bool in_range = gi >= 0 && gi < P.n_grid;
+          if (!in_range) gi = 0;
+          point_coords(gi, P.N, P.d, x);
+          sv = (MODE == 1 && valid && in_range) ? P.scale * P.v[gi] : 0.f;
+        };
+        setup(tile0, x0, sv0, valid0);
+        setup(tile1, x1, sv1, valid1);
       }
-      // ---- GEMM stages ----
-      for (int s = 0; s < P.n_stages; ++s) {
-        const uint32_t b = acc_ctr & 1;
-        if (!warp_wait(&acc_full[b], (af >> b) & 1u, &abort_flag, err, 402)) goto epi_done;
-        af ^= 1u << b;
-        tc_fence_after();
-        const int kind = P.st_kind[s], l = P.st_layer[s];
-        const bool write_panel = s + 1 < P.n_stages;  // the next stage's input
-        float dot = 0.f;
-        for (int c = 0; c < W / 64; ++c) {
+      // ---- first stage input of both slots ----
+      for (int t = 0; t < 2; ++t) {
+        const int64_t prow_t = (t ? tile1 : tile0) * kTile + r;  // scratch row (padded to the tile)
+        const bool store_t = (t ? tile1 : tile0) < n_tiles;      // dummy tiles write nowhere
+        const float xt[3] = {t ? x1[0] : x0[0], t ? x1[1] : x0[1], t ? x1[2] : x0[2]};
+        for (int c = 0; c < P.in_panels; ++c) {
           const int col0 = 64 * c + CW * g;
-          tmem_ld<CW>(tmem + lane_off + b * W + col0, v);
-          if (MODE == 1 && kind == kBwd) {
-            // v = (W'_l^T delta_l) for layer l; delta_{l-1} = v * sigma'(u_{l-1})
-            float sg[CW];
-            if (KIND == INRCT_FFN_RELU) {
-              load_row_bf16<CW>(P.Act + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
+          if (KIND == INRCT_FFN_RELU) {
+            const bool is_sin = col0 >= P.F;
+            const int f0 = is_sin ? col0 - P.F : col0;
 #pragma unroll
-              for (int i = 0; i < CW; ++i) v[i] = sg[i] > 0.f ? v[i] : 0.f;
-            } else {
-              load_row_bf16<CW>(P.Cos + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, sg);
-#pragma unroll
-              for (int i = 0; i < CW; ++i) v[i] *= sg[i];
+            for (int i = 0; i < CW; ++i) {
+              const float4 bf = first_s[f0 + i];
+              float ph = __fadd_rn(__fmul_rn(bf.x, xt[0]), __fmul_rn(bf.y, xt[1]));
+              if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, xt[2]));
+              v[i] = four_feat(ph, is_sin);
             }
-            store_row_bf16<CW>(P.Dlt + ((int64_t)(l - 1) * P.npts_pad + prow) * W + col0, v);
+            if (MODE == 1 && store_t) store_row_bf16<CW>(P.E + prow_t * (2 * P.F) + col0, v);
           } else {
-            const float4* bl = reinterpret_cast<const float4*>(bias_s + (size_t)l * W + col0);
             float cs[CW];
 #pragma unroll
-            for (int i4 = 0; i4 < CW / 4; ++i4) {
-              const float4 bb = bl[i4];
-              const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                const int i = 4 * i4 + k;
-                const float z = v[i] + bq[k];
-                if (KIND == INRCT_FFN_RELU) {
-                  v[i] = fmaxf(z, 0.f);
-                  if (MODE == 1) cs[i] = z > 0.f ? 1.f : 0.f;
-                } else if (MODE == 1) {
-                  __sincosf(z, &v[i], &cs[i]);
-                } else {
-                  v[i] = __sinf(z);
-                }
-              }
+            for (int i = 0; i < CW; ++i) {
+              const float4 w1 = first_s[col0 + i];
+              const float z = fmaf(w1.x, xt[0], fmaf(w1.y, xt[1], fmaf(w1.z, xt[2], w1.w)));
+              if (MODE == 1)
+                __sincosf(z, &v[i], &cs[i]);
+              else
+                v[i] = __sinf(z);
             }
-            if (MODE == 1) {
-              store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
-              if (KIND == INRCT_SIREN && kind == kFwdHidden)
-                store_row_bf16<CW>(P.Cos + ((int64_t)l * P.npts_pad + prow) * W + col0, cs);
-            }
-            if (kind == kFwdLast) {
-              const float4* wo = reinterpret_cast<const float4*>(wout_s + col0);
-              if (MODE == 0) {
+            if (MODE == 1 && store_t) {
+              store_row_bf16<CW>(P.Act + prow_t * W + col0, v);
+              store_row_bf16<CW>(P.Cos + prow_t * W + col0, cs);
+              if (c == 0 && g == 0) {
 #pragma unroll
-                for (int i4 = 0; i4 < CW / 4; ++i4) {
-                  const float4 ww = wo[i4];
-                  dot = fmaf(v[4 * i4], ww.x, dot);
-                  dot = fmaf(v[4 * i4 + 1], ww.y, dot);
-                  dot = fmaf(v[4 * i4 + 2], ww.z, dot);
-                  dot = fmaf(v[4 * i4 + 3], ww.w, dot);
-                }
-              } else {
-                // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
-#pragma unroll
-                for (int i4 = 0; i4 < CW / 4; ++i4) {
-                  const float4 ww = wo[i4];
-                  v[4 * i4] = sv * ww.x * cs[4 * i4];
-                  v[4 * i4 + 1] = sv * ww.y * cs[4 * i4 + 1];
-                  v[4 * i4 + 2] = sv * ww.z * cs[4 * i4 + 2];
-                  v[4 * i4 + 3] = sv * ww.w * cs[4 * i4 + 3];
-                }
-                store_row_bf16<CW>(P.Dlt + ((int64_t)l * P.npts_pad + prow) * W + col0, v);
-                if (c == 0 && g == 0) P.Y16o[prow] = __float2bfloat16_rn(sv);
+                for (int k = 0; k < 3; ++k)
+                  if (k < P.d) P.Y16c[(int64_t)k * P.npts_pad + prow_t] = __float2bfloat16_rn(xt[k]);
               }
             }
           }
-          if (write_panel) {
-            if (!warp_wait(&a_empty[c], (ae >> c) & 1u, &abort_flag, err, 403)) goto epi_done;
-            ae ^= 1u << c;
-            st_panel_row<CW>(apan + c * kPanelBytes, r, (CW / 8) * g, v);
+          const int as = c & 3;
+          if (c >= 4) {  // streamed panel: the MMA must have read panel c - 4 from this buffer
+            const int bit = 4 * t + as;
+            if (!warp_wait(&a_empty[t][as], (ae >> bit) & 1u, &abort_flag, err, 401)) goto epi_done;
+            ae ^= 1u << bit;
+          }
+          st_panel_row<CW>(apan + (4 * t + as) * kPanelBytes, r, (CW / 8) * g, v);
+          if (c == n0 - 1) {
+            // panels 0 .. n0-1 written and (program order) this slot's accumulator drained
             fence_async_smem();
-            mbar_arrive(&a_full[c]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&in_ready[t]);
+          } else if (c >= 4) {
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[t][as]);
           }
         }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[b]);
-        ++acc_ctr;
-        if (MODE == 0 && kind == kFwdLast) {
-          dotp[g][r] = dot;
-          mbar_arrive(&dot_bar);
-          if (!warp_wait(&dot_bar, dotph, &abort_flag, err, 404)) goto epi_done;
-          dotph ^= 1;
-          if (g == 0 && valid) {
-            float f = bout;
+      }
+      // ---- GEMM stages, alternating slots ----
+      for (int s = 0; s < P.n_stages; ++s) {
+        const int kind = P.st_kind[s], l = P.st_layer[s];
+        const bool write_panel = s + 1 < P.n_stages;  // the next stage's input
+        for (int t = 0; t < 2; ++t) {
+          const int64_t prow_t = (t ? tile1 : tile0) * kTile + r;
+          const bool store_t = (t ? tile1 : tile0) < n_tiles;
+          const bool valid_t = t ? valid1 : valid0;
+          const float sv_t = t ? sv1 : sv0;
+          const bool bwd = MODE == 1 && kind == kBwd;
+          // backward: sigma'(u_{l-1}) rows of this tile; chunk c + 1 is fetched while chunk c is
+          // processed, chunk 0 before the wait for the accumulator (a dummy tile reads nothing)
+          const __nv_bfloat16* sg_row =
+              (KIND == INRCT_FFN_RELU ? P.Act : P.Cos) + ((int64_t)(l - 1) * P.npts_pad + prow_t) * W;
+          uint4 sgn[CW / 8];
+          if (bwd) {
 #pragma unroll
-            for (int q2 = 0; q2 < NWG; ++q2) f += dotp[q2][r];
-            P.out[pt] = f;
+            for (int k = 0; k < CW / 8; ++k)
+              sgn[k] = store_t ? reinterpret_cast<const uint4*>(sg_row + CW * g)[k] : make_uint4(0, 0, 0, 0);
+          }
+          if (!warp_wait(&acc_full[t], (af >> t) & 1u, &abort_flag, err, 402)) goto epi_done;
+          af ^= 1u << t;
+          tc_fence_after();
+          float dot = 0.f;
+          for (int c = 0; c < W / 64; ++c) {
+            const int col0 = 64 * c + CW * g;
+            tmem_ld<CW>(tmem + lane_off + t * W + col0, v);
+            if (bwd) {
+              // v = (W'_l^T delta_l) for layer l; delta_{l-1} = v * sigma'(u_{l-1})
+              float sg[CW];
+#pragma unroll
+              for (int k = 0; k < CW / 8; ++k) {
+                const uint32_t u[4] = {sgn[k].x, sgn[k].y, sgn[k].z, sgn[k].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  sg[8 * k + 2 * e] = __uint_as_float(u[e] << 16);
+                  sg[8 * k + 2 * e + 1] = __uint_as_float(u[e] & 0xffff0000u);
+                }
+              }
+              if (c + 1 < W / 64) {
+#pragma unroll
+                for (int k = 0; k < CW / 8; ++k)
+                  sgn[k] = store_t ? reinterpret_cast<const uint4*>(sg_row + col0 + 64)[k]
+                                   : make_uint4(0, 0, 0, 0);
+              }
+              if (KIND == INRCT_FFN_RELU) {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] = sg[i] > 0.f ? v[i] : 0.f;
+              } else {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] *= sg[i];
+              }
+              if (store_t)
+                store_row_bf16<CW>(P.Dlt + ((int64_t)(l - 1) * P.npts_pad + prow_t) * W + col0, v);
+            } else {
+              const float4* bl = reinterpret_cast<const float4*>(bias_s + (size_t)l * W + col0);
+              float cs[CW];
+#pragma unroll
+              for (int i4 = 0; i4 < CW / 4; ++i4) {
+                const float4 bb = bl[i4];
+                const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  const int i = 4 * i4 + k;
+                  const float z = v[i] + bq[k];
+                  if (KIND == INRCT_FFN_RELU) {
+                    v[i] = fmaxf(z, 0.f);
+                    if (MODE == 1) cs[i] = z > 0.f ? 1.f : 0.f;
+                  } else if (MODE == 1) {
+                    __sincosf(z, &v[i], &cs[i]);
+                  } else {
+                    v[i] = __sinf(z);
+                  }
+                }
+              }
+              if (MODE == 1 && store_t) {
+                store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
+                if (KIND == INRCT_SIREN && kind == kFwdHidden)
+                  store_row_bf16<CW>(P.Cos + ((int64_t)l * P.npts_pad + prow_t) * W + col0, cs);
+              }
+              if (kind == kFwdLast) {
+                const float4* wo = reinterpret_cast<const float4*>(wout_s + col0);
+                if (MODE == 0) {
+#pragma unroll
+                  for (int i4 = 0; i4 < CW / 4; ++i4) {
+                    const float4 ww = wo[i4];
+                    dot = fmaf(v[4 * i4], ww.x, dot);
+                    dot = fmaf(v[4 * i4 + 1], ww.y, dot);
+                    dot = fmaf(v[4 * i4 + 2], ww.z, dot);
+                    dot = fmaf(v[4 * i4 + 3], ww.w, dot);
+                  }
+                } else {
+                  // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
+#pragma unroll
+                  for (int i4 = 0; i4 < CW / 4; ++i4) {
+                    const float4 ww = wo[i4];
+                    v[4 * i4] = sv_t * ww.x * cs[4 * i4];
+                    v[4 * i4 + 1] = sv_t * ww.y * cs[4 * i4 + 1];
+                    v[4 * i4 + 2] = sv_t * ww.z * cs[4 * i4 + 2];
+                    v[4 * i4 + 3] = sv_t * ww.w * cs[4 * i4 + 3];
+                  }
+                  if (store_t) {
+                    store_row_bf16<CW>(P.Dlt + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
+                    if (c == 0 && g == 0) P.Y16o[prow_t] = __float2bfloat16_rn(sv_t);
+                  }
+                }
+              }
+            }
+            if (write_panel) st_panel_row<CW>(apan + (4 * t + c) * kPanelBytes, r, (CW / 8) * g, v);
+          }
+          if (write_panel) fence_async_smem();
+          tc_fence_before();
+          __syncwarp();
+          if (write_panel && lane == 0) mbar_arrive(&in_ready[t]);
+          if (MODE == 0 && kind == kFwdLast) {
+            // out = b_out + sum of the NWG column-group partial dot products of row r
+            dotp[t][g][r] = dot;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&dot_bar[t][q]);
+            if (g == 0) {
+              if (!warp_wait(&dot_bar[t][q], (dotph >> t) & 1u, &abort_flag, err, 404)) goto epi_done;
+              dotph ^= 1u << t;
+              if (valid_t) {
+                float f = bout;
+#pragma unroll
+                for (int q2 = 0; q2 < NWG; ++q2) f += dotp[t][q2][r];
+                P.out[prow_t] = f;
+              }
+            }
           }
         }
       }
@@ -740,7 +834,7 @@ int num_sms() {
 }
 
 size_t tile_smem(const Net& n) {
-  return 4 * (size_t)kPanelBytes + (size_t)kRing * n.W * 128 +
+  return 8 * (size_t)kPanelBytes + (size_t)kRingBytes +
          sizeof(float) * param_floats(n.L, n.W, n.F, n.kind) + 1024;
 }
 
@@ -851,8 +945,13 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
     P->st_kind[s] = l == n.L - 1 ? kFwdLast : kFwdHidden;
     P->st_layer[s] = l;
     P->st_panels[s] = n.in_dim[l] / 64;
+    INRCT_REQUIRE(s == 0 || P->st_panels[s] <= 4, "tile kernel: stage %d has %d input panels", s,
+                  P->st_panels[s]);
     P->st_map[s] = mi;
-    INRCT_TRY(make_map(&maps->m[mi++], w.Wb[l], n.in_dim[l], n.out_dim[l], 64, n.out_dim[l]));
+    // a ring slot holds out_dim / kNSplit output rows x 64 K (see mlp_tile_kernel)
+    INRCT_TRY(make_map(&maps->m[mi++], w.Wb[l], n.in_dim[l], n.out_dim[l], 64, n.out_dim[l] / kNSplit));
+    INRCT_REQUIRE(n.out_dim[l] == n.W, "tile kernel: MMA layer %d has %d outputs, expected %d", l,
+                  n.out_dim[l], n.W);
   }
   if (mode == 1) {
     for (int l = n.L - 1; l >= 1; --l, ++s) {
@@ -860,8 +959,10 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
       P->st_layer[s] = l;
       P->st_panels[s] = n.out_dim[l] / 64;
       P->st_map[s] = mi;
-      // W'_l^T is [in][out]: rows = in (the MMA N), K = out
-      INRCT_TRY(make_map(&maps->m[mi++], w.WbT[l], n.out_dim[l], n.in_dim[l], 64, n.in_dim[l]));
+      // W'_l^T is [in][out]: rows = in (the MMA N), K = out; chunks of in / kNSplit rows
+      INRCT_REQUIRE(n.in_dim[l] == n.W, "tile kernel: backward stage %d has N=%d, expected %d", l,
+                    n.in_dim[l], n.W);
+      INRCT_TRY(make_map(&maps->m[mi++], w.WbT[l], n.out_dim[l], n.in_dim[l], 64, n.in_dim[l] / kNSplit));
     }
   }
   P->n_stages = s;
@@ -936,7 +1037,7 @@ int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image,
   P.npts = npts;
   P.out = image;
   const int64_t tiles = (npts + kTile - 1) / kTile;
-  const int grid = (int)std::min<int64_t>(tiles, num_sms());
+  const int grid = (int)std::min<int64_t>((tiles + 1) / 2, num_sms());  // tiles go in pairs per CTA
   prof_mark(kMarkEvalKernel, st);
   INRCT_TRY(launch_tile(0, n, maps, P, grid, err, st));
   prof_mark(kMarkEvalDone, st);
@@ -1111,7 +1212,7 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     cudaMemsetAsync(w.Y16o, 0, sizeof(__nv_bfloat16) * 16 * w.pad, st);
     const int64_t tiles = (np + kTile - 1) / kTile;
     if (c0 == 0) prof_mark(kMarkVjpKernel, st);
-    INRCT_TRY(launch_tile(1, n, tmaps, P, (int)std::min<int64_t>(tiles, num_sms()), w.err, st));
+    INRCT_TRY(launch_tile(1, n, tmaps, P, (int)std::min<int64_t>((tiles + 1) / 2, num_sms()), w.err, st));
     if (c0 == 0) prof_mark(kMarkVjpKernelDone, st);
     // split-K weight-gradient GEMMs over this chunk's points
     int64_t pf;
