@@ -371,9 +371,16 @@ struct TileProg {
   const float* v;
   float scale;
   __nv_bfloat16* E;     // [npts_pad][2F] layer-1 input (FFN)
-  __nv_bfloat16* Act;   // [L][npts_pad][W] activations a_l
-  __nv_bfloat16* Dlt;   // [L][npts_pad][W] deltas
-  __nv_bfloat16* Cos;   // [L][npts_pad][W] cos(u_l) (SIREN)
+  __nv_bfloat16* Act;   // [L][npts_pad][W] activations a_l; a_0 .. a_{L-2} arrive by TMA store
+  __nv_bfloat16* Dlt;   // [L][npts_pad][W] deltas, all by TMA store from the input panels
+  // sigma'(u_l) for l = 0 .. L-2 (SIREN: cos u_l with omega0 folded in the weights; FFN: 1[u_l > 0]),
+  // read back only by this kernel: blocked so that a warp's 32 rows x CW columns are one
+  // contiguous 1 KB run, index (((l * n_tiles + tile) * W/64 + c) * NWG + g) * 128 + row
+  __nv_bfloat16* Sg;
+  int st_in_arr[kMaxStages];    // the stage's input panels are row block tile of: 0 Act, 1 Dlt, -1 none
+  int st_in_layer[kMaxStages];  // ... layer of that array
+  int tail_layer;               // Dlt layer held by the panels after the last stage
+  int map_act, map_dlt;         // tensor maps (in the kernel's Maps) for the panel stores
   __nv_bfloat16* Y16c;  // [16][npts_pad] coordinates (SIREN)
   __nv_bfloat16* Y16o;  // [16][npts_pad] output-layer weights scale * v
   int64_t npts_pad;
@@ -459,7 +466,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   float4* first_s = reinterpret_cast<float4*>(wout_s + W);
   constexpr int CW = 64 / NWG, EPI_WARPS = 4 * NWG;  // one arrival per epilogue warp
   __shared__ uint64_t w_full[kRingMax], w_empty[kRingMax], in_ready[2], acc_full[2], a_full[2][4],
-      a_empty[2][4], dot_bar[2][4], drain_bar;
+      a_empty[2][4], dot_bar[2][4], st_done[2], drain_bar;
   __shared__ float dotp[2][NWG][kTile];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
@@ -477,6 +484,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     for (int t = 0; t < 2; ++t) {
       mbar_init(&in_ready[t], EPI_WARPS);
       mbar_init(&acc_full[t], 1);
+      mbar_init(&st_done[t], 1);
       for (int s = 0; s < 4; ++s) {
         mbar_init(&a_full[t][s], EPI_WARPS);
         mbar_init(&a_empty[t][s], 1);
@@ -539,12 +547,27 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
       uint32_t slot = 0, wf = 0, irp = 0u, ap = 0u;
       const uint32_t idesc = idesc_bf16(128, NW, false, false);
       bool issued = false;
+      // VJP: the input panels of a slot (activations or deltas of its tile) are also the
+      // scratch rows the weight-gradient GEMM reads; they are written out with TMA stores
+      // issued here once the epilogue has published them.  Before the slot's next
+      // acc_full (after which the epilogue overwrites the panels) the stores must have
+      // read shared memory.
+      auto store_panels = [&](int t, int map, int layer, int64_t tile) {
+        for (int c = 0; c < W / 64; ++c)
+          tma_store_2d(&maps.m[map], apan + (4 * t + c) * kPanelBytes, 64 * c,
+                       (int)(layer * P.npts_pad + tile * kTile));
+        bulk_commit_group();
+      };
       for (int64_t pr = 0; pr < n_pairs; ++pr) {
+        const int64_t tile0 = blockIdx.x + (2 * pr) * (int64_t)gridDim.x;
         for (int s = 0; s < P.n_stages; ++s) {
           for (int t = 0; t < 2; ++t) {
             if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, &abort_flag, err, 301)) goto mma_done;
             irp ^= 1u << t;
             tc_fence_after();
+            if (MODE == 1 && P.st_in_arr[s] >= 0 && tile0 + t * gridDim.x < n_tiles)
+              store_panels(t, P.st_in_arr[s] ? P.map_dlt : P.map_act, P.st_in_layer[s],
+                           tile0 + t * gridDim.x);
             const int np = P.st_panels[s];
             for (int c = 0; c < np; ++c) {
               const int as = c & 3;
@@ -573,11 +596,24 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               }
               if (c + 4 < np) mma_commit(&a_empty[t][as]);  // the buffer takes panel c + 4 next
             }
+            if (MODE == 1) bulk_wait_read_all();
             mma_commit(&acc_full[t]);
+          }
+        }
+        if (MODE == 1) {
+          // the deltas of the last stage: stored, then the feature pass of the next pair may
+          // overwrite the panels
+          for (int t = 0; t < 2; ++t) {
+            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, &abort_flag, err, 304)) goto mma_done;
+            irp ^= 1u << t;
+            if (tile0 + t * gridDim.x < n_tiles) store_panels(t, P.map_dlt, P.tail_layer, tile0 + t * gridDim.x);
+            bulk_wait_read_all();
+            mbar_arrive(&st_done[t]);
           }
         }
       }
     mma_done:
+      if (MODE == 1) bulk_wait_all();
       if (issued) {
         // drain: every issued MMA completes before TMEM is released (matters on the
         // abort path; otherwise the epilogue has already waited for all of them)
@@ -590,7 +626,11 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     const int q = warp & 3, g = warp >> 2;
     const int r = q * 32 + lane;                 // row of the tile = TMEM lane
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    uint32_t ae = 0u, af = 0u, dotph = 0u;       // phase parities (a_empty per slot and buffer; per slot)
+    uint32_t ae = 0u, af = 0u, dotph = 0u, sdp = 0u;  // phase parities (a_empty per slot and buffer; per slot)
+    // offset of this thread's CW sigma' values of (layer, tile, 64-column chunk c) in P.Sg
+    auto sg_off = [&](int layer, int64_t tile, int c) -> int64_t {
+      return ((((int64_t)layer * n_tiles + tile) * (W / 64) + c) * NWG + g) * (kTile * CW) + (int64_t)r * CW;
+    };
     const float bout = P.theta[P.offbout];
     const int n0 = P.in_panels < 4 ? P.in_panels : 4;  // first-stage panels published together
     float v[CW];
@@ -617,7 +657,13 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
       for (int t = 0; t < 2; ++t) {
         const int64_t prow_t = (t ? tile1 : tile0) * kTile + r;  // scratch row (padded to the tile)
         const bool store_t = (t ? tile1 : tile0) < n_tiles;      // dummy tiles write nowhere
+        const int64_t tile_t = t ? tile1 : tile0;
         const float xt[3] = {t ? x1[0] : x0[0], t ? x1[1] : x0[1], t ? x1[2] : x0[2]};
+        if (MODE == 1 && pr > 0) {
+          // the previous pair's last deltas are still being stored from these panels
+          if (!warp_wait(&st_done[t], (sdp >> t) & 1u, &abort_flag, err, 405)) goto epi_done;
+          sdp ^= 1u << t;
+        }
         for (int c = 0; c < P.in_panels; ++c) {
           const int col0 = 64 * c + CW * g;
           if (KIND == INRCT_FFN_RELU) {
@@ -643,8 +689,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                 v[i] = __sinf(z);
             }
             if (MODE == 1 && store_t) {
-              store_row_bf16<CW>(P.Act + prow_t * W + col0, v);
-              store_row_bf16<CW>(P.Cos + prow_t * W + col0, cs);
+              store_row_bf16<CW>(P.Sg + sg_off(0, tile_t, c), cs);
               if (c == 0 && g == 0) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
@@ -681,16 +726,17 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           const bool store_t = (t ? tile1 : tile0) < n_tiles;
           const bool valid_t = t ? valid1 : valid0;
           const float sv_t = t ? sv1 : sv0;
+          const int64_t tile_t = t ? tile1 : tile0;
           const bool bwd = MODE == 1 && kind == kBwd;
-          // backward: sigma'(u_{l-1}) rows of this tile; chunk c + 1 is fetched while chunk c is
+          const bool pub = write_panel || MODE == 1;  // VJP: the last deltas are stored from the panels
+          // backward: sigma'(u_{l-1}) of this tile; chunk c + 1 is fetched while chunk c is
           // processed, chunk 0 before the wait for the accumulator (a dummy tile reads nothing)
-          const __nv_bfloat16* sg_row =
-              (KIND == INRCT_FFN_RELU ? P.Act : P.Cos) + ((int64_t)(l - 1) * P.npts_pad + prow_t) * W;
           uint4 sgn[CW / 8];
           if (bwd) {
 #pragma unroll
             for (int k = 0; k < CW / 8; ++k)
-              sgn[k] = store_t ? reinterpret_cast<const uint4*>(sg_row + CW * g)[k] : make_uint4(0, 0, 0, 0);
+              sgn[k] = store_t ? reinterpret_cast<const uint4*>(P.Sg + sg_off(l - 1, tile_t, 0))[k]
+                               : make_uint4(0, 0, 0, 0);
           }
           if (!warp_wait(&acc_full[t], (af >> t) & 1u, &abort_flag, err, 402)) goto epi_done;
           af ^= 1u << t;
@@ -714,7 +760,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               if (c + 1 < W / 64) {
 #pragma unroll
                 for (int k = 0; k < CW / 8; ++k)
-                  sgn[k] = store_t ? reinterpret_cast<const uint4*>(sg_row + col0 + 64)[k]
+                  sgn[k] = store_t ? reinterpret_cast<const uint4*>(P.Sg + sg_off(l - 1, tile_t, c + 1))[k]
                                    : make_uint4(0, 0, 0, 0);
               }
               if (KIND == INRCT_FFN_RELU) {
@@ -724,8 +770,6 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
 #pragma unroll
                 for (int i = 0; i < CW; ++i) v[i] *= sg[i];
               }
-              if (store_t)
-                store_row_bf16<CW>(P.Dlt + ((int64_t)(l - 1) * P.npts_pad + prow_t) * W + col0, v);
             } else {
               const float4* bl = reinterpret_cast<const float4*>(bias_s + (size_t)l * W + col0);
               float cs[CW];
@@ -748,9 +792,10 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                 }
               }
               if (MODE == 1 && store_t) {
-                store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
-                if (KIND == INRCT_SIREN && kind == kFwdHidden)
-                  store_row_bf16<CW>(P.Cos + ((int64_t)l * P.npts_pad + prow_t) * W + col0, cs);
+                if (kind == kFwdHidden)  // a_l itself goes out from the panels
+                  store_row_bf16<CW>(P.Sg + sg_off(l, tile_t, c), cs);
+                else                     // a_{L-1} is not a panel (the panels take delta_{L-1})
+                  store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
               }
               if (kind == kFwdLast) {
                 const float4* wo = reinterpret_cast<const float4*>(wout_s + col0);
@@ -773,19 +818,16 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                     v[4 * i4 + 2] = sv_t * ww.z * cs[4 * i4 + 2];
                     v[4 * i4 + 3] = sv_t * ww.w * cs[4 * i4 + 3];
                   }
-                  if (store_t) {
-                    store_row_bf16<CW>(P.Dlt + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
-                    if (c == 0 && g == 0) P.Y16o[prow_t] = __float2bfloat16_rn(sv_t);
-                  }
+                  if (store_t && c == 0 && g == 0) P.Y16o[prow_t] = __float2bfloat16_rn(sv_t);
                 }
               }
             }
-            if (write_panel) st_panel_row<CW>(apan + (4 * t + c) * kPanelBytes, r, (CW / 8) * g, v);
+            if (pub) st_panel_row<CW>(apan + (4 * t + c) * kPanelBytes, r, (CW / 8) * g, v);
           }
-          if (write_panel) fence_async_smem();
+          if (pub) fence_async_smem();
           tc_fence_before();
           __syncwarp();
-          if (write_panel && lane == 0) mbar_arrive(&in_ready[t]);
+          if (pub && lane == 0) mbar_arrive(&in_ready[t]);
           if (MODE == 0 && kind == kFwdLast) {
             // out = b_out + sum of the NWG column-group partial dot products of row r
             dotp[t][g][r] = dot;
@@ -944,6 +986,9 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
   for (int l = first_mma_layer(n); l < n.L; ++l, ++s) {
     P->st_kind[s] = l == n.L - 1 ? kFwdLast : kFwdHidden;
     P->st_layer[s] = l;
+    // input of a forward stage: a_{l-1}; for the first MMA layer of an FFN, the features (E)
+    P->st_in_arr[s] = l == 0 ? -1 : 0;
+    P->st_in_layer[s] = l - 1;
     P->st_panels[s] = n.in_dim[l] / 64;
     INRCT_REQUIRE(s == 0 || P->st_panels[s] <= 4, "tile kernel: stage %d has %d input panels", s,
                   P->st_panels[s]);
@@ -957,6 +1002,8 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
     for (int l = n.L - 1; l >= 1; --l, ++s) {
       P->st_kind[s] = kBwd;
       P->st_layer[s] = l;
+      P->st_in_arr[s] = 1;  // delta_l
+      P->st_in_layer[s] = l;
       P->st_panels[s] = n.out_dim[l] / 64;
       P->st_map[s] = mi;
       // W'_l^T is [in][out]: rows = in (the MMA N), K = out; chunks of in / kNSplit rows
@@ -966,6 +1013,12 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
     }
   }
   P->n_stages = s;
+  // after the last stage the panels hold delta_{l-1} of its layer (a backward stage) or
+  // delta_{L-1} (a network whose only MMA layer is the last one)
+  P->tail_layer = P->st_kind[s - 1] == kBwd ? P->st_layer[s - 1] - 1 : P->st_layer[s - 1];
+  P->map_act = mi;  // filled by the caller, which owns the scratch
+  P->map_dlt = mi + 1;
+  INRCT_REQUIRE(mi + 2 <= kMaxJobs, "tile kernel: %d tensor maps", mi + 2);
   return INRCT_OK;
 }
 
@@ -1049,7 +1102,7 @@ namespace {
 struct TcVjpWs {
   int* err;
   TcWeights w;
-  __nv_bfloat16 *E, *Act, *Dlt, *Cos, *Y16c, *Y16o;
+  __nv_bfloat16 *E, *Act, *Dlt, *Sg, *Y16c, *Y16o;
   float* part;
   double* bias_part;
   int64_t pad;
@@ -1148,7 +1201,7 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* ou
   w.E = n.kind == INRCT_FFN_RELU ? c.take<__nv_bfloat16>((size_t)pad * n.K0) : nullptr;
   w.Act = c.take<__nv_bfloat16>((size_t)pad * n.L * n.W);
   w.Dlt = c.take<__nv_bfloat16>((size_t)pad * n.L * n.W);
-  w.Cos = n.kind == INRCT_SIREN ? c.take<__nv_bfloat16>((size_t)pad * n.L * n.W) : nullptr;
+  w.Sg = c.take<__nv_bfloat16>((size_t)pad * std::max(n.L - 1, 1) * n.W);
   w.Y16c = c.take<__nv_bfloat16>((size_t)16 * pad);
   w.Y16o = c.take<__nv_bfloat16>((size_t)16 * pad);
   int64_t pf;
@@ -1199,7 +1252,10 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
   P.E = w.E;
   P.Act = w.Act;
   P.Dlt = w.Dlt;
-  P.Cos = w.Cos;
+  P.Sg = w.Sg;
+  // panel stores: the scratch as [L * pad rows][W], 128-row x 64-column boxes like the panels
+  INRCT_TRY(make_map(&tmaps.m[P.map_act], w.Act, n.W, (uint64_t)n.L * w.pad, 64, kTile));
+  INRCT_TRY(make_map(&tmaps.m[P.map_dlt], w.Dlt, n.W, (uint64_t)n.L * w.pad, 64, kTile));
   P.Y16c = w.Y16c;
   P.Y16o = w.Y16o;
   P.npts_pad = w.pad;
