@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "INR-CT grad steps/s, proj+backproj GRays/s; BF16 vs FP32 at <=1e-2 grad err"
 L2_BYTES = 129 * 1024 * 1024
+BATCHED = "batched16_siren128"
 
 
 def parse():
@@ -46,6 +47,9 @@ def parse():
     p.add_argument("--loss", default="ls", choices=["ls", "fls"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=200)
+    p.add_argument("--no-fp32", action="store_true", help="skip the FP32 path and the BF16/FP32 gradient check")
+    p.add_argument("--fp32-steps", type=int, default=10)
+    p.add_argument("--no-fractions", action="store_true", help="skip the |I|/n = 1.0 and 0.05 step rates")
     return p.parse_args()
 
 
@@ -140,12 +144,19 @@ def oracle_sample(w, frac: float, seed: int = 0) -> float:
     return time.perf_counter() - t0
 
 
+def oracle_sample_any(w, frac: float, seed: int = 0) -> float:
+    """oracle_sample for one workload, or summed over a batch of problems (a list)."""
+    if isinstance(w, list):
+        return sum(oracle_sample(q, frac, seed) for q in w)
+    return oracle_sample(w, frac, seed)
+
+
 def oracle_rate(w, budget_s: float, frac: float):
     """(steps/s, samples timed, frac) of the oracle within about budget_s seconds."""
-    oracle_sample(w, min(frac, 1 / 64))       # warm-up (builds the C projector)
+    oracle_sample_any(w, min(frac, 1 / 64))       # warm-up (builds the C projector)
     total, k = 0.0, 0
     while total < budget_s or k == 0:
-        total += oracle_sample(w, frac, seed=k)
+        total += oracle_sample_any(w, frac, seed=k)
         k += 1
     per_step = total / k / frac
     return 1.0 / per_step, k
@@ -157,21 +168,22 @@ def run_reference(args, w, rank, world):
         return
     # each step is one oracle sample of a fraction of the step, sized so that the
     # whole --steps run takes about two minutes
-    est = oracle_sample(w, 1 / 64) * 64            # also warms the C projector up
+    est = oracle_sample_any(w, 1 / 64) * 64            # also warms the C projector up
     frac = min(1 / 16, max(1 / 512, 120.0 / (max(args.steps, 1) * est)))
     for _ in range(max(1, min(args.warmup, 2))):
-        oracle_sample(w, frac)
+        oracle_sample_any(w, frac)
     total = 0.0
     steps = max(1, args.steps)
     for k in range(steps):
-        total += oracle_sample(w, frac, seed=k)
+        total += oracle_sample_any(w, frac, seed=k)
     value = steps * frac / total
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
             "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "note": w.note, "batch": w.batch},
+            "config": ({"workload": BATCHED, "problems": len(w)} if isinstance(w, list)
+                       else {"workload": w.name, "note": w.note, "batch": w.batch}),
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{steps} samples of {frac:.4g} of a step each (forward "
                                        "on that fraction of the grid, P/P^T on that fraction of "
@@ -198,6 +210,145 @@ def dw_flops(a, pts):
     return 2.0 * pts * sum(o * i for o, i in shapes[:-1] if i >= 64)
 
 
+def run_batched(args, probs, rank, world, local, dev):
+    """The batched workload: 16 uneven 2-D problems stepped together by one graph launch."""
+    import torch
+
+    from paper_2604_09884_gb300 import inrct, synth
+    arch = probs[0].arch
+    mlp = inrct.mlp_desc(arch, inrct.BF16, device=dev)
+    n_sets = 4
+    state, idx_host, idx_dev = [], [], []
+    for k, w in enumerate(probs):
+        g = w.geom
+        seed = w.seed + 1000 * rank
+        x_true = torch.tensor(synth.phantom(g.d, g.N, w.n_shapes, seed).reshape(-1), dtype=torch.float32,
+                              device=dev)
+        y = torch.tensor(synth.noisy(inrct.project(g, x_true).cpu().numpy(), w.noise, seed + 1), device=dev)
+        theta = torch.tensor(synth.init_theta(arch, seed + 3), dtype=torch.float32, device=dev)
+        n_idx = w.batch
+        state.append({"geom": g, "theta": theta, "y": y, "idx": torch.empty(n_idx, dtype=torch.int32, device=dev),
+                      "scale": g.n / n_idx, "m": torch.zeros_like(theta), "s": torch.zeros_like(theta),
+                      "loss": torch.zeros(1, dtype=torch.float64, device=dev)})
+        hs = [torch.from_numpy(synth.index_set(g.n, n_idx, seed + 10 + j)).pin_memory() for j in range(n_sets)]
+        idx_host.append(hs)
+        idx_dev.append([h.to(dev) for h in hs])
+    batch = inrct.Batch(mlp, state, inrct.adam(lr=probs[0].lr), device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def set_idx(t):
+        for k, q in enumerate(state):
+            q["idx"].copy_(idx_dev[k][t % n_sets], non_blocking=True)
+
+    t = 0
+    for _ in range(args.warmup):
+        t += 1
+        set_idx(t)
+        batch.step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = inrct.launch_count()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            t += 1
+            starts[k].record(stream)
+            set_idx(t)                      # a new index set per problem and step (device copies)
+            batch.step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    launches = inrct.launch_count() - l0
+    total_ms = sum(st.elapsed_time(en) for st, en in zip(starts, ends))
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # end to end: index sets from pinned host memory, losses back to the host
+    loss_host = torch.zeros(len(state), dtype=torch.float64).pin_memory()
+    loss_dev = torch.zeros(len(state), dtype=torch.float64, device=dev)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        t += 1
+        for k, q in enumerate(state):
+            q["idx"].copy_(idx_host[k][t % n_sets], non_blocking=True)
+        batch.step()
+        for k, q in enumerate(state):
+            loss_dev[k:k + 1].copy_(q["loss"])
+        loss_host.copy_(loss_dev, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_value = world * e2e_steps / (time.perf_counter() - t0)
+    peak_mem = torch.cuda.max_memory_allocated(dev)
+
+    # dominant kernel: the same problems stepped one by one with the stage profile on
+    prof = 4
+    ws = [torch.empty(inrct.step_ws_bytes(q["geom"], mlp, q["idx"].numel()), dtype=torch.uint8, device=dev)
+          for q in state]
+    th = [q["theta"].clone() for q in state]
+    mm = [q["m"].clone() for q in state]
+    ss = [q["s"].clone() for q in state]
+    inrct.profile_begin(prof * len(state))
+    for r in range(prof):
+        for k, q in enumerate(state):
+            inrct.grad_step(q["geom"], mlp, th[k], q["y"], q["idx"], q["scale"],
+                            inrct.adam(lr=probs[0].lr, t=t + 1 + r), mm[k], ss[k], None, None, ws[k])
+    stages, nprof = inrct.profile_end()
+    per_batch = {k: v / prof for k, v in stages.items()}   # ms per batched step, summed over problems
+    n_eval = sum(q["geom"].n for q in state)
+    n_vjp = sum(q["idx"].numel() for q in state)
+    f_eval = mlp_flops(arch, n_eval, vjp=False)
+    f_vjp = mlp_flops(arch, n_vjp, vjp=True)
+    dominant = max(("eval_mlp_kernel", "vjp_mlp_kernel"), key=lambda k: per_batch[k])
+    flops = f_eval if dominant == "eval_mlp_kernel" else f_vjp
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = flops / per_batch[dominant] / 1e9
+    roofline = {"kernel": "mlp_tile_kernel (" + ("grid evaluation" if dominant == "eval_mlp_kernel" else "VJP")
+                + "), summed over the 16 problems, timed with the problems stepped one by one",
+                "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": achieved / bf16_peak,
+                "peak_source": ("measured" if peaks else "fallback") + " (bf16 burst)", "traffic": None}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, k = oracle_rate(probs, budget_s=20.0, frac=1 / 32)
+        cpu = {"value": rate, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{k} samples of 1/32 of every problem's step (forward on n/32 points, P/P^T on "
+                         "V/32 views, VJP on |I|/32 points), summed over the 16 problems, full-step time "
+                         "extrapolated linearly"}
+    if rank == 0:
+        sizes = sorted(q["geom"].N for q in state)
+        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "data": "synthetic",
+                "config": {"workload": BATCHED, "problems": len(state), "grid_sizes": sizes,
+                           "pixels_total": n_eval, "batch_total": n_vjp,
+                           "note": "16 independent 2-D par/fan problems, SIREN 3x128 each, |I| = n/4; "
+                                   "one CUDA graph launch per step (a branch per problem)",
+                           "l2": "flushed between timed steps (untimed 258 MB write)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "problem_steps_per_s": value * len(state),
+                "stage_ms_sequential": per_batch, "roofline": roofline,
+                "e2e": {"value": e2e_value, "unit": "steps/s",
+                        "h2d_bytes_per_step": int(sum(q["idx"].numel() * 4 for q in state)),
+                        "d2h_bytes_per_step": 8 * len(state)},
+                "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": cpu,
+                "peak_mem_bytes": int(peak_mem),
+                "loss_last": [float(x) for x in loss_host.tolist()]}
+        print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main():
     args = parse()
     import torch
@@ -208,10 +359,13 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     wl = synth.workloads()
-    if args.workload not in wl:
-        raise SystemExit(f"unknown workload {args.workload}; choose from {sorted(wl)}")
-    w = wl[args.workload]
-    if args.frac is not None:
+    if args.workload == BATCHED:
+        w = synth.batched_problems()
+    elif args.workload not in wl:
+        raise SystemExit(f"unknown workload {args.workload}; choose from {sorted(wl) + [BATCHED]}")
+    else:
+        w = wl[args.workload]
+    if args.frac is not None and not isinstance(w, list):
         w.batch = max(1, int(round(args.frac * w.geom.n)))
 
     if world > 1:
@@ -226,6 +380,11 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if isinstance(w, list):
+        run_batched(args, w, rank, world, local, dev)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     g, a = w.geom, w.arch
     seed = w.seed + 1000 * rank                      # every replica its own problem
     # ---- synthetic problem, resident on the device ----
@@ -312,6 +471,66 @@ def main():
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(tt.item())
     e2e_value = world * e2e_steps / e2e_s
+    peak_mem = torch.cuda.max_memory_allocated(dev)
+
+    # ---- reconstruction error of the trained INR, and other subsampling fractions ----
+    with torch.no_grad():
+        mse = float(((inrct.inr_eval_grid(mlp, theta, g.N) - x_true) ** 2).mean())
+    fractions = {f"{n_idx / g.n:.4g}": {"steps_per_s": value / world, "batch": n_idx}}
+    if not args.no_fractions:
+        for f in (1.0, 0.05):
+            nI = max(1, int(round(f * g.n)))
+            wsf = torch.empty(inrct.step_ws_bytes(g, mlp, nI), dtype=torch.uint8, device=dev)
+            idxf = torch.from_numpy(synth.index_set(g.n, nI, seed + 99)).to(dev)
+            thf, mf, sf = theta.clone(), torch.zeros_like(theta), torch.zeros_like(theta)
+            kf = 20
+            for tf in range(1, 3 + kf):
+                if tf == 3:
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                inrct.grad_step(g, mlp, thf, y, idxf, g.n / nI, inrct.adam(lr=w.lr, t=tf), mf, sf, None, None,
+                                wsf, loss_kind)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fractions[f"{f:.4g}"] = {"steps_per_s": 1000.0 * kf / e0.elapsed_time(e1), "batch": nI,
+                                     "timing": f"{kf} steps back to back, L2 not flushed"}
+            del wsf
+
+    # ---- the plain FP32 path (|I| = n) and the BF16 / FP32 gradient agreement ----
+    fp32 = None
+    if args.prec == "bf16" and not args.no_fp32:
+        mlp32 = inrct.mlp_desc(a, inrct.FP32, B, device=dev)
+        idx_all = torch.arange(g.n, dtype=torch.int32, device=dev)
+        ws32 = torch.empty(inrct.step_ws_bytes(g, mlp32, g.n), dtype=torch.uint8, device=dev)
+        th32, m32, s32 = theta.clone(), torch.zeros_like(theta), torch.zeros_like(theta)
+        loss32 = torch.zeros(1, dtype=torch.float64, device=dev)
+        for t32 in range(1, 3):
+            inrct.grad_step(g, mlp32, th32, y, idx_all, 1.0, inrct.adam(lr=w.lr, t=t32), m32, s32, loss32,
+                            None, ws32, loss_kind)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k32 = max(1, args.fp32_steps)
+        e0.record(stream)
+        for t32 in range(3, 3 + k32):
+            inrct.grad_step(g, mlp32, th32, y, idx_all, 1.0, inrct.adam(lr=w.lr, t=t32), m32, s32, loss32,
+                            None, ws32, loss_kind)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / k32
+        del ws32
+        # one estimator at the current theta: v = P^T r of its own image, the same index set
+        img = inrct.inr_eval_grid(mlp32, theta, g.N)
+        _, r, _ = inrct.project(g, img, y)
+        vfull = inrct.backproject(g, r)
+        g16 = inrct.inr_weighted_vjp(mlp, theta, g.N, idx_dev[0], vfull, scale)
+        g32 = inrct.inr_weighted_vjp(mlp32, theta, g.N, idx_dev[0], vfull, scale)
+        rel = float(torch.linalg.norm(g16 - g32) / torch.linalg.norm(g32))
+        cos = float(torch.dot(g16, g32) / (torch.linalg.norm(g16) * torch.linalg.norm(g32)))
+        fp32 = {"steps_per_s": 1000.0 / ms32, "ms_per_step": ms32, "batch": g.n, "steps": k32,
+                "grad_bf16_vs_fp32": {"rel_l2": rel, "cosine": cos, "batch": n_idx,
+                                      "v": "P^T (P f_theta - y) at the current theta"}}
 
     # ---- kernel rates from the stage profile (live, inside the timed steps) ----
     peaks = {}
@@ -377,6 +596,8 @@ def main():
                 "e2e": {"value": e2e_value, "unit": "steps/s",
                         "h2d_bytes_per_step": int(idx_host[0].numel() * 4), "d2h_bytes_per_step": 8},
                 "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": cpu,
+                "peak_mem_bytes": int(peak_mem), "fp32_path": fp32, "fractions": fractions,
+                "mse_vs_x_true": mse,
                 "loss_last": float(loss_host.item())}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -238,6 +238,56 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
               double* grad_out, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/*
+ * Batched independent problems -- one step of Algorithm 1 plus Adam for each of
+ * n_probs unrelated reconstructions (own geometry, grid, parameters, data), all
+ * sharing one INR architecture.  The paper trains one problem at a time; running
+ * many small ones together is this library's own addition, so that problems far
+ * smaller than the GPU still fill it.
+ *
+ * inrct_batch_create records the whole batched step once as a CUDA graph with
+ * one branch per problem (branches run concurrently on internal streams); each
+ * grad_step_batched call launches that graph on `stream`.  Every pointer in the
+ * problem table is captured: the caller keeps the buffers alive and at the same
+ * addresses for the lifetime of the batch, and may change their CONTENTS
+ * between launches (new index sets in idx, new data in y).
+ *
+ * The Adam step index lives in device memory: *step_counter (one int64, device)
+ * is advanced by one at the start of every launch and read by the Adam update,
+ * which therefore sees t = (previous value) + 1.  Set it to 0 before the first
+ * launch.  The update is bit-identical to grad_step with adam->t equal to that t.
+ *
+ * Problem table entries (inrct_problem) are copied; theta, y, idx, adam_m,
+ * adam_s, loss_out (nullable) have the meaning and layout of grad_step.
+ * ws: at least inrct_batch_ws_bytes(...) bytes of device memory, owned by the
+ * caller, kept alive with the batch.  Errors: INVALID_ARG for a bad problem
+ * (its index in the message), WORKSPACE, UNSUPPORTED (an architecture the
+ * selected precision cannot run), CUDA (graph capture or instantiation).
+ * inrct_batch_destroy frees the graph and the internal streams (host side only).
+ */
+typedef struct {
+  inrct_geom geom;
+  inrct_grid grid;
+  float* theta;
+  const float* y;
+  const int32_t* idx;
+  int64_t n_idx;
+  double scale;          /* n / |I| for the estimator of Eq. 2 */
+  float* adam_m;
+  float* adam_s;
+  double* loss_out;      /* nullable */
+} inrct_problem;
+
+typedef struct inrct_batch inrct_batch;
+
+size_t inrct_batch_ws_bytes(const inrct_mlp* mlp, const inrct_problem* probs, int n_probs);
+int inrct_batch_create(const inrct_mlp* mlp, int loss, const inrct_problem* probs, int n_probs,
+                       const inrct_adam* adam, long long* step_counter, void* ws, size_t ws_bytes,
+                       inrct_batch** out);
+int grad_step_batched(inrct_batch* batch, cudaStream_t stream);
+int inrct_batch_destroy(inrct_batch* batch);
+
+/* ------------------------------------------------------------------------ */
 /* Instrumentation (host-side, not part of the method) */
 
 /* Number of kernel launches this library has issued since it was loaded. */

@@ -38,7 +38,11 @@ struct Profile {
 };
 static Profile g_prof;
 
+// Set while a batched step is being recorded into a CUDA graph: no profile marks then.
+static thread_local bool g_capturing = false;
+
 void prof_mark(int mark, cudaStream_t st) {
+  if (g_capturing) return;
   std::lock_guard<std::mutex> lk(g_prof.mu);
   if (!g_prof.on || g_prof.step < 0 || g_prof.step >= g_prof.max_steps) return;
   const size_t i = (size_t)g_prof.step * kNumMarks + mark;
@@ -46,6 +50,7 @@ void prof_mark(int mark, cudaStream_t st) {
 }
 
 static void prof_step_begin() {
+  if (g_capturing) return;
   std::lock_guard<std::mutex> lk(g_prof.mu);
   if (g_prof.on) ++g_prof.step;
 }
@@ -227,11 +232,12 @@ size_t inrct_step_ws_bytes(const inrct_geom* geom, const inrct_grid* grid, const
   return step_layout(geom, grid, mlp, n, n_idx, INRCT_LOSS_FLS, nullptr, 0, nullptr, nullptr);
 }
 
-int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* mlp, int loss,
-              float* theta, const float* y, const int32_t* idx, int64_t n_idx, double scale,
-              const inrct_adam* adam, float* adam_m, float* adam_s, double* loss_out,
-              double* grad_out, void* ws, size_t ws_bytes, cudaStream_t stream) {
-  clear_error();
+// One step of Algorithm 1 + Adam.  t_dev != NULL: the Adam step index is read from
+// device memory (batched steps recorded in a graph), adam->t is ignored.
+static int step_impl(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* mlp, int loss,
+                     float* theta, const float* y, const int32_t* idx, int64_t n_idx, double scale,
+                     const inrct_adam* adam, const long long* t_dev, float* adam_m, float* adam_s,
+                     double* loss_out, double* grad_out, void* ws, size_t ws_bytes, cudaStream_t stream) {
   INRCT_TRY(check_geom(geom, grid));
   Net n;
   INRCT_TRY(make_net(mlp, grid, &n));
@@ -276,8 +282,174 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
       return INRCT_ERR_CUDA;
     }
   }
-  if (adam) INRCT_TRY(adam_update(theta, g, adam_m, adam_s, n.p, adam, stream));
+  if (adam && t_dev) {
+    INRCT_TRY(adam_update_devt(theta, g, adam_m, adam_s, n.p, adam, t_dev, stream));
+  } else if (adam) {
+    INRCT_TRY(adam_update(theta, g, adam_m, adam_s, n.p, adam, stream));
+  }
   prof_mark(kMarkEnd, stream);
+  return INRCT_OK;
+}
+
+int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* mlp, int loss,
+              float* theta, const float* y, const int32_t* idx, int64_t n_idx, double scale,
+              const inrct_adam* adam, float* adam_m, float* adam_s, double* loss_out,
+              double* grad_out, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  return step_impl(geom, grid, mlp, loss, theta, y, idx, n_idx, scale, adam, nullptr, adam_m, adam_s,
+                   loss_out, grad_out, ws, ws_bytes, stream);
+}
+
+// ---------------------------------------------------------------------------
+// batched independent problems: one CUDA graph, one branch per problem
+// ---------------------------------------------------------------------------
+struct inrct_batch {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  long long launches = 0;  // kernels per launch of the graph
+};
+
+static constexpr int kBatchStreams = 8;
+
+static size_t batch_problem_ws(const inrct_mlp* mlp, const inrct_problem& q) {
+  const size_t b = inrct_step_ws_bytes(&q.geom, &q.grid, mlp, q.n_idx);
+  return (b + 255) / 256 * 256;
+}
+
+static void batch_free(inrct_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto e : b->events) cudaEventDestroy(e);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  delete b;
+}
+
+size_t inrct_batch_ws_bytes(const inrct_mlp* mlp, const inrct_problem* probs, int n_probs) {
+  if (!mlp || !probs || n_probs <= 0) return 0;
+  size_t total = 0;
+  for (int i = 0; i < n_probs; ++i) {
+    const size_t b = batch_problem_ws(mlp, probs[i]);
+    if (b <= 256) return 0;  // an invalid problem
+    total += b;
+  }
+  return total + 256;
+}
+
+int inrct_batch_create(const inrct_mlp* mlp, int loss, const inrct_problem* probs, int n_probs,
+                       const inrct_adam* adam, long long* step_counter, void* ws, size_t ws_bytes,
+                       inrct_batch** out) {
+  clear_error();
+  INRCT_REQUIRE(out, "out must not be NULL");
+  *out = nullptr;
+  INRCT_REQUIRE(mlp && probs && n_probs > 0 && n_probs <= 4096, "invalid problem table (%d problems)",
+                n_probs);
+  INRCT_REQUIRE(adam && step_counter, "adam parameters and the device step counter are required");
+  INRCT_REQUIRE(loss == INRCT_LOSS_LS || loss == INRCT_LOSS_FLS, "unknown loss kind %d", loss);
+  // validate every problem up front (the graph must not be half-recorded)
+  for (int i = 0; i < n_probs; ++i) {
+    const inrct_problem& q = probs[i];
+    Net n;
+    int rc = check_geom(&q.geom, &q.grid);
+    if (rc == INRCT_OK) rc = make_net(mlp, &q.grid, &n);
+    if (rc == INRCT_OK) rc = check_tc(mlp, n);
+    if (rc != INRCT_OK) {
+      char why[400];
+      snprintf(why, sizeof(why), "%s", inrct_last_error());
+      set_error("problem %d: %s", i, why);
+      return rc;
+    }
+    INRCT_REQUIRE(q.theta && q.y && q.idx && q.adam_m && q.adam_s, "problem %d: NULL buffer", i);
+    INRCT_REQUIRE(q.n_idx > 0, "problem %d: n_idx must be positive", i);
+  }
+  const size_t need = inrct_batch_ws_bytes(mlp, probs, n_probs);
+  if (!ws || ws_bytes < need) {
+    set_error("grad_step_batched: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  inrct_batch* b = new inrct_batch;
+  const int ns = std::min(n_probs, kBatchStreams);
+  auto fail = [&](const char* what, cudaError_t e) {
+    set_error("grad_step_batched: %s: %s", what, cudaGetErrorString(e));
+    batch_free(b);
+    return INRCT_ERR_CUDA;
+  };
+  for (int k = 0; k < ns; ++k) {
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail("stream", e);
+    b->streams.push_back(s);
+  }
+  for (int k = 0; k < ns; ++k) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail("event", e);
+    b->events.push_back(ev);
+  }
+  cudaStream_t s0 = b->streams[0];
+  cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return fail("begin capture", e);
+  g_capturing = true;
+  const long long l0 = g_launches.load();
+  int rc = advance_step_counter(step_counter, s0);
+  // fork: every branch stream waits for the counter update
+  if (rc == INRCT_OK && cudaEventRecord(b->events[0], s0) != cudaSuccess) rc = INRCT_ERR_CUDA;
+  for (int k = 1; k < ns && rc == INRCT_OK; ++k)
+    if (cudaStreamWaitEvent(b->streams[k], b->events[0], 0) != cudaSuccess) rc = INRCT_ERR_CUDA;
+  char* wp = static_cast<char*>(ws);
+  for (int i = 0; i < n_probs && rc == INRCT_OK; ++i) {
+    const inrct_problem& q = probs[i];
+    const size_t nb = batch_problem_ws(mlp, q);
+    rc = step_impl(&q.geom, &q.grid, mlp, loss, q.theta, q.y, q.idx, q.n_idx, q.scale, adam,
+                   step_counter, q.adam_m, q.adam_s, q.loss_out, nullptr, wp, nb, b->streams[i % ns]);
+    if (rc != INRCT_OK) {
+      char why[400];
+      snprintf(why, sizeof(why), "%s", inrct_last_error());
+      set_error("problem %d: %s", i, why);
+    }
+    wp += nb;
+  }
+  // join
+  for (int k = 1; k < ns && rc == INRCT_OK; ++k) {
+    if (cudaEventRecord(b->events[k], b->streams[k]) != cudaSuccess ||
+        cudaStreamWaitEvent(s0, b->events[k], 0) != cudaSuccess)
+      rc = INRCT_ERR_CUDA;
+  }
+  g_capturing = false;
+  b->launches = g_launches.load() - l0;
+  g_launches.fetch_sub(b->launches);  // recorded, not launched
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(s0, &graph);
+  b->graph = graph;
+  if (rc != INRCT_OK) {
+    if (rc == INRCT_ERR_CUDA && !inrct_last_error()[0]) set_error("grad_step_batched: capture failed");
+    batch_free(b);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail("end capture", e);
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) return fail("instantiate", e);
+  *out = b;
+  return INRCT_OK;
+}
+
+int grad_step_batched(inrct_batch* b, cudaStream_t stream) {
+  clear_error();
+  INRCT_REQUIRE(b && b->exec, "invalid batch");
+  cudaError_t e = cudaGraphLaunch(b->exec, stream);
+  if (e != cudaSuccess) {
+    set_error("grad_step_batched: graph launch: %s", cudaGetErrorString(e));
+    return INRCT_ERR_CUDA;
+  }
+  g_launches.fetch_add(b->launches);
+  return INRCT_OK;
+}
+
+int inrct_batch_destroy(inrct_batch* b) {
+  clear_error();
+  batch_free(b);
   return INRCT_OK;
 }
 

@@ -64,6 +64,11 @@ int gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int
 // shared small kernels (optim.cu)
 int adam_update(float* theta, const double* grad, float* m, float* s, int64_t p,
                 const inrct_adam* adam, cudaStream_t st);
+// Adam reading the step index from *t_dev (device); a->t is ignored.
+int adam_update_devt(float* theta, const double* grad, float* m, float* s, int64_t p,
+                     const inrct_adam* a, const long long* t_dev, cudaStream_t st);
+// *t_dev += 1 on the stream.
+int advance_step_counter(long long* t_dev, cudaStream_t st);
 int f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t st);
 
 // Points processed per VJP chunk: scratch is sized for min(n_idx, this).

@@ -46,32 +46,117 @@ int make_net(const inrct_mlp* mlp, const inrct_grid* grid, Net* n) {
   return INRCT_OK;
 }
 
-__global__ void adam_kernel(float* __restrict__ theta, const double* __restrict__ g,
-                            float* __restrict__ m, float* __restrict__ s, int64_t p, float b1,
-                            float b2, float lr_t, float eps_t) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p) return;
+// Bias-corrected step size and epsilon of Adam step t, with both corrections folded:
+// lr_t = lr * sqrt(1 - b2^t) / (1 - b1^t) and eps_t = eps * sqrt(1 - b2^t), so that
+// theta -= lr_t * m / (sqrt(s) + eps_t) equals lr * m_hat / (sqrt(s_hat) + eps).
+// Every operation is rounded on its own (no contraction into fused multiply-adds) and
+// the powers are formed by square-and-multiply, so host and device produce the same
+// bits: the graph-driven batched step reads t from device memory and must agree with
+// the host-driven single-problem step.
+namespace {
+__host__ __device__ inline double rn_mul(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  volatile double r = a * b;
+  return r;
+#endif
+}
+__host__ __device__ inline double rn_sub(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, -b);
+#else
+  volatile double r = a - b;
+  return r;
+#endif
+}
+__host__ __device__ inline double rn_sqrt(double a) {
+#ifdef __CUDA_ARCH__
+  return __dsqrt_rn(a);
+#else
+  return sqrt(a);
+#endif
+}
+__host__ __device__ inline double rn_div(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __ddiv_rn(a, b);
+#else
+  volatile double r = a / b;
+  return r;
+#endif
+}
+__host__ __device__ inline double rn_pow(double b, long long t) {
+  double r = 1.0;
+  while (t > 0) {
+    if (t & 1) r = rn_mul(r, b);
+    b = rn_mul(b, b);
+    t >>= 1;
+  }
+  return r;
+}
+__host__ __device__ inline void adam_folded(double lr, double b1, double b2, double eps, long long t,
+                                            float* lr_t, float* eps_t) {
+  const double bc1 = rn_sub(1.0, rn_pow(b1, t));
+  const double rb2 = rn_sqrt(rn_sub(1.0, rn_pow(b2, t)));
+  *lr_t = (float)rn_div(rn_mul(lr, rb2), bc1);
+  *eps_t = (float)rn_mul(eps, rb2);
+}
+
+__device__ __forceinline__ void adam_elem(float* theta, const double* g, float* m, float* s, int64_t i,
+                                          float b1, float b2, float lr_t, float eps_t) {
   const float gi = (float)g[i];
   const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
   const float si = fmaf(b2, s[i], (1.f - b2) * gi * gi);
   m[i] = mi;
   s[i] = si;
-  // theta -= lr * m_hat / (sqrt(s_hat) + eps), with both bias corrections folded
-  // into lr_t = lr * sqrt(1 - b2^t) / (1 - b1^t) and eps_t = eps * sqrt(1 - b2^t).
   theta[i] -= lr_t * mi / (sqrtf(si) + eps_t);
 }
+}  // namespace
+
+__global__ void adam_kernel(float* __restrict__ theta, const double* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ s, int64_t p, float b1,
+                            float b2, float lr_t, float eps_t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < p) adam_elem(theta, g, m, s, i, b1, b2, lr_t, eps_t);
+}
+
+// Adam with the step index read from device memory (*t, already advanced for this step).
+__global__ void adam_devt_kernel(float* __restrict__ theta, const double* __restrict__ g,
+                                 float* __restrict__ m, float* __restrict__ s, int64_t p, double lr,
+                                 double b1, double b2, double eps, const long long* __restrict__ t) {
+  __shared__ float fold[2];
+  if (threadIdx.x == 0) adam_folded(lr, b1, b2, eps, *t, &fold[0], &fold[1]);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < p) adam_elem(theta, g, m, s, i, (float)b1, (float)b2, fold[0], fold[1]);
+}
+
+__global__ void step_counter_kernel(long long* t) { *t += 1; }
 
 int adam_update(float* theta, const double* grad, float* m, float* s, int64_t p,
                 const inrct_adam* a, cudaStream_t st) {
   INRCT_REQUIRE(a->t >= 1, "Adam step index t must be >= 1");
   INRCT_REQUIRE(m && s, "Adam moments must not be NULL");
-  const double bc1 = 1.0 - pow(a->beta1, (double)a->t);
-  const double bc2 = 1.0 - pow(a->beta2, (double)a->t);
-  const float lr_t = (float)(a->lr * sqrt(bc2) / bc1);
-  const float eps_t = (float)(a->eps * sqrt(bc2));
+  float lr_t, eps_t;
+  adam_folded(a->lr, a->beta1, a->beta2, a->eps, a->t, &lr_t, &eps_t);
   adam_kernel<<<ceil_div(p, 256), 256, 0, st>>>(theta, grad, m, s, p, (float)a->beta1,
                                                 (float)a->beta2, lr_t, eps_t);
   INRCT_CHECK_LAUNCH("adam");
+  return INRCT_OK;
+}
+
+int adam_update_devt(float* theta, const double* grad, float* m, float* s, int64_t p,
+                     const inrct_adam* a, const long long* t_dev, cudaStream_t st) {
+  INRCT_REQUIRE(m && s && t_dev, "Adam moments and the step counter must not be NULL");
+  adam_devt_kernel<<<ceil_div(p, 256), 256, 0, st>>>(theta, grad, m, s, p, a->lr, a->beta1, a->beta2,
+                                                     a->eps, t_dev);
+  INRCT_CHECK_LAUNCH("adam (device step index)");
+  return INRCT_OK;
+}
+
+int advance_step_counter(long long* t_dev, cudaStream_t st) {
+  step_counter_kernel<<<1, 1, 0, st>>>(t_dev);
+  INRCT_CHECK_LAUNCH("step counter");
   return INRCT_OK;
 }
 

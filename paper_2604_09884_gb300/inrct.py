@@ -56,6 +56,12 @@ class Adam(ctypes.Structure):
                 ("eps", ctypes.c_double), ("t", ctypes.c_int64)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("geom", Geom), ("grid", Grid), ("theta", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("n_idx", ctypes.c_int64), ("scale", ctypes.c_double),
+                ("adam_m", ctypes.c_void_p), ("adam_s", ctypes.c_void_p), ("loss_out", ctypes.c_void_p)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _SZ = ctypes.c_size_t
@@ -97,6 +103,11 @@ def lib():
         "inrct_gemm_tn": ([_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, _P, _P, _SZ, _P], ctypes.c_int),
         "grad_step": ([g, gr, m, ctypes.c_int, _P, _P, _P, _I64, ctypes.c_double,
                        ctypes.POINTER(Adam), _P, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+        "inrct_batch_ws_bytes": ([m, ctypes.POINTER(Problem), ctypes.c_int], _SZ),
+        "inrct_batch_create": ([m, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
+                                ctypes.POINTER(Adam), _P, _P, _SZ, ctypes.POINTER(_P)], ctypes.c_int),
+        "grad_step_batched": ([_P, _P], ctypes.c_int),
+        "inrct_batch_destroy": ([_P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -280,6 +291,53 @@ def grad_step(g: synth.GeomSpec, mlp: MlpHandle, theta: torch.Tensor, y: torch.T
                        idx.numel(), float(scale), ctypes.byref(adam) if adam is not None else None,
                        _ptr(m), _ptr(s), _ptr(loss_out), _ptr(grad_out), _ptr(ws), ws.numel(),
                        _stream(stream)))
+
+
+class Batch:
+    """grad_step_batched over independent problems sharing one INR architecture.
+
+    problems: list of dicts with keys geom (GeomSpec), theta, y, idx, scale, m, s and
+    optionally loss (a [1] float64 tensor).  The tensors are held here so their
+    addresses stay valid for the recorded graph; their contents may change between
+    steps.  `counter` is the device step index (int64 [1]), advanced by every step()."""
+
+    def __init__(self, mlp: MlpHandle, problems: list, adam: Adam, loss_kind: int = LOSS_LS,
+                 device="cuda"):
+        L = lib()
+        self._keep = [mlp, problems]
+        arr = (Problem * len(problems))()
+        for k, q in enumerate(problems):
+            g = q["geom"]
+            arr[k] = Problem(geom_desc(g), grid_desc(g.d, g.N), _ptr(q["theta"], torch.float32).value,
+                             _ptr(q["y"], torch.float32).value, _ptr(q["idx"], torch.int32).value,
+                             q["idx"].numel(), float(q["scale"]), _ptr(q["m"], torch.float32).value,
+                             _ptr(q["s"], torch.float32).value,
+                             _ptr(q["loss"], torch.float64).value if q.get("loss") is not None else None)
+        self._arr = arr
+        nb = L.inrct_batch_ws_bytes(ctypes.byref(mlp.desc), arr, len(problems))
+        if nb == 0:
+            raise InrctError(1, "invalid problem table")
+        self.ws = _ws(nb, device)
+        self.counter = torch.zeros(1, dtype=torch.int64, device=device)
+        self._adam = adam
+        h = ctypes.c_void_p()
+        _check(L.inrct_batch_create(ctypes.byref(mlp.desc), loss_kind, arr, len(problems), ctypes.byref(adam),
+                                    _ptr(self.counter), _ptr(self.ws), self.ws.numel(), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, stream=None):
+        _check(lib().grad_step_batched(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().inrct_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gemm_tn(X: torch.Tensor, Y: torch.Tensor | None, Y16: torch.Tensor | None, stream=None):

@@ -27,7 +27,8 @@ def L():
 
 def test_exports_every_declared_symbol(L):
     names = _declared()
-    assert {"project", "backproject", "inr_eval_grid", "inr_weighted_vjp", "grad_step"} <= set(names)
+    assert {"project", "backproject", "inr_eval_grid", "inr_weighted_vjp", "grad_step",
+            "grad_step_batched"} <= set(names)
     for n in names:
         assert hasattr(L, n), n
 
@@ -94,3 +95,35 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(inrct, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(inrct.InrctError):
         inrct.lib()
+
+
+def _problem(g, ptr=256, n_idx=16):
+    p = ctypes.c_void_p(ptr).value
+    return inrct.Problem(inrct.geom_desc(g), inrct.grid_desc(g.d, g.N), p, p, p, n_idx, 4.0, p, p, None)
+
+
+def test_batch_create_rejects_a_bad_problem_by_index(L):
+    a = synth.ArchSpec("siren", 2, 128, 3, omega0=30.0)
+    h = inrct.MlpHandle(inrct.Mlp(1, 2, 0, None, 30.0, 3, 128, inrct.BF16), None, a)
+    good = synth.GeomSpec("par2d", 64, 30, 91)
+    bad = synth.GeomSpec("par2d", 64, 0, 91)          # no views
+    arr = (inrct.Problem * 2)(_problem(good), _problem(bad))
+    out = ctypes.c_void_p()
+    counter = ctypes.c_void_p(256)
+    rc = L.inrct_batch_create(ctypes.byref(h.desc), 0, arr, 2, ctypes.byref(inrct.adam()), counter,
+                              counter, 1 << 30, ctypes.byref(out))
+    assert rc == 1 and b"problem 1" in L.inrct_last_error() and not out.value
+
+
+def test_batch_create_requires_its_workspace(L):
+    a = synth.ArchSpec("siren", 2, 128, 3, omega0=30.0)
+    h = inrct.MlpHandle(inrct.Mlp(1, 2, 0, None, 30.0, 3, 128, inrct.BF16), None, a)
+    g = synth.GeomSpec("fan2d", 64, 30, 91, sod=256.0, sdd=384.0, span=2 * 3.141592653589793)
+    arr = (inrct.Problem * 1)(_problem(g))
+    need = L.inrct_batch_ws_bytes(ctypes.byref(h.desc), arr, 1)
+    assert need > L.inrct_step_ws_bytes(ctypes.byref(inrct.geom_desc(g)), ctypes.byref(inrct.grid_desc(2, 64)),
+                                         ctypes.byref(h.desc), 16)
+    out = ctypes.c_void_p()
+    rc = L.inrct_batch_create(ctypes.byref(h.desc), 0, arr, 1, ctypes.byref(inrct.adam()),
+                              ctypes.c_void_p(256), ctypes.c_void_p(256), need - 1, ctypes.byref(out))
+    assert rc == 3 and not out.value
