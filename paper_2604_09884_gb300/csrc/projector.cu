@@ -393,55 +393,115 @@ __global__ void reduce_f64_kernel(const double* __restrict__ in, int64_t n, doub
 // ---------------------------------------------------------------------------
 // adjoint (gather form)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-    backproject2d_kernel(GeomDev g, const int4* __restrict__ tab, const float2* __restrict__ views,
-                         const float* __restrict__ sino, float* __restrict__ img) {
-  extern __shared__ float2 sv[];
-  for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < g.V; k += blockDim.x * blockDim.y)
-    sv[k] = views[k];
-  __syncthreads();
+// 2-D adjoint, tile-driven.  A block owns a 32 x 32 pixel tile; its warps take
+// disjoint subsets of the views.  For one view, a warp walks the rays whose
+// window can reach the tile (the bin range spanned by the tile's corners plus
+// the interpolation reach), and lane l evaluates each ray at the tile's slice l
+// of the ray's driving axis: the ray's fixed-point crossing there, identical
+// to the forward projector's, gives the two taps 1 - f and f on transverse
+// indices floor(u) and floor(u) + 1, which are added into the warp's
+// accumulator of the tile.  A crossing is thus evaluated once per (ray, slice)
+// instead of once per (pixel, candidate ray).  Accumulators are laid out
+// [transverse][slice] (row stride 32), one for x-driven and one for y-driven
+// rays, so that lane l always writes bank l: no conflicts and no atomics.  The
+// warps' accumulators are summed in a fixed order at the end (deterministic).
+constexpr int kBpTile = 32, kBpWarps = 8;
+constexpr size_t kBpSmem = sizeof(float) * ((size_t)kBpWarps * 2 * kBpTile * kBpTile + kBpTile * (kBpTile + 1));
+
+__global__ void __launch_bounds__(32 * kBpWarps)
+    backproject2d_tile_kernel(GeomDev g, const int4* __restrict__ tab, const float2* __restrict__ views,
+                              const float* __restrict__ sino, float* __restrict__ img) {
+  extern __shared__ float bsm[];
+  float* accx = bsm + (size_t)(threadIdx.y * 2) * kBpTile * kBpTile;  // this warp's x-driven taps [q][lane]
+  float* accy = accx + kBpTile * kBpTile;                              // y-driven taps [q][lane]
+  float* fin = bsm + (size_t)kBpWarps * 2 * kBpTile * kBpTile;          // [row][col], stride 33
+  const int lane = threadIdx.x, wv = threadIdx.y;
+  for (int i = lane; i < 2 * kBpTile * kBpTile; i += 32) accx[i] = 0.f;
   const int N = g.N, A = g.A;
   const int jref = N / 2;
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  const int iy = blockIdx.y * blockDim.y + threadIdx.y;
-  if (ix >= N || iy >= N) return;
+  const int x0 = blockIdx.x * kBpTile, y0 = blockIdx.y * kBpTile;
   const float D = 2.f / (float)N;
-  const float px = -1.f + ((float)ix + 0.5f) * D, py = -1.f + ((float)iy + 0.5f) * D;
+  // pixel-centre box of the tile (clipped to the image)
+  const float xlo = -1.f + ((float)x0 + 0.5f) * D, xhi = -1.f + ((float)min(x0 + kBpTile, N) - 0.5f) * D;
+  const float ylo = -1.f + ((float)y0 + 0.5f) * D, yhi = -1.f + ((float)min(y0 + kBpTile, N) - 0.5f) * D;
   const float cA = 0.5f * (float)(A - 1);
   const bool par = g.kind == INRCT_PAR2D;
   const float inv_pitch = (float)(1.0 / (g.du * (2.0 / N)));  // parallel: bins per world unit
   const float inv_dgam = (float)(g.sod / g.du);                // fan: bins per radian
   const float R = (float)(g.sod * (2.0 / N));
   const float hpar = (float)(1.0 / g.du) + 0.02f;
-  float acc = 0.f;
-  for (int k = 0; k < g.V; ++k) {
-    const float cb = sv[k].x, sb = sv[k].y;
-    float bc, h;
+  __syncwarp();
+  for (int k = wv; k < g.V; k += kBpWarps) {
+    const float2 cs = views[k];
+    const float cb = cs.x, sb = cs.y;
+    // bins whose window (centre +- h, as for a single pixel) can reach a pixel of the tile
+    float blo, bhi;
     if (par) {
-      bc = fmaf(px * cb + py * sb, inv_pitch, cA);
-      h = hpar;
+      const float c00 = (xlo * cb + ylo * sb), c10 = (xhi * cb + ylo * sb);
+      const float c01 = (xlo * cb + yhi * sb), c11 = (xhi * cb + yhi * sb);
+      blo = fmaf(fminf(fminf(c00, c10), fminf(c01, c11)), inv_pitch, cA) - hpar;
+      bhi = fmaf(fmaxf(fmaxf(c00, c10), fmaxf(c01, c11)), inv_pitch, cA) + hpar;
     } else {
-      const float wx = px - R * cb, wy = py - R * sb;
-      const float along = -(wx * cb + wy * sb);
-      const float across = sb * wx - cb * wy;
-      bc = fmaf(atan2f(across, along), inv_dgam, cA);
-      const float x = D * rsqrtf(wx * wx + wy * wy);
-      h = x * (1.f + x * x * (1.f / 6.f) + 4e-3f) * inv_dgam + 0.02f;
+      // fan angle of a point seen from the source, as a bin coordinate; extreme at the corners
+      const float sx = R * cb, sy = R * sb;
+      auto bin_of = [&](float px, float py) {
+        const float wx = px - sx, wy = py - sy;
+        return fmaf(atan2f(sb * wx - cb * wy, -(wx * cb + wy * sb)), inv_dgam, cA);
+      };
+      const float b00 = bin_of(xlo, ylo), b10 = bin_of(xhi, ylo), b01 = bin_of(xlo, yhi), b11 = bin_of(xhi, yhi);
+      // the widest single-pixel window: the tile point closest to the source
+      const float qx = fminf(fmaxf(sx, xlo), xhi) - sx, qy = fminf(fmaxf(sy, ylo), yhi) - sy;
+      const float x = D * rsqrtf(qx * qx + qy * qy);
+      const float h = x * (1.f + x * x * (1.f / 6.f) + 4e-3f) * inv_dgam + 0.02f;
+      blo = fminf(fminf(b00, b10), fminf(b01, b11)) - h;
+      bhi = fmaxf(fmaxf(b00, b10), fmaxf(b01, b11)) + h;
     }
-    const int b0 = max(0, (int)ceilf(bc - h));
-    const int b1 = min(A - 1, (int)floorf(bc + h));
+    const int b0 = max(0, (int)ceilf(blo));
+    const int b1 = min(A - 1, (int)floorf(bhi));
     const int4* trow = tab + (size_t)k * A;
     const float* srow = sino + (size_t)k * A;
+#pragma unroll 4  // independent table loads and crossings of four rays in flight
     for (int b = b0; b <= b1; ++b) {
       const int4 P = __ldg(trow + b);
+      const float s = __ldg(srow + b);
       const float sc = __int_as_float(P.w);
-      const bool xd = sc > 0.f;
-      const int j = xd ? ix : iy, q = xd ? iy : ix;
-      const float w = tap_weight(ray_U0(P) + (int64_t)(j - jref) * slope_fx(P), q);
-      if (w != 0.f) acc = fmaf(w * fabsf(sc), __ldg(srow + b), acc);
+      const bool xd = sc > 0.f;  // x-driven: slices are columns
+      const float asc = fabsf(sc);
+      const int j = (xd ? x0 : y0) + lane;
+      const int qbase = xd ? y0 : x0;
+      int i0;
+      float f;
+      split_fx(ray_U0(P) + (int64_t)(j - jref) * slope_fx(P), i0, f);
+      const int q0 = i0 - qbase;
+      float* acc = xd ? accx : accy;
+      if (j < N) {
+        const float w0 = __fsub_rn(1.f, f);
+        if (q0 >= 0 && q0 < kBpTile && i0 < N && w0 != 0.f)
+          acc[q0 * kBpTile + lane] = fmaf(w0 * asc, s, acc[q0 * kBpTile + lane]);
+        if (q0 + 1 >= 0 && q0 + 1 < kBpTile && i0 + 1 < N && f != 0.f)
+          acc[(q0 + 1) * kBpTile + lane] = fmaf(f * asc, s, acc[(q0 + 1) * kBpTile + lane]);
+      }
     }
   }
-  img[(size_t)iy * N + ix] = acc;
+  __syncthreads();
+  const int t = wv * 32 + lane;
+  // y-driven taps: accy[q = column][slice = row]; transpose through fin
+  for (int i = t; i < kBpTile * kBpTile; i += 32 * kBpWarps) {
+    const int c = i >> 5, r = i & 31;
+    float sy = 0.f;
+#pragma unroll
+    for (int w = 0; w < kBpWarps; ++w) sy += bsm[(size_t)(2 * w + 1) * kBpTile * kBpTile + c * kBpTile + r];
+    fin[r * (kBpTile + 1) + c] = sy;
+  }
+  __syncthreads();
+  for (int i = t; i < kBpTile * kBpTile; i += 32 * kBpWarps) {
+    const int r = i >> 5, c = i & 31;
+    float sx = 0.f;
+#pragma unroll
+    for (int w = 0; w < kBpWarps; ++w) sx += bsm[(size_t)(2 * w) * kBpTile * kBpTile + r * kBpTile + c];
+    const int iy = y0 + r, ix = x0 + c;
+    if (iy < N && ix < N) img[(size_t)iy * N + ix] = sx + fin[r * (kBpTile + 1) + c];
+  }
 }
 
 template <int ZC>
@@ -748,9 +808,19 @@ int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float
                                                     sino, image);
     INRCT_CHECK_LAUNCH("backproject3d");
   } else {
-    dim3 blk(32, 8);
-    dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 8));
-    backproject2d_kernel<<<grd, blk, shm, st>>>(g, w.t.tab0, w.t.views, sino, image);
+    static bool attr_set = false;  // per process; the attribute is per function, all devices alike
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(backproject2d_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kBpSmem);
+      if (e != cudaSuccess) {
+        set_error("backproject2d: shared memory attribute: %s", cudaGetErrorString(e));
+        return INRCT_ERR_CUDA;
+      }
+      attr_set = true;
+    }
+    dim3 blk(32, kBpWarps);
+    dim3 grd(ceil_div(g.N, kBpTile), ceil_div(g.N, kBpTile));
+    backproject2d_tile_kernel<<<grd, blk, kBpSmem, st>>>(g, w.t.tab0, w.t.views, sino, image);
     INRCT_CHECK_LAUNCH("backproject2d");
   }
   return INRCT_OK;
