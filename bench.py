@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "INR-CT grad steps/s, proj+backproj GRays/s; BF16 vs FP32 at <=1e-2 grad err"
 L2_BYTES = 129 * 1024 * 1024
 BATCHED = "batched16_siren128"
+VJP_CHUNK = 1 << 20          # points per VJP chunk (the library's scratch unit)
 
 
 def parse():
@@ -115,9 +116,10 @@ class ClockSampler:
 # oracle timing (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------
 def oracle_sample(w, frac: float, seed: int = 0) -> float:
-    """Seconds of one oracle sample covering `frac` of a full step: forward on
-    frac*n grid points, P and P^T on frac*V views, the estimator on frac*|I|
-    points, Adam.  (Every part of the oracle step scales linearly in these.)"""
+    """Extrapolated seconds of one full oracle step, from one sample covering about
+    `frac` of it: the forward on frac*n grid points, P and P^T on max(1, frac*V)
+    views, the estimator on frac*|I| points, and Adam on all of theta.  Each part
+    scales linearly in what it covers, so each is divided by its own fraction."""
     import oracle as O
     from paper_2604_09884_gb300 import synth
     g, a = w.geom, w.arch
@@ -132,16 +134,20 @@ def oracle_sample(w, frac: float, seed: int = 0) -> float:
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     f = O.forward(oa, theta, O.grid_coords(g.d, g.N, np.arange(n_pts)))
+    t1 = time.perf_counter()
     img = np.zeros(g.n)
     img[:n_pts] = f
     z = O.project(og, img)
     L, r = O.ls_loss(z, np.zeros_like(z))
     v = O.backproject(og, r)
+    t2 = time.perf_counter()
     I = rng.choice(g.n, n_I, replace=False)
     ghat = O.vjp(oa, theta, O.grid_coords(g.d, g.N, I), (g.n / w.batch) * v[I])
+    t3 = time.perf_counter()
     st = O.AdamState(np.zeros_like(theta), np.zeros_like(theta))
     O.adam_step(theta, ghat, st, lr=w.lr)
-    return time.perf_counter() - t0
+    t4 = time.perf_counter()
+    return ((t1 - t0) * g.n / n_pts + (t2 - t1) * g.V / Vs + (t3 - t2) * w.batch / n_I + (t4 - t3))
 
 
 def oracle_sample_any(w, frac: float, seed: int = 0) -> float:
@@ -151,32 +157,41 @@ def oracle_sample_any(w, frac: float, seed: int = 0) -> float:
     return oracle_sample(w, frac, seed)
 
 
-def oracle_rate(w, budget_s: float, frac: float):
-    """(steps/s, samples timed, frac) of the oracle within about budget_s seconds."""
-    oracle_sample_any(w, min(frac, 1 / 64))       # warm-up (builds the C projector)
-    total, k = 0.0, 0
-    while total < budget_s or k == 0:
+def oracle_frac(w, budget_s: float, frac_max: float) -> float:
+    """A sample fraction for which one oracle sample takes about budget_s / 4 seconds,
+    found from a tiny first sample (which also builds and warms the C projector)."""
+    q = w[0] if isinstance(w, list) else w
+    f0 = min(frac_max, max(1.0 / 65536, 2048.0 / q.geom.n))
+    t = time.perf_counter()
+    oracle_sample_any(w, f0)
+    dt = max(time.perf_counter() - t, 1e-3)
+    return min(frac_max, max(f0, f0 * (budget_s / 4) / dt))
+
+
+def oracle_rate(w, budget_s: float, frac_max: float):
+    """(steps/s, samples timed, fraction per sample) of the oracle within about budget_s seconds."""
+    frac = oracle_frac(w, budget_s, frac_max)
+    total, k, t0 = 0.0, 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or k == 0:
         total += oracle_sample_any(w, frac, seed=k)
         k += 1
-    per_step = total / k / frac
-    return 1.0 / per_step, k
+    return k / total, k, frac
 
 
 # ----------------------------------------------------------------------------
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
-    # each step is one oracle sample of a fraction of the step, sized so that the
-    # whole --steps run takes about two minutes
-    est = oracle_sample_any(w, 1 / 64) * 64            # also warms the C projector up
-    frac = min(1 / 16, max(1 / 512, 120.0 / (max(args.steps, 1) * est)))
+    # each step is one oracle sample of a fraction of the step (extrapolated to the whole
+    # step part by part), sized so that the whole --steps run takes about two minutes
+    steps = max(1, args.steps)
+    frac = oracle_frac(w, 4.0 * 120.0 / (steps + 2), 1 / 16)
     for _ in range(max(1, min(args.warmup, 2))):
         oracle_sample_any(w, frac)
     total = 0.0
-    steps = max(1, args.steps)
     for k in range(steps):
         total += oracle_sample_any(w, frac, seed=k)
-    value = steps * frac / total
+    value = steps / total
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
             "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
@@ -185,13 +200,29 @@ def run_reference(args, w, rank, world):
             "config": ({"workload": BATCHED, "problems": len(w)} if isinstance(w, list)
                        else {"workload": w.name, "note": w.note, "batch": w.batch}),
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{steps} samples of {frac:.4g} of a step each (forward "
+                             "sample": f"{steps} samples of about {frac:.4g} of a step each (forward "
                                        "on that fraction of the grid, P/P^T on that fraction of "
-                                       "the views, VJP on that fraction of |I|), full-step time "
-                                       "extrapolated linearly"},
+                                       "the views (at least one), VJP on that fraction of |I|), each "
+                                       "part extrapolated linearly to the full step"},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def recorded_traffic(kernel_key: str, workload: str):
+    """DRAM bytes per launch of a kernel from the committed ncu record, or None when
+    there is none or the kernel's source file changed since it was captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(f"{kernel_key}@{workload}")
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+        return None
+    return rec["dram_bytes_per_launch"]
 
 
 def mlp_flops(a, pts, vjp):
@@ -320,11 +351,11 @@ def run_batched(args, probs, rank, world, local, dev):
                 "peak_source": ("measured" if peaks else "fallback") + " (bf16 burst)", "traffic": None}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, k = oracle_rate(probs, budget_s=20.0, frac=1 / 32)
+        rate, k, fr = oracle_rate(probs, budget_s=20.0, frac_max=1 / 32)
         cpu = {"value": rate, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{k} samples of 1/32 of every problem's step (forward on n/32 points, P/P^T on "
-                         "V/32 views, VJP on |I|/32 points), summed over the 16 problems, full-step time "
-                         "extrapolated linearly"}
+               "sample": f"{k} samples of about {fr:.3g} of every problem's step (forward, P/P^T on at "
+                         "least one view, VJP), each part extrapolated linearly, summed over the 16 "
+                         "problems"}
     if rank == 0:
         sizes = sorted(q["geom"].N for q in state)
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
@@ -543,8 +574,12 @@ def main():
     per = {k: v / max(nprof, 1) for k, v in stages.items()}
     kernels = {}
     f_eval = mlp_flops(a, g.n, vjp=False)
-    f_vjp = mlp_flops(a, n_idx, vjp=True)
-    f_dw = dw_flops(a, n_idx)
+    # the VJP runs in chunks of at most VJP_CHUNK points; the profile marks bracket the
+    # first chunk's tile kernel, everything after it (further chunks, all GEMMs) is the
+    # "rest" stage
+    first = min(n_idx, VJP_CHUNK)
+    f_vjp = mlp_flops(a, first, vjp=True)
+    f_dw = dw_flops(a, n_idx) + mlp_flops(a, n_idx - first, vjp=True)
     if per["eval_mlp_kernel"] > 0:
         kernels["eval_mlp_kernel"] = {"ms": per["eval_mlp_kernel"],
                                       "TFLOP/s": f_eval / per["eval_mlp_kernel"] / 1e9}
@@ -552,8 +587,8 @@ def main():
         kernels["vjp_mlp_kernel"] = {"ms": per["vjp_mlp_kernel"],
                                      "TFLOP/s": f_vjp / per["vjp_mlp_kernel"] / 1e9}
     if per["vjp_dw_gemm_reduce"] > 0:
-        kernels["vjp_dw_gemm_reduce"] = {"ms": per["vjp_dw_gemm_reduce"],
-                                         "TFLOP/s": f_dw / per["vjp_dw_gemm_reduce"] / 1e9}
+        key = "vjp_dw_gemm_reduce" if n_idx <= VJP_CHUNK else "vjp_rest (further chunks + dW GEMMs)"
+        kernels[key] = {"ms": per["vjp_dw_gemm_reduce"], "TFLOP/s": f_dw / per["vjp_dw_gemm_reduce"] / 1e9}
     # projector: compulsory bytes = image once + sinogram out (+ y in, residual out)
     proj_bytes = 4.0 * (g.n + 3 * g.m)
     back_bytes = 4.0 * (g.n + g.m)
@@ -571,17 +606,19 @@ def main():
                                                  else "VJP") + ")",
                 "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": achieved / bf16_peak, "peak_source": f"{peak_src} (bf16 burst)",
-                "traffic": None}
+                "traffic": recorded_traffic("mlp_tile_kernel_" + ("eval" if dominant == "eval_mlp_kernel"
+                                                                  else "vjp"), w.name)}
     if args.prec != "bf16":
         roofline = {"kernel": "simt_fwd_kernel", "bound": "alu", "achieved": achieved, "peak": None,
                     "unit": "TFLOP/s", "frac": None, "traffic": None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, k = oracle_rate(w, budget_s=15.0, frac=1 / 16)
+        rate, k, fr = oracle_rate(w, budget_s=15.0, frac_max=1 / 16)
         cpu = {"value": rate, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{k} samples of 1/16 of a step each (forward on n/16 points, P/P^T on "
-                         "V/16 views, VJP on |I|/16 points), full-step time extrapolated linearly"}
+               "sample": f"{k} samples of about {fr:.3g} of a step each (forward on that fraction of "
+                         "the grid, P/P^T on that fraction of the views (at least one), VJP on that "
+                         "fraction of |I|), each part extrapolated linearly to the full step"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

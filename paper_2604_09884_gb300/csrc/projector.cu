@@ -406,11 +406,17 @@ __global__ void reduce_f64_kernel(const double* __restrict__ in, int64_t n, doub
 // rays, so that lane l always writes bank l: no conflicts and no atomics.  The
 // warps' accumulators are summed in a fixed order at the end (deterministic).
 constexpr int kBpTile = 32, kBpWarps = 8;
+// When an image has few tiles, each tile's views are split over S blocks that write S
+// partial images, summed in a fixed order afterwards: S is the smallest split that
+// gives about three blocks per SM of a 152-SM GPU.
+constexpr int kBpTargetBlocks = 3 * 152;
 constexpr size_t kBpSmem = sizeof(float) * ((size_t)kBpWarps * 2 * kBpTile * kBpTile + kBpTile * (kBpTile + 1));
 
 __global__ void __launch_bounds__(32 * kBpWarps)
     backproject2d_tile_kernel(GeomDev g, const int4* __restrict__ tab, const float2* __restrict__ views,
-                              const float* __restrict__ sino, float* __restrict__ img) {
+                              const float* __restrict__ sino, float* __restrict__ out, int nsplit) {
+  // view split blockIdx.z of nsplit writes its own partial image (the image itself if nsplit == 1)
+  float* img = out + (size_t)blockIdx.z * g.N * g.N;
   extern __shared__ float bsm[];
   float* accx = bsm + (size_t)(threadIdx.y * 2) * kBpTile * kBpTile;  // this warp's x-driven taps [q][lane]
   float* accy = accx + kBpTile * kBpTile;                              // y-driven taps [q][lane]
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(32 * kBpWarps)
   const float R = (float)(g.sod * (2.0 / N));
   const float hpar = (float)(1.0 / g.du) + 0.02f;
   __syncwarp();
-  for (int k = wv; k < g.V; k += kBpWarps) {
+  for (int k = blockIdx.z * kBpWarps + wv; k < g.V; k += nsplit * kBpWarps) {
     const float2 cs = views[k];
     const float cb = cs.x, sb = cs.y;
     // bins whose window (centre +- h, as for a single pixel) can reach a pixel of the tile
@@ -502,6 +508,15 @@ __global__ void __launch_bounds__(32 * kBpWarps)
     const int iy = y0 + r, ix = x0 + c;
     if (iy < N && ix < N) img[(size_t)iy * N + ix] = sx + fin[r * (kBpTile + 1) + c];
   }
+}
+
+// Sum of the nsplit partial images in split order.
+__global__ void bp_sum_kernel(const float* __restrict__ part, int nsplit, int64_t n, float* __restrict__ img) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float acc = part[i];
+  for (int s = 1; s < nsplit; ++s) acc += part[(int64_t)s * n + i];
+  img[i] = acc;
 }
 
 template <int ZC>
@@ -691,7 +706,18 @@ struct ProjWs {
   ProjTables t;
   float* imgT;
   double* loss_part;
+  float* bp_part;  // 2-D adjoint: partial images of the view splits (NULL: one split)
+  int bp_splits;
 };
+
+// Number of view splits of the 2-D adjoint (see backproject2d_tile_kernel).
+static int bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
+  if (geom->kind == INRCT_CONE3D) return 1;
+  const int tiles = ceil_div(grid->N, kBpTile) * ceil_div(grid->N, kBpTile);
+  const int want = ceil_div(kBpTargetBlocks, tiles);
+  const int most = std::max(1, geom->n_views / kBpWarps);
+  return std::max(1, std::min(want, most));
+}
 
 static size_t proj_layout(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t cap,
                           ProjWs* out, bool forward, bool with_tables, bool* ok) {
@@ -703,6 +729,8 @@ static size_t proj_layout(const inrct_geom* geom, const inrct_grid* grid, void* 
   const int64_t blocks = cone ? (int64_t)ceil_div(geom->n_bins_u, 32) * geom->n_bins_v * geom->n_views
                               : (int64_t)ceil_div(num_rays(geom), 32);
   w.loss_part = forward ? c.take<double>(blocks) : nullptr;
+  w.bp_splits = forward ? 1 : bp_splits(geom, grid);
+  w.bp_part = w.bp_splits > 1 ? c.take<float>((size_t)w.bp_splits * grid_points(grid)) : nullptr;
   if (out) *out = w;
   if (ok) *ok = c.ok;
   return c.off + 256;
@@ -819,9 +847,15 @@ int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float
       attr_set = true;
     }
     dim3 blk(32, kBpWarps);
-    dim3 grd(ceil_div(g.N, kBpTile), ceil_div(g.N, kBpTile));
-    backproject2d_tile_kernel<<<grd, blk, kBpSmem, st>>>(g, w.t.tab0, w.t.views, sino, image);
+    dim3 grd(ceil_div(g.N, kBpTile), ceil_div(g.N, kBpTile), w.bp_splits);
+    backproject2d_tile_kernel<<<grd, blk, kBpSmem, st>>>(g, w.t.tab0, w.t.views, sino,
+                                                         w.bp_splits > 1 ? w.bp_part : image, w.bp_splits);
     INRCT_CHECK_LAUNCH("backproject2d");
+    if (w.bp_splits > 1) {
+      const int64_t n = (int64_t)g.N * g.N;
+      bp_sum_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(w.bp_part, w.bp_splits, n, image);
+      INRCT_CHECK_LAUNCH("backproject2d (split sum)");
+    }
   }
   return INRCT_OK;
 }
