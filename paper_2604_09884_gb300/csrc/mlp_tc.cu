@@ -48,11 +48,19 @@ namespace {
 
 constexpr int kTile = 128;       // points per tile (MMA M)
 constexpr int kNSplit = 1;       // MMA N-groups per weight K-panel: N = W / kNSplit
-constexpr int kRingBytes = 64 * 1024;  // weight ring: kRingBytes / (W / kNSplit * 128 B) slots
+constexpr int kKChunk = 64;      // K per weight ring slot (16, 32 or 64: 32-, 64-, 128-byte swizzle);
+                                 // 64 measured fastest: each slot costs a fixed hand-off
+// Weight ring: ring_bytes(mode) / (W / kNSplit * 2 kKChunk B) slots.  Evaluation takes the
+// deepest ring that fits; the VJP keeps 64 KB so that more of the SM's L1 is left for its
+// sigma' and scratch traffic.
+__host__ __device__ constexpr int ring_bytes(int mode) { return mode == 0 ? 96 * 1024 : 64 * 1024; }
 constexpr int kRingMax = 8;
+// 64-bit words after the ring: 2 kRingMax + 31 barriers, then tmem base and abort flag (one word)
+constexpr int kTileBars = 2 * kRingMax + 31 + 1;
 constexpr int kPanelBytes = kTile * 128;  // one 64-column BF16 panel of 128 rows
 constexpr int kMaxStages = 2 * kMaxLayers;
 constexpr int kMaxJobs = 24;
+constexpr int kMaxSplits = 16;   // split-K factor of the weight-gradient GEMM
 
 // ---------------------------------------------------------------------------
 // host: tensor maps
@@ -73,7 +81,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D BF16 row-major tensor [outer][inner], 128-byte swizzled boxes of {box_inner, box_outer}.
 int make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-             uint32_t box_outer) {
+             uint32_t box_outer, int swizzle_bytes = 128) {
   auto fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is unavailable from the driver");
@@ -84,7 +92,9 @@ int make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, u
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                       : (swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d): dims %llu x %llu box %u x %u", (int)r,
@@ -108,12 +118,35 @@ struct PrepTable {
   __nv_bfloat16* Wb[kMaxLayers];
   __nv_bfloat16* WbT[kMaxLayers];
   float* bias[kMaxLayers];
+  // the row blockIdx.y == n fills the small tables the tile kernel reads through L1:
+  // first-layer table (SIREN {w'_0, w'_1, w'_2, b'} per output; FFN {B_0, B_1, B_2, 0} per
+  // feature) and an aligned copy of the output-layer weights
+  int kind, d, n_first, W;
+  int64_t offW0, offb0, offWout;
+  const float* B;
+  float4* first;
+  float* wout;
 };
 
 // All MMA layers in one launch: blockIdx.y selects the layer.
 __global__ void prep_all_kernel(const float* __restrict__ theta, const __grid_constant__ PrepTable T,
                                 float scale) {
   const int l = blockIdx.y;
+  if (l == T.n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.n_first; i += gridDim.x * blockDim.x) {
+      if (T.kind == INRCT_SIREN) {
+        const float* w1 = theta + T.offW0 + (int64_t)i * T.d;
+        T.first[i] = make_float4(scale * w1[0], scale * w1[1], T.d == 3 ? scale * w1[2] : 0.f,
+                                 scale * theta[T.offb0 + i]);
+      } else {
+        const float* bf = T.B + (int64_t)i * T.d;
+        T.first[i] = make_float4(bf[0], bf[1], T.d == 3 ? bf[2] : 0.f, 0.f);
+      }
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.W; i += gridDim.x * blockDim.x)
+      T.wout[i] = theta[T.offWout + i];
+    return;
+  }
   const int out = T.out[l], in = T.in[l];
   const int64_t cnt = (int64_t)out * in;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
@@ -154,6 +187,11 @@ struct GemmPlan {
   int64_t per_split;  // points per split (multiple of 64)
   int cta_begin[kMaxJobs + 1];
   GemmJob job[kMaxJobs];
+  // output-layer bias gradient: FP64 partial sums of scale * v_i from the VJP tile kernel,
+  // summed by the reduction's extra block row into grad[off_bout] (n_bpart == 0: none)
+  const double* bpart;
+  int n_bpart;
+  int64_t off_bout;
 };
 
 constexpr int kGemmStages = 4;
@@ -292,6 +330,20 @@ __global__ void __launch_bounds__(192, 1)
 __global__ void gemm_reduce_kernel(const __grid_constant__ GemmPlan plan, const float* __restrict__ part,
                                    int accumulate, double* __restrict__ grad) {
   const int jb = blockIdx.y;
+  if (jb == plan.n_jobs) {  // output bias: fixed-order tree over the partials
+    if (blockIdx.x != 0) return;
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < plan.n_bpart; i += blockDim.x) s += plan.bpart[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) grad[plan.off_bout] = accumulate ? grad[plan.off_bout] + sh[0] : sh[0];
+    return;
+  }
   const GemmJob& J = plan.job[jb];
   const int cols = J.w_cols + (J.offb >= 0 ? 1 : 0);
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -307,45 +359,19 @@ __global__ void gemm_reduce_kernel(const __grid_constant__ GemmPlan plan, const 
     col = J.N;  // first column of the ones block
     dst = J.offb + m;
   }
+  // all split partials are loaded before the in-order FP64 sum (independent loads in flight)
+  float pv[kMaxSplits];
+#pragma unroll
+  for (int q = 0; q < kMaxSplits; ++q)
+    pv[q] = q < plan.S ? part[J.part_off + ((int64_t)q * J.M + m) * ldc + col] : 0.f;
   double s = 0.0;
-  for (int q = 0; q < plan.S; ++q) s += (double)part[J.part_off + ((int64_t)q * J.M + m) * ldc + col];
+#pragma unroll
+  for (int q = 0; q < kMaxSplits; ++q)
+    if (q < plan.S) s += (double)pv[q];
   s *= J.mult;
   grad[dst] = accumulate ? grad[dst] + s : s;
 }
 
-// Output-layer bias gradient: grad[off] (+)= sum_k scale * v[idx[k]] (FP64).  Pass 1: one
-// partial per block (fixed order); pass 2: one block sums the partials in order.
-constexpr int kBiasBlocks = 128;
-__global__ void out_bias_partial_kernel(const int32_t* __restrict__ idx, int64_t npts,
-                                        const float* __restrict__ v, int64_t n_grid, float scale,
-                                        double* __restrict__ part) {
-  __shared__ double sh[256];
-  double s = 0.0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npts;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx[k];
-    if (i >= 0 && i < n_grid) s += (double)(scale * v[i]);
-  }
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
-}
-
-__global__ void out_bias_final_kernel(const double* __restrict__ part, int n, int accumulate,
-                                      double* __restrict__ grad) {
-  __shared__ double sh[kBiasBlocks];
-  sh[threadIdx.x] = threadIdx.x < n ? part[threadIdx.x] : 0.0;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) grad[0] = accumulate ? grad[0] + sh[0] : sh[0];
-}
 
 // ---------------------------------------------------------------------------
 // fused MLP tile engine
@@ -360,6 +386,10 @@ struct TileProg {
   const float* B;       // F x d (FFN)
   const float* theta;   // FP32 parameters (SIREN first layer, output layer)
   const float* bias;    // folded FP32 biases, [L][W]
+  const float4* first;  // first-layer table (see PrepTable)
+  int n_first;          // its entries (SIREN W, FFN F)
+  int first_staged;     // VJP: the table fits the shared-memory staging area
+  const float* wout;    // output-layer weights [W], 16-byte aligned
   int64_t offW0, offb0, offWout, offbout;  // theta offsets (first layer, output layer)
   int n_stages;
   int st_kind[kMaxStages], st_layer[kMaxStages], st_panels[kMaxStages], st_map[kMaxStages];
@@ -383,6 +413,7 @@ struct TileProg {
   int map_act, map_dlt;         // tensor maps (in the kernel's Maps) for the panel stores
   __nv_bfloat16* Y16c;  // [16][npts_pad] coordinates (SIREN)
   __nv_bfloat16* Y16o;  // [16][npts_pad] output-layer weights scale * v
+  double* bias_part;    // [gridDim.x][4] FP64 sums of scale * v_i (output-layer bias gradient)
   int64_t npts_pad;
   int stall;            // diagnostic: the producer issues nothing (tests bounded waits)
 };
@@ -422,12 +453,6 @@ __device__ __forceinline__ float four_feat(float ph, bool want_sin) {
   return want_sin ? s : c;
 }
 
-// Parameters staged in shared memory after the panels and the ring (FP32):
-// bias [L][W] (omega0 folded for SIREN), w_out [W], and the first-layer table:
-// SIREN float4 {w'_0, w'_1, w'_2, b'} per output, FFN float4 {B_0, B_1, B_2, 0} per feature.
-__host__ __device__ inline size_t param_floats(int L, int W, int F, int kind) {
-  return (size_t)L * W + W + 4 * (size_t)(kind == INRCT_SIREN ? W : F);
-}
 
 // Two tiles are in flight per CTA (slots 0 and 1), each with one FP32 accumulator of
 // W TMEM columns and its own four input panels.  The MMA issuer alternates the slots
@@ -453,23 +478,42 @@ template <int MODE, int KIND, int NWG>
 __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     mlp_tile_kernel(const __grid_constant__ Maps maps, const __grid_constant__ TileProg P,
                     int* __restrict__ err) {
+  // Dynamic shared memory only (no static): [8 input panels][weight ring][barriers][dot scratch].
+  // The panels and the ring need 1024-byte alignment (128-byte swizzle atoms); the dynamic
+  // window starts there when the kernel has no static shared memory, which is checked.
   extern __shared__ __align__(1024) uint8_t dsm[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  if ((smem_u32(dsm) & 1023u) != 0) {
+    if (threadIdx.x == 0) atomicExch(err, 901);
+    return;
+  }
+  uint8_t* smem = dsm;
   const int W = P.W;
-  uint8_t* apan = smem;                          // 2 slots x 4 x 16 KB input panels
   const int NW = W / kNSplit;                    // MMA N and weight rows per ring slot
-  uint8_t* ring = smem + 8 * kPanelBytes;        // n_ring x (NW x 128 B) weight chunks
-  const uint32_t chunk_bytes = (uint32_t)NW * 128;
-  const int n_ring = kRingBytes / (int)chunk_bytes;
-  float* bias_s = reinterpret_cast<float*>(ring + kRingBytes);
-  float* wout_s = bias_s + (size_t)P.L * W;
-  float4* first_s = reinterpret_cast<float4*>(wout_s + W);
+  uint8_t* apan = smem;                          // 2 slots x 4 x 16 KB input panels
+  uint8_t* ring = smem + 8 * kPanelBytes;        // n_ring x (NW x 2 kKChunk B) weight chunks
+  const uint32_t chunk_bytes = (uint32_t)NW * (2 * kKChunk);
+  const int n_ring = ring_bytes(MODE) / (int)chunk_bytes;
   constexpr int CW = 64 / NWG, EPI_WARPS = 4 * NWG;  // one arrival per epilogue warp
-  __shared__ uint64_t w_full[kRingMax], w_empty[kRingMax], in_ready[2], acc_full[2], a_full[2][4],
-      a_empty[2][4], dot_bar[2][4], st_done[2], drain_bar;
-  __shared__ float dotp[2][NWG][kTile];
-  __shared__ uint32_t tmem_base;
-  __shared__ volatile int abort_flag;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + ring_bytes(MODE));
+  uint64_t* w_full = bars;                       // [kRingMax]
+  uint64_t* w_empty = w_full + kRingMax;         // [kRingMax]
+  uint64_t* in_ready = w_empty + kRingMax;       // [2]
+  uint64_t* acc_full = in_ready + 2;             // [2]
+  uint64_t* a_full = acc_full + 2;               // [2][4]
+  uint64_t* a_empty = a_full + 8;                // [2][4]
+  uint64_t* dot_bar = a_empty + 8;               // [4] per row quarter: partial dots written
+  uint64_t* dot_free = dot_bar + 4;              // [4]: the summing warp has read them
+  uint64_t* st_done = dot_free + 4;              // [2]
+  uint64_t* drain_bar = st_done + 2;
+  uint32_t* tmem_base = reinterpret_cast<uint32_t*>(drain_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base + 1);
+  float* dotp = reinterpret_cast<float*>(bars + kTileBars);  // [NWG][kTile]
+  // VJP (64 KB ring): the small parameter tables are staged in shared memory after the dot
+  // scratch; evaluation (96 KB ring) reads them from global memory through L1.
+  constexpr bool kStage = MODE == 1;
+  float* bias_s = dotp + NWG * kTile;                   // [L][W]
+  float* wout_s = bias_s + (size_t)P.L * W;             // [W]
+  float4* first_s = reinterpret_cast<float4*>(wout_s + W);  // [n_first] when P.first_staged
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_tiles = (P.npts + kTile - 1) / kTile;
   // this CTA's tiles are blockIdx.x + j * gridDim.x; they are taken in pairs (slot 0, slot 1)
@@ -486,35 +530,29 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
       mbar_init(&acc_full[t], 1);
       mbar_init(&st_done[t], 1);
       for (int s = 0; s < 4; ++s) {
-        mbar_init(&a_full[t][s], EPI_WARPS);
-        mbar_init(&a_empty[t][s], 1);
-        mbar_init(&dot_bar[t][s], NWG);
+        mbar_init(&a_full[4 * t + s], EPI_WARPS);
+        mbar_init(&a_empty[4 * t + s], 1);
       }
     }
-    mbar_init(&drain_bar, 1);
-    abort_flag = 0;
+    for (int q = 0; q < 4; ++q) {
+      mbar_init(&dot_bar[q], NWG);
+      mbar_init(&dot_free[q], 1);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
     fence_mbar_init();
   }
-  // stage the small parameters
-  for (int i = threadIdx.x; i < P.L * W; i += blockDim.x) bias_s[i] = P.bias[i];
-  for (int i = threadIdx.x; i < W; i += blockDim.x) wout_s[i] = P.theta[P.offWout + i];
-  if (KIND == INRCT_SIREN) {
-    for (int o = threadIdx.x; o < W; o += blockDim.x) {
-      const float* w1 = P.theta + P.offW0 + (int64_t)o * P.d;
-      first_s[o] = make_float4(P.omega0 * w1[0], P.omega0 * w1[1], P.d == 3 ? P.omega0 * w1[2] : 0.f,
-                               P.omega0 * P.theta[P.offb0 + o]);
-    }
-  } else {
-    for (int f = threadIdx.x; f < P.F; f += blockDim.x) {
-      const float* bf = P.B + (int64_t)f * P.d;
-      first_s[f] = make_float4(bf[0], bf[1], P.d == 3 ? bf[2] : 0.f, 0.f);
-    }
+  if (kStage) {
+    for (int i = threadIdx.x; i < P.L * W; i += blockDim.x) bias_s[i] = P.bias[i];
+    for (int i = threadIdx.x; i < W; i += blockDim.x) wout_s[i] = P.wout[i];
+    if (P.first_staged)
+      for (int i = threadIdx.x; i < P.n_first; i += blockDim.x) first_s[i] = P.first[i];
   }
-  if (warp == 0) tmem_alloc(&tmem_base, 2 * W);
+  if (warp == 0) tmem_alloc(tmem_base, 2 * W);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = tmem_base;
+  const uint32_t tmem = *tmem_base;
 
   if (warp == 4 * NWG) {
     // ---------------- TMA producer ----------------
@@ -525,13 +563,16 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
         for (int s = 0; s < P.n_stages; ++s) {
           for (int t = 0; t < 2; ++t) {
             for (int c = 0; c < P.st_panels[s]; ++c) {
-              for (int h = 0; h < kNSplit; ++h) {
-                if (!mbar_wait(&w_empty[slot], ep, &abort_flag, err, 201)) goto producer_done;
-                mbar_arrive_expect_tx(&w_full[slot], chunk_bytes);
-                tma_load_2d(ring + slot * chunk_bytes, &maps.m[P.st_map[s]], &w_full[slot], 64 * c, h * NW);
-                if (++slot == n_ring) {
-                  slot = 0;
-                  ep ^= 1;
+              for (int kk = 0; kk < 64 / kKChunk; ++kk) {
+                for (int h = 0; h < kNSplit; ++h) {
+                  if (!mbar_wait(&w_empty[slot], ep, abort_flag, err, 201)) goto producer_done;
+                  mbar_arrive_expect_tx(&w_full[slot], chunk_bytes);
+                  tma_load_2d(ring + slot * chunk_bytes, &maps.m[P.st_map[s]], &w_full[slot],
+                              64 * c + kKChunk * kk, h * NW);
+                  if (++slot == n_ring) {
+                    slot = 0;
+                    ep ^= 1;
+                  }
                 }
               }
             }
@@ -562,7 +603,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
         const int64_t tile0 = blockIdx.x + (2 * pr) * (int64_t)gridDim.x;
         for (int s = 0; s < P.n_stages; ++s) {
           for (int t = 0; t < 2; ++t) {
-            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, &abort_flag, err, 301)) goto mma_done;
+            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, abort_flag, err, 301)) goto mma_done;
             irp ^= 1u << t;
             tc_fence_after();
             if (MODE == 1 && P.st_in_arr[s] >= 0 && tile0 + t * gridDim.x < n_tiles)
@@ -573,28 +614,33 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               const int as = c & 3;
               if (c >= 4) {  // a streamed input panel (first stage only)
                 const int bit = 4 * t + as;
-                if (!mbar_wait(&a_full[t][as], (ap >> bit) & 1u, &abort_flag, err, 302)) goto mma_done;
+                if (!mbar_wait(&a_full[4 * t + as], (ap >> bit) & 1u, abort_flag, err, 302)) goto mma_done;
                 ap ^= 1u << bit;
                 tc_fence_after();
               }
               const uint32_t abase = smem_u32(apan + (4 * t + as) * kPanelBytes);
-              for (int h = 0; h < kNSplit; ++h) {
-                if (!mbar_wait(&w_full[slot], wf, &abort_flag, err, 303)) goto mma_done;
-                tc_fence_after();
-                const uint32_t bbase = smem_u32(ring + slot * chunk_bytes);
-                const uint32_t dcol = tmem + t * W + h * NW;
+              for (int kk = 0; kk < 64 / kKChunk; ++kk) {
+                for (int h = 0; h < kNSplit; ++h) {
+                  if (!mbar_wait(&w_full[slot], wf, abort_flag, err, 303)) goto mma_done;
+                  tc_fence_after();
+                  const uint32_t bbase = smem_u32(ring + slot * chunk_bytes);
+                  const uint32_t dcol = tmem + t * W + h * NW;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                  mma_bf16(dcol, desc_sw128(abase + 32 * j, 16, 1024),
-                           desc_sw128(bbase + 32 * j, 16, 1024), idesc, (c > 0 || j > 0) ? 1u : 0u);
-                issued = true;
-                mma_commit(&w_empty[slot]);
-                if (++slot == n_ring) {
-                  slot = 0;
-                  wf ^= 1;
+                  for (int j = 0; j < kKChunk / 16; ++j) {
+                    const int ks = kk * (kKChunk / 16) + j;  // K=16 step within the 64-wide panel
+                    mma_bf16(dcol, desc_sw128(abase + 32 * ks, 16, 1024),
+                             desc_sw(bbase + 32 * j, 16, 16 * kKChunk, 2 * kKChunk), idesc,
+                             (c > 0 || ks > 0) ? 1u : 0u);
+                  }
+                  issued = true;
+                  mma_commit(&w_empty[slot]);
+                  if (++slot == n_ring) {
+                    slot = 0;
+                    wf ^= 1;
+                  }
                 }
               }
-              if (c + 4 < np) mma_commit(&a_empty[t][as]);  // the buffer takes panel c + 4 next
+              if (c + 4 < np) mma_commit(&a_empty[4 * t + as]);  // the buffer takes panel c + 4 next
             }
             if (MODE == 1) bulk_wait_read_all();
             mma_commit(&acc_full[t]);
@@ -604,7 +650,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           // the deltas of the last stage: stored, then the feature pass of the next pair may
           // overwrite the panels
           for (int t = 0; t < 2; ++t) {
-            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, &abort_flag, err, 304)) goto mma_done;
+            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, abort_flag, err, 304)) goto mma_done;
             irp ^= 1u << t;
             if (tile0 + t * gridDim.x < n_tiles) store_panels(t, P.map_dlt, P.tail_layer, tile0 + t * gridDim.x);
             bulk_wait_read_all();
@@ -617,8 +663,8 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
       if (issued) {
         // drain: every issued MMA completes before TMEM is released (matters on the
         // abort path; otherwise the epilogue has already waited for all of them)
-        mma_commit(&drain_bar);
-        mbar_wait_drain(&drain_bar, 0);
+        mma_commit(drain_bar);
+        mbar_wait_drain(drain_bar, 0);
       }
     }
   } else {
@@ -626,7 +672,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     const int q = warp & 3, g = warp >> 2;
     const int r = q * 32 + lane;                 // row of the tile = TMEM lane
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    uint32_t ae = 0u, af = 0u, dotph = 0u, sdp = 0u;  // phase parities (a_empty per slot and buffer; per slot)
+    uint32_t ae = 0u, af = 0u, sdp = 0u, dot_uses = 0u;  // phase parities (a_empty per slot and buffer; per slot)
     // offset of this thread's CW sigma' values of (layer, tile, 64-column chunk c) in P.Sg
     auto sg_off = [&](int layer, int64_t tile, int c) -> int64_t {
       return ((((int64_t)layer * n_tiles + tile) * (W / 64) + c) * NWG + g) * (kTile * CW) + (int64_t)r * CW;
@@ -634,6 +680,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     const float bout = P.theta[P.offbout];
     const int n0 = P.in_panels < 4 ? P.in_panels : 4;  // first-stage panels published together
     float v[CW];
+    double bsum = 0.0;  // VJP: this row's share of sum scale * v_i (warps of column group 0)
     for (int64_t pr = 0; pr < n_pairs; ++pr) {
       // per-slot point data, kept in scalars (slot t selects with a conditional)
       const int64_t tile0 = blockIdx.x + (2 * pr) * (int64_t)gridDim.x;
@@ -653,6 +700,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
         setup(tile0, x0, sv0, valid0);
         setup(tile1, x1, sv1, valid1);
       }
+      if (MODE == 1 && g == 0) bsum += (double)sv0 + (double)sv1;
       // ---- first stage input of both slots ----
       for (int t = 0; t < 2; ++t) {
         const int64_t prow_t = (t ? tile1 : tile0) * kTile + r;  // scratch row (padded to the tile)
@@ -661,7 +709,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
         const float xt[3] = {t ? x1[0] : x0[0], t ? x1[1] : x0[1], t ? x1[2] : x0[2]};
         if (MODE == 1 && pr > 0) {
           // the previous pair's last deltas are still being stored from these panels
-          if (!warp_wait(&st_done[t], (sdp >> t) & 1u, &abort_flag, err, 405)) goto epi_done;
+          if (!warp_wait(&st_done[t], (sdp >> t) & 1u, abort_flag, err, 405)) goto epi_done;
           sdp ^= 1u << t;
         }
         for (int c = 0; c < P.in_panels; ++c) {
@@ -671,7 +719,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
             const int f0 = is_sin ? col0 - P.F : col0;
 #pragma unroll
             for (int i = 0; i < CW; ++i) {
-              const float4 bf = first_s[f0 + i];
+              const float4 bf = (kStage && P.first_staged) ? first_s[f0 + i] : __ldg(P.first + f0 + i);
               float ph = __fadd_rn(__fmul_rn(bf.x, xt[0]), __fmul_rn(bf.y, xt[1]));
               if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, xt[2]));
               v[i] = four_feat(ph, is_sin);
@@ -681,7 +729,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
             float cs[CW];
 #pragma unroll
             for (int i = 0; i < CW; ++i) {
-              const float4 w1 = first_s[col0 + i];
+              const float4 w1 = (kStage && P.first_staged) ? first_s[col0 + i] : __ldg(P.first + col0 + i);
               const float z = fmaf(w1.x, xt[0], fmaf(w1.y, xt[1], fmaf(w1.z, xt[2], w1.w)));
               if (MODE == 1)
                 __sincosf(z, &v[i], &cs[i]);
@@ -700,7 +748,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           const int as = c & 3;
           if (c >= 4) {  // streamed panel: the MMA must have read panel c - 4 from this buffer
             const int bit = 4 * t + as;
-            if (!warp_wait(&a_empty[t][as], (ae >> bit) & 1u, &abort_flag, err, 401)) goto epi_done;
+            if (!warp_wait(&a_empty[4 * t + as], (ae >> bit) & 1u, abort_flag, err, 401)) goto epi_done;
             ae ^= 1u << bit;
           }
           st_panel_row<CW>(apan + (4 * t + as) * kPanelBytes, r, (CW / 8) * g, v);
@@ -713,7 +761,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           } else if (c >= 4) {
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&a_full[t][as]);
+            if (lane == 0) mbar_arrive(&a_full[4 * t + as]);
           }
         }
       }
@@ -738,7 +786,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               sgn[k] = store_t ? reinterpret_cast<const uint4*>(P.Sg + sg_off(l - 1, tile_t, 0))[k]
                                : make_uint4(0, 0, 0, 0);
           }
-          if (!warp_wait(&acc_full[t], (af >> t) & 1u, &abort_flag, err, 402)) goto epi_done;
+          if (!warp_wait(&acc_full[t], (af >> t) & 1u, abort_flag, err, 402)) goto epi_done;
           af ^= 1u << t;
           tc_fence_after();
           float dot = 0.f;
@@ -771,11 +819,11 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                 for (int i = 0; i < CW; ++i) v[i] *= sg[i];
               }
             } else {
-              const float4* bl = reinterpret_cast<const float4*>(bias_s + (size_t)l * W + col0);
+              const float4* bl = reinterpret_cast<const float4*>((kStage ? bias_s : P.bias) + (size_t)l * W + col0);
               float cs[CW];
 #pragma unroll
               for (int i4 = 0; i4 < CW / 4; ++i4) {
-                const float4 bb = bl[i4];
+                const float4 bb = kStage ? bl[i4] : __ldg(bl + i4);
                 const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -798,11 +846,11 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                   store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
               }
               if (kind == kFwdLast) {
-                const float4* wo = reinterpret_cast<const float4*>(wout_s + col0);
+                const float4* wo = reinterpret_cast<const float4*>((kStage ? wout_s : P.wout) + col0);
                 if (MODE == 0) {
 #pragma unroll
                   for (int i4 = 0; i4 < CW / 4; ++i4) {
-                    const float4 ww = wo[i4];
+                    const float4 ww = kStage ? wo[i4] : __ldg(wo + i4);
                     dot = fmaf(v[4 * i4], ww.x, dot);
                     dot = fmaf(v[4 * i4 + 1], ww.y, dot);
                     dot = fmaf(v[4 * i4 + 2], ww.z, dot);
@@ -812,7 +860,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                   // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
 #pragma unroll
                   for (int i4 = 0; i4 < CW / 4; ++i4) {
-                    const float4 ww = wo[i4];
+                    const float4 ww = kStage ? wo[i4] : __ldg(wo + i4);
                     v[4 * i4] = sv_t * ww.x * cs[4 * i4];
                     v[4 * i4 + 1] = sv_t * ww.y * cs[4 * i4 + 1];
                     v[4 * i4 + 2] = sv_t * ww.z * cs[4 * i4 + 2];
@@ -829,23 +877,32 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           __syncwarp();
           if (pub && lane == 0) mbar_arrive(&in_ready[t]);
           if (MODE == 0 && kind == kFwdLast) {
-            // out = b_out + sum of the NWG column-group partial dot products of row r
-            dotp[t][g][r] = dot;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&dot_bar[t][q]);
-            if (g == 0) {
-              if (!warp_wait(&dot_bar[t][q], (dotph >> t) & 1u, &abort_flag, err, 404)) goto epi_done;
-              dotph ^= 1u << t;
-              if (valid_t) {
-                float f = bout;
-#pragma unroll
-                for (int q2 = 0; q2 < NWG; ++q2) f += dotp[t][q2][r];
-                P.out[prow_t] = f;
-              }
+            // out = b_out + sum of the NWG column-group partial dot products of row r; one
+            // scratch buffer per row quarter, released by its summing warp (dot_free)
+            if (dot_uses > 0) {
+              if (!warp_wait(&dot_free[q], (dot_uses - 1) & 1u, abort_flag, err, 406)) goto epi_done;
             }
+            dotp[g * kTile + r] = dot;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&dot_bar[q]);
+            if (g == 0) {
+              if (!warp_wait(&dot_bar[q], dot_uses & 1u, abort_flag, err, 404)) goto epi_done;
+              float f = bout;
+#pragma unroll
+              for (int q2 = 0; q2 < NWG; ++q2) f += dotp[q2 * kTile + r];
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&dot_free[q]);
+              if (valid_t) P.out[prow_t] = f;
+            }
+            ++dot_uses;
           }
         }
       }
+    }
+    if (MODE == 1 && g == 0) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) bsum += __shfl_down_sync(0xffffffffu, bsum, o);
+      if (lane == 0) P.bias_part[(int64_t)blockIdx.x * 4 + q] = bsum;
     }
   epi_done:;
   }
@@ -875,16 +932,27 @@ int num_sms() {
   return n;
 }
 
-size_t tile_smem(const Net& n) {
-  return 8 * (size_t)kPanelBytes + (size_t)kRingBytes +
-         sizeof(float) * param_floats(n.L, n.W, n.F, n.kind) + 1024;
+constexpr int kTileNWG = 4;  // epilogue warpgroups of the tile kernel
+
+size_t tile_smem_base(int mode) {
+  return 8 * (size_t)kPanelBytes + (size_t)ring_bytes(mode) + 8 * (size_t)kTileBars +
+         sizeof(float) * (size_t)kTileNWG * kTile;
+}
+// VJP: biases and output weights staged, and the first-layer table too when it fits
+bool first_fits(const Net& n) {
+  const size_t n_first = n.kind == INRCT_SIREN ? n.W : n.F;
+  return tile_smem_base(1) + sizeof(float) * ((size_t)n.L * n.W + n.W) + 16 * n_first <= 232448;
+}
+size_t tile_smem(const Net& n, int mode = 0) {
+  if (mode == 0) return tile_smem_base(0);
+  const size_t n_first = n.kind == INRCT_SIREN ? n.W : n.F;
+  return tile_smem_base(1) + sizeof(float) * ((size_t)n.L * n.W + n.W) + (first_fits(n) ? 16 * n_first : 0);
 }
 
-constexpr int kTileNWG = 4;  // epilogue warpgroups of the tile kernel
 
 template <int MODE, int KIND>
 int launch_tile_t(const Net& n, const Maps& maps, const TileProg& P, int grid, int* err, cudaStream_t st) {
-  const size_t sm = tile_smem(n);
+  const size_t sm = tile_smem(n, MODE);
   cudaError_t e = cudaFuncSetAttribute(mlp_tile_kernel<MODE, KIND, kTileNWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
@@ -910,6 +978,8 @@ struct TcWeights {
   __nv_bfloat16* Wb[kMaxLayers];
   __nv_bfloat16* WbT[kMaxLayers];
   float* bias;
+  float4* first;  // SIREN: W entries; FFN: F entries
+  float* wout;    // W
 };
 
 // Layers handled by the MMA stages: FFN 0..L-1, SIREN 1..L-1 (the SIREN first layer is FP32).
@@ -918,6 +988,8 @@ int first_mma_layer(const Net& n) { return n.kind == INRCT_SIREN ? 1 : 0; }
 // BF16 weights (and their transposes) plus FP32 biases, laid out in order.
 void weights_layout(const Net& n, Carver& c, TcWeights* w) {
   w->bias = c.take<float>((size_t)n.L * n.W);
+  w->first = c.take<float4>((size_t)(n.kind == INRCT_SIREN ? n.W : n.F));
+  w->wout = c.take<float>((size_t)n.W);
   for (int l = 0; l < kMaxLayers; ++l) w->Wb[l] = w->WbT[l] = nullptr;
   for (int l = first_mma_layer(n); l < n.L; ++l) {
     w->Wb[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
@@ -948,9 +1020,19 @@ int prep_weights(const Net& n, const float* theta, const TcWeights& w, cudaStrea
     T.bias[i] = w.bias + (int64_t)l * n.W;
     most = std::max<int64_t>(most, (int64_t)n.in_dim[l] * n.out_dim[l]);
   }
-  if (T.n == 0) return INRCT_OK;
+  T.kind = n.kind;
+  T.d = n.d;
+  T.W = n.W;
+  T.n_first = n.kind == INRCT_SIREN ? n.W : n.F;
+  T.offW0 = n.offW[0];
+  T.offb0 = n.offb[0];
+  T.offWout = n.offW[n.L];
+  T.B = n.B;
+  T.first = w.first;
+  T.wout = w.wout;
   const float sc = n.kind == INRCT_SIREN ? n.omega0 : 1.f;
-  dim3 grd((unsigned)std::min<int64_t>(ceil_div(most, 256), 512), T.n);
+  most = std::max<int64_t>(most, T.n_first);
+  dim3 grd((unsigned)std::min<int64_t>(ceil_div(most, 256), 512), T.n + 1);
   prep_all_kernel<<<grd, 256, 0, st>>>(theta, T, sc);
   INRCT_CHECK_LAUNCH("weight preparation");
   return INRCT_OK;
@@ -977,6 +1059,10 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
   P->omega0 = n.omega0;
   P->B = n.B;
   P->bias = w.bias;
+  P->first = w.first;
+  P->n_first = n.kind == INRCT_SIREN ? n.W : n.F;
+  P->first_staged = first_fits(n) ? 1 : 0;
+  P->wout = w.wout;
   P->offW0 = n.offW[0];
   P->offb0 = n.offb[0];
   P->offWout = n.offW[n.L];
@@ -994,7 +1080,8 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
                   P->st_panels[s]);
     P->st_map[s] = mi;
     // a ring slot holds out_dim / kNSplit output rows x 64 K (see mlp_tile_kernel)
-    INRCT_TRY(make_map(&maps->m[mi++], w.Wb[l], n.in_dim[l], n.out_dim[l], 64, n.out_dim[l] / kNSplit));
+    INRCT_TRY(make_map(&maps->m[mi++], w.Wb[l], n.in_dim[l], n.out_dim[l], kKChunk, n.out_dim[l] / kNSplit,
+                       2 * kKChunk));
     INRCT_REQUIRE(n.out_dim[l] == n.W, "tile kernel: MMA layer %d has %d outputs, expected %d", l,
                   n.out_dim[l], n.W);
   }
@@ -1009,7 +1096,8 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
       // W'_l^T is [in][out]: rows = in (the MMA N), K = out; chunks of in / kNSplit rows
       INRCT_REQUIRE(n.in_dim[l] == n.W, "tile kernel: backward stage %d has N=%d, expected %d", l,
                     n.in_dim[l], n.W);
-      INRCT_TRY(make_map(&maps->m[mi++], w.WbT[l], n.out_dim[l], n.in_dim[l], 64, n.in_dim[l] / kNSplit));
+      INRCT_TRY(make_map(&maps->m[mi++], w.WbT[l], n.out_dim[l], n.in_dim[l], kKChunk, n.in_dim[l] / kNSplit,
+                         2 * kKChunk));
     }
   }
   P->n_stages = s;
@@ -1041,7 +1129,7 @@ bool tc_supported(const Net& n, char* why, size_t len) {
     snprintf(why, len, "n_feat=%d too large (<= 1024)", n.F);
     return false;
   }
-  if (tile_smem(n) + 4096 > 232448) {
+  if (std::max(tile_smem(n, 0), tile_smem(n, 1)) > 232448) {  // all of it is dynamic
     snprintf(why, len, "network too large for the tile kernel's shared memory (%zu bytes)", tile_smem(n));
     return false;
   }
@@ -1114,7 +1202,7 @@ GemmPlan plan_gemm(const Net& n, int64_t K, int64_t* part_floats) {
   memset(&G, 0, sizeof(G));
   G.K = K;
   const int64_t nch = (K + 63) / 64;
-  int S = (int)std::min<int64_t>(nch, 16);
+  int S = (int)std::min<int64_t>(nch, kMaxSplits);
   const int64_t per_ch = (nch + S - 1) / S;
   S = (int)((nch + per_ch - 1) / per_ch);
   G.S = S;
@@ -1208,7 +1296,7 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* ou
   plan_gemm(n, chunk, &pf);
   w.part_floats = (size_t)pf;
   w.part = c.take<float>((size_t)pf);
-  w.bias_part = c.take<double>(kBiasBlocks);
+  w.bias_part = c.take<double>(4 * 1024);  // 4 per tile-kernel CTA
   if (out) *out = w;
   if (ok) *ok = c.ok;
   return c.off + 256;
@@ -1258,6 +1346,7 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
   INRCT_TRY(make_map(&tmaps.m[P.map_dlt], w.Dlt, n.W, (uint64_t)n.L * w.pad, 64, kTile));
   P.Y16c = w.Y16c;
   P.Y16o = w.Y16o;
+  P.bias_part = w.bias_part;
   P.npts_pad = w.pad;
   INRCT_TRY(set_smem_attr((const void*)tn_gemm_kernel, kGemmSmem));
   for (int64_t c0 = 0; c0 < n_idx; c0 += chunk) {
@@ -1268,7 +1357,9 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     cudaMemsetAsync(w.Y16o, 0, sizeof(__nv_bfloat16) * 16 * w.pad, st);
     const int64_t tiles = (np + kTile - 1) / kTile;
     if (c0 == 0) prof_mark(kMarkVjpKernel, st);
-    INRCT_TRY(launch_tile(1, n, tmaps, P, (int)std::min<int64_t>((tiles + 1) / 2, num_sms()), w.err, st));
+    const int tile_grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 1) / 2, num_sms()));
+    INRCT_REQUIRE(tile_grid <= 1024, "tile grid %d exceeds the bias partial buffer", tile_grid);
+    INRCT_TRY(launch_tile(1, n, tmaps, P, tile_grid, w.err, st));
     if (c0 == 0) prof_mark(kMarkVjpKernelDone, st);
     // split-K weight-gradient GEMMs over this chunk's points
     int64_t pf;
@@ -1290,13 +1381,11 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     int maxe = 0;
     for (int q = 0; q < G.n_jobs; ++q)
       maxe = std::max(maxe, G.job[q].M * (G.job[q].w_cols + 1));
-    gemm_reduce_kernel<<<dim3(ceil_div(maxe, 256), G.n_jobs), 256, 0, st>>>(G, w.part, c0 > 0, grad_f64);
+    G.bpart = w.bias_part;
+    G.n_bpart = 4 * tile_grid;
+    G.off_bout = n.offb[n.L];
+    gemm_reduce_kernel<<<dim3(ceil_div(maxe, 256), G.n_jobs + 1), 256, 0, st>>>(G, w.part, c0 > 0, grad_f64);
     INRCT_CHECK_LAUNCH("gemm reduce");
-    out_bias_partial_kernel<<<kBiasBlocks, 256, 0, st>>>(idx + c0, np, v, ng, (float)scale, w.bias_part);
-    INRCT_CHECK_LAUNCH("output bias gradient");
-    out_bias_final_kernel<<<1, kBiasBlocks, 0, st>>>(w.bias_part, kBiasBlocks, c0 > 0,
-                                                     grad_f64 + n.offb[n.L]);
-    INRCT_CHECK_LAUNCH("output bias gradient (final)");
   }
   if (grad_f32) INRCT_TRY(f64_to_f32(grad_f64, grad_f32, n.p, st));
   return INRCT_OK;
@@ -1318,7 +1407,7 @@ GemmPlan diag_plan(int64_t K, int M, int N, bool y16, int64_t* pf) {
   memset(&G, 0, sizeof(G));
   G.K = K;
   const int64_t nch = (K + 63) / 64;
-  int S = (int)std::min<int64_t>(nch, 16);
+  int S = (int)std::min<int64_t>(nch, kMaxSplits);
   const int64_t per_ch = (nch + S - 1) / S;
   S = (int)((nch + per_ch - 1) / per_ch);
   G.S = S;

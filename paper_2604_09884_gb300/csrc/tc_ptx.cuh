@@ -131,10 +131,17 @@ __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
-// tcgen05 shared-memory matrix descriptor, 128-byte swizzle.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+// tcgen05 shared-memory matrix descriptor: start address, leading / stride byte offsets,
+// fixed version bit, and the swizzle mode of the tile (32-, 64- or 128-byte rows, the pattern a
+// TMA load with the same CU_TENSOR_MAP_SWIZZLE_* writes; the atom is 8 rows, SBO apart).
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes,
+                                            int swizzle_bytes) {
+  const uint64_t mode = swizzle_bytes == 128 ? 2ull : (swizzle_bytes == 64 ? 4ull : 6ull);
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+         ((uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (mode << 61);
+}
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+  return desc_sw(saddr, lbo_bytes, sbo_bytes, 128);
 }
 
 // Instruction descriptor of tcgen05.mma.kind::f16 with BF16 A/B and FP32 accumulation.
