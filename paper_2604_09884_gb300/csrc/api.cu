@@ -260,11 +260,12 @@ static int step_impl(const inrct_geom* geom, const inrct_grid* grid, const inrct
                           stream, w.wprep));
   ProjTables tabs;
   INRCT_TRY(build_tables(geom, grid, w.tables, w.tables_bytes, &tabs, stream));
-  INRCT_TRY(project_impl(geom, grid, w.x, w.z, y, w.r, w.loss, w.stage, w.stage_bytes, stream, &tabs));
+  double* L = loss_out ? loss_out : w.loss;  // the loss at the incoming theta, written in place
+  INRCT_TRY(project_impl(geom, grid, w.x, w.z, y, w.r, L, w.stage, w.stage_bytes, stream, &tabs));
   prof_mark(kMarkProjDone, stream);
   // Algorithm 1, step 2: v = P^T dL/dz  (LS: z - y; FLS: F (z - y), Sec. 3)
   if (loss == INRCT_LOSS_FLS) {
-    INRCT_TRY(ramp_filter_impl(geom, grid, w.r, w.z, w.loss, w.stage, w.stage_bytes, stream));
+    INRCT_TRY(ramp_filter_impl(geom, grid, w.r, w.z, L, w.stage, w.stage_bytes, stream));
     INRCT_TRY(backproject_impl(geom, grid, w.z, w.v, w.stage, w.stage_bytes, stream, &tabs));
   } else {
     INRCT_TRY(backproject_impl(geom, grid, w.r, w.v, w.stage, w.stage_bytes, stream, &tabs));
@@ -275,13 +276,6 @@ static int step_impl(const inrct_geom* geom, const inrct_grid* grid, const inrct
   INRCT_TRY(vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, w.v, scale, g, nullptr, w.stage,
                          w.stage_bytes, stream, w.wprep));
   prof_mark(kMarkVjpDone, stream);
-  if (loss_out) {
-    cudaError_t e = cudaMemcpyAsync(loss_out, w.loss, sizeof(double), cudaMemcpyDeviceToDevice, stream);
-    if (e != cudaSuccess) {
-      set_error("loss copy: %s", cudaGetErrorString(e));
-      return INRCT_ERR_CUDA;
-    }
-  }
   if (adam && t_dev) {
     INRCT_TRY(adam_update_devt(theta, g, adam_m, adam_s, n.p, adam, t_dev, stream));
   } else if (adam) {

@@ -411,8 +411,11 @@ struct TileProg {
   int st_in_layer[kMaxStages];  // ... layer of that array
   int tail_layer;               // Dlt layer held by the panels after the last stage
   int map_act, map_dlt;         // tensor maps (in the kernel's Maps) for the panel stores
-  __nv_bfloat16* Y16c;  // [16][npts_pad] coordinates (SIREN)
-  __nv_bfloat16* Y16o;  // [16][npts_pad] output-layer weights scale * v
+  // 16-row K-major GEMM operands; only rows 0..2 of Y16c (coordinates, SIREN; row d.. zero for
+  // d = 2) and row 0 of Y16o (scale * v) are written: the other rows only feed output columns
+  // of the weight-gradient GEMM that the reduction never reads (each column depends on its row)
+  __nv_bfloat16* Y16c;  // [16][npts_pad]
+  __nv_bfloat16* Y16o;  // [16][npts_pad]
   double* bias_part;    // [gridDim.x][4] FP64 sums of scale * v_i (output-layer bias gradient)
   int64_t npts_pad;
   int stall;            // diagnostic: the producer issues nothing (tests bounded waits)
@@ -741,7 +744,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               if (c == 0 && g == 0) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
-                  if (k < P.d) P.Y16c[(int64_t)k * P.npts_pad + prow_t] = __float2bfloat16_rn(xt[k]);
+                  P.Y16c[(int64_t)k * P.npts_pad + prow_t] = __float2bfloat16_rn(k < P.d ? xt[k] : 0.f);
               }
             }
           }
@@ -1197,12 +1200,19 @@ struct TcVjpWs {
   size_t part_floats;
 };
 
-GemmPlan plan_gemm(const Net& n, int64_t K, int64_t* part_floats) {
+// Split-K GEMM plan.  The split count fills about one wave of CTAs (one CTA per SM);
+// for_sizing: the largest plan any device could use (workspace sizing).
+GemmPlan plan_gemm(const Net& n, int64_t K, int64_t* part_floats, bool for_sizing = false) {
   GemmPlan G;
   memset(&G, 0, sizeof(G));
   G.K = K;
   const int64_t nch = (K + 63) / 64;
-  int S = (int)std::min<int64_t>(nch, kMaxSplits);
+  int mt = 0;  // m-tiles over all jobs (see the job list below)
+  for (int l = 0; l < n.L; ++l)
+    mt += (l == 0 && n.kind == INRCT_SIREN) ? n.W / 128 : (n.W / 128) * ((n.in_dim[l] + 255) / 256);
+  mt += n.W / 128;
+  const int per_wave = for_sizing ? kMaxSplits : std::max(1, num_sms() / std::max(mt, 1));
+  int S = (int)std::min<int64_t>(nch, std::min(kMaxSplits, per_wave));
   const int64_t per_ch = (nch + S - 1) / S;
   S = (int)((nch + per_ch - 1) / per_ch);
   G.S = S;
@@ -1293,7 +1303,7 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* ou
   w.Y16c = c.take<__nv_bfloat16>((size_t)16 * pad);
   w.Y16o = c.take<__nv_bfloat16>((size_t)16 * pad);
   int64_t pf;
-  plan_gemm(n, chunk, &pf);
+  plan_gemm(n, chunk, &pf, true);
   w.part_floats = (size_t)pf;
   w.part = c.take<float>((size_t)pf);
   w.bias_part = c.take<double>(4 * 1024);  // 4 per tile-kernel CTA
@@ -1353,8 +1363,6 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     const int64_t np = std::min(chunk, n_idx - c0);
     P.idx = idx + c0;
     P.npts = np;
-    cudaMemsetAsync(w.Y16c, 0, sizeof(__nv_bfloat16) * 16 * w.pad, st);
-    cudaMemsetAsync(w.Y16o, 0, sizeof(__nv_bfloat16) * 16 * w.pad, st);
     const int64_t tiles = (np + kTile - 1) / kTile;
     if (c0 == 0) prof_mark(kMarkVjpKernel, st);
     const int tile_grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 1) / 2, num_sms()));
