@@ -29,7 +29,14 @@
  *   Linear(w -> 1).  SIREN: sin(omega0 (W x + b)) layers, same count, then
  *   Linear(w -> 1).
  * - Scratch memory is passed as (ws, ws_bytes); each call documents how to
- *   size it.  Workspace contents need not be initialised.
+ *   size it.  Workspace contents need not be initialised.  project,
+ *   backproject and grad_step keep the geometry's ray tables in their
+ *   workspace between calls: a later call with the same geometry and the same
+ *   ws reuses them when the fingerprints written at both ends of the table
+ *   region after a completed build still match, and rebuilds them otherwise.
+ *   A caller that writes into a workspace between calls must not leave both
+ *   fingerprints intact (clearing any byte of either suffices; reusing the
+ *   memory for other data normally does).
  */
 #ifndef INRCT_H
 #define INRCT_H

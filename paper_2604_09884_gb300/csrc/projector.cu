@@ -65,8 +65,18 @@ __device__ __forceinline__ int64_t ray_U0(const int4& t) {
   return ((int64_t)t.y << 32) | (int64_t)(uint32_t)t.x;
 }
 
-// FP64 cos/sin of every view angle and (fan) every bin's fan angle.
-__global__ void trig_kernel(GeomDev g, double2* __restrict__ vtrig, double2* __restrict__ btrig) {
+// FP64 cos/sin of every view angle and (fan) every bin's fan angle.  The tables of a
+// geometry persist in the workspace between calls: when both seals already carry this
+// geometry's fingerprint (the previous build completed into this very region) the build is
+// skipped; otherwise the seal is invalidated and the tables are rebuilt.
+__global__ void trig_kernel(GeomDev g, double2* __restrict__ vtrig, double2* __restrict__ btrig,
+                            TabSeal* s0, TabSeal* s1, unsigned long long fp) {
+  const bool valid = s0->fp == fp && s1->fp == fp;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s0->skip = valid ? 1u : 0u;
+    s0->done = 0u;
+  }
+  if (valid) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < g.V) {
     const double ang = g.angle0 + g.span * (double)i / (double)g.V;
@@ -82,13 +92,23 @@ __global__ void trig_kernel(GeomDev g, double2* __restrict__ vtrig, double2* __r
   }
 }
 
-__global__ void build_rays2d_kernel(GeomDev g, const double2* __restrict__ vtrig,
-                                    const double2* __restrict__ btrig, int4* __restrict__ tab,
-                                    float2* __restrict__ views) {
-  const int64_t m = (int64_t)g.V * g.A;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < g.V) views[r] = make_float2((float)vtrig[r].x, (float)vtrig[r].y);
-  if (r >= m) return;
+// The last block of a completed table build writes the fingerprint (trailer first).
+__device__ __forceinline__ void seal_tables(TabSeal* s0, TabSeal* s1, unsigned long long fp) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&s0->done, 1u);
+    if (prev == gridDim.x - 1) {
+      s1->fp = fp;
+      __threadfence();
+      s0->fp = fp;
+    }
+  }
+}
+
+__device__ __forceinline__ void build_ray2d(const GeomDev& g, const double2* __restrict__ vtrig,
+                                            const double2* __restrict__ btrig, int4* __restrict__ tab,
+                                            int64_t r) {
   const int k = (int)(r / g.A), b = (int)(r % g.A);
   const double D = 2.0 / g.N;
   const double cb = vtrig[k].x, sb = vtrig[k].y;
@@ -120,13 +140,21 @@ __global__ void build_rays2d_kernel(GeomDev g, const double2* __restrict__ vtrig
   tab[r] = pack_ray(uref, slope, xd ? sc : -sc);
 }
 
-__global__ void build_cols3d_kernel(GeomDev g, const double2* __restrict__ vtrig, int4* __restrict__ t0,
-                                    int4* __restrict__ t1, float* __restrict__ t2,
-                                    float2* __restrict__ views) {
-  const int64_t cnt = (int64_t)g.V * g.A;
+__global__ void build_rays2d_kernel(GeomDev g, const double2* __restrict__ vtrig,
+                                    const double2* __restrict__ btrig, int4* __restrict__ tab,
+                                    float2* __restrict__ views, TabSeal* s0, TabSeal* s1,
+                                    unsigned long long fp) {
+  if (s0->skip) return;  // tables valid (uniform over the grid)
+  const int64_t m = (int64_t)g.V * g.A;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < g.V) views[r] = make_float2((float)vtrig[r].x, (float)vtrig[r].y);
-  if (r >= cnt) return;
+  if (r < m) build_ray2d(g, vtrig, btrig, tab, r);
+  seal_tables(s0, s1, fp);
+}
+
+__device__ __forceinline__ void build_col3d(const GeomDev& g, const double2* __restrict__ vtrig,
+                                            int4* __restrict__ t0, int4* __restrict__ t1,
+                                            float* __restrict__ t2, int64_t r) {
   const int k = (int)(r / g.A), a = (int)(r % g.A);
   const double D = 2.0 / g.N;
   const double cb = vtrig[k].x, sb = vtrig[k].y;
@@ -158,6 +186,18 @@ __global__ void build_cols3d_kernel(GeomDev g, const double2* __restrict__ vtrig
   t1[r] = make_int4((int)(unsigned)(Hh & 0xffffffffll), (int)(Hh >> 32),
                     (int)(unsigned)(Kk & 0xffffffffll), (int)(Kk >> 32));
   t2[r] = (float)L2;
+}
+
+__global__ void build_cols3d_kernel(GeomDev g, const double2* __restrict__ vtrig, int4* __restrict__ t0,
+                                    int4* __restrict__ t1, float* __restrict__ t2,
+                                    float2* __restrict__ views, TabSeal* s0, TabSeal* s1,
+                                    unsigned long long fp) {
+  if (s0->skip) return;
+  const int64_t cnt = (int64_t)g.V * g.A;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < g.V) views[r] = make_float2((float)vtrig[r].x, (float)vtrig[r].y);
+  if (r < cnt) build_col3d(g, vtrig, t0, t1, t2, r);
+  seal_tables(s0, s1, fp);
 }
 
 // ---------------------------------------------------------------------------
@@ -663,12 +703,32 @@ int64_t num_rays(const inrct_geom* geom) {
 static void tables_layout(const inrct_geom* geom, Carver& c, ProjTables* t) {
   const bool cone = geom->kind == INRCT_CONE3D;
   const int64_t entries = cone ? (int64_t)geom->n_views * geom->n_bins_u : num_rays(geom);
+  t->seal0 = c.take<TabSeal>(1);
   t->tab0 = c.take<int4>(entries);
   t->tab1 = cone ? c.take<int4>(entries) : nullptr;
   t->tab2 = cone ? c.take<float>(entries) : nullptr;
   t->views = c.take<float2>(geom->n_views);
   t->vtrig = c.take<double2>(geom->n_views);
   t->btrig = geom->kind == INRCT_FAN2D ? c.take<double2>(geom->n_bins_u) : nullptr;
+  t->seal1 = c.take<TabSeal>(1);
+}
+
+// Fingerprint of a geometry's tables at a given place: FNV-1a over the geometry, the grid,
+// a layout version and the tables' addresses.
+static unsigned long long tables_fp(const GeomDev& g, const ProjTables& t) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  const int version = 1;
+  mix(&version, sizeof(version));
+  mix(&g.kind, sizeof(int) * 5);
+  const double dd[6] = {g.du, g.dv, g.sod, g.sdd, g.angle0, g.span};
+  mix(dd, sizeof(dd));
+  const void* ptrs[8] = {t.seal0, t.tab0, t.tab1, t.tab2, t.views, t.vtrig, t.btrig, t.seal1};
+  mix(ptrs, sizeof(ptrs));
+  return h == 0 ? 1 : h;  // 0 never marks valid tables
 }
 
 size_t tables_bytes(const inrct_geom* geom) {
@@ -688,14 +748,16 @@ int build_tables(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_
     return INRCT_ERR_WORKSPACE;
   }
   const GeomDev g = to_dev(geom, grid);
-  trig_kernel<<<ceil_div(std::max(g.V, g.A), 256), 256, 0, st>>>(g, t->vtrig, t->btrig);
+  const unsigned long long fp = tables_fp(g, *t);
+  trig_kernel<<<ceil_div(std::max(g.V, g.A), 256), 256, 0, st>>>(g, t->vtrig, t->btrig, t->seal0, t->seal1, fp);
   INRCT_CHECK_LAUNCH("trig table");
   const int64_t cnt = (int64_t)g.V * g.A;
   if (g.kind == INRCT_CONE3D) {
     build_cols3d_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(g, t->vtrig, t->tab0, t->tab1, t->tab2,
-                                                           t->views);
+                                                           t->views, t->seal0, t->seal1, fp);
   } else {
-    build_rays2d_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(g, t->vtrig, t->btrig, t->tab0, t->views);
+    build_rays2d_kernel<<<ceil_div(cnt, 256), 256, 0, st>>>(g, t->vtrig, t->btrig, t->tab0, t->views,
+                                                           t->seal0, t->seal1, fp);
   }
   INRCT_CHECK_LAUNCH("ray table");
   return INRCT_OK;

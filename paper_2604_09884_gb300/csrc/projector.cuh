@@ -10,8 +10,17 @@ struct GeomDev {
   double du, dv, sod, sdd, angle0, span;
 };
 
+// Cache seal of a geometry's ray tables in a workspace (see trig_kernel in projector.cu).
+struct TabSeal {
+  unsigned long long fp;  // fingerprint of the geometry and placement of the completed tables
+  unsigned int skip;      // set by the first build kernel: the tables are valid, skip the build
+  unsigned int done;      // blocks of the ray build that finished (the last one seals)
+};
+
 // Ray tables of one geometry (see projector.cu).
 struct ProjTables {
+  TabSeal* seal0;
+  TabSeal* seal1;
   int4* tab0;
   int4* tab1;
   float* tab2;

@@ -95,3 +95,36 @@ def test_ramp_filter_matches_oracle(g):
     assert rel(out.cpu().numpy(), want) <= TOL
     L0 = 0.5 * float(r.astype(np.float64) @ want)
     assert abs(loss.item() - L0) <= 1e-4 * abs(L0)
+
+
+def _project_with(L, g, x, ws):
+    import ctypes
+    gd, grd = inrct.geom_desc(g), inrct.grid_desc(g.d, g.N)
+    z = torch.empty(g.m, dtype=torch.float32, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.project(ctypes.byref(gd), ctypes.byref(grd), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                   None, None, None, ctypes.c_void_p(ws.data_ptr()), ws.numel(), s)
+    assert rc == 0, L.inrct_last_error().decode()
+    return z
+
+
+def test_ray_tables_persist_in_a_workspace_only_while_valid():
+    """The ray tables stay in the workspace between calls and are reused only when the seals
+    at both ends of their region carry this geometry's fingerprint: reusing one workspace
+    for geometry A, then B, then A, and clobbering it between calls, gives exactly the
+    projections of fresh workspaces."""
+    L = inrct.lib()
+    ga = synth.GeomSpec("fan2d", 96, 30, 137, sod=300.0, sdd=450.0, span=2 * math.pi)
+    gb = synth.GeomSpec("fan2d", 96, 31, 137, sod=300.0, sdd=450.0, span=2 * math.pi)
+    import ctypes
+    nb = max(L.inrct_project_ws_bytes(ctypes.byref(inrct.geom_desc(g)), ctypes.byref(inrct.grid_desc(2, 96)))
+             for g in (ga, gb))
+    x = cuda(synth.phantom(2, 96, 5, seed=3).reshape(-1))
+    ref = {id(g): _project_with(L, g, x, torch.zeros(nb, dtype=torch.uint8, device="cuda")) for g in (ga, gb)}
+    ws = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    for g in (ga, ga, gb, ga, gb, gb):
+        assert torch.equal(_project_with(L, g, x, ws), ref[id(g)])
+    ws.fill_(7)  # clobbered workspace: the seals no longer match, the tables are rebuilt
+    assert torch.equal(_project_with(L, ga, x, ws), ref[id(ga)])
+    ws[: nb // 2].fill_(0)  # only the first half (the leading seal) overwritten
+    assert torch.equal(_project_with(L, ga, x, ws), ref[id(ga)])
