@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-fp32", action="store_true", help="skip the FP32 path and the BF16/FP32 gradient check")
     p.add_argument("--fp32-steps", type=int, default=10)
     p.add_argument("--no-fractions", action="store_true", help="skip the |I|/n = 1.0 and 0.05 step rates")
+    p.add_argument("--subsets", type=int, default=1,
+                   help="ordered subsets: step t uses interleaved view subset t mod S (Sec. 3)")
     return p.parse_args()
 
 
@@ -442,9 +444,16 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    S = max(1, args.subsets)
+    sub_g = [inrct.view_subset(g, S, k) for k in range(S)] if S > 1 else [g]
+    sub_y = [inrct.view_subset_rows(g, y, S, k) for k in range(S)] if S > 1 else [y]
+    sub_ws = [ws] if S == 1 else [torch.empty(inrct.step_ws_bytes(q, mlp, n_idx), dtype=torch.uint8, device=dev)
+                                  for q in sub_g]
+
     def step(t, idx):
-        inrct.grad_step(g, mlp, theta, y, idx, scale, inrct.adam(lr=w.lr, t=t), m, s, loss, None,
-                        ws, loss_kind)
+        k = t % S
+        inrct.grad_step(sub_g[k], mlp, theta, sub_y[k], idx, scale, inrct.adam(lr=w.lr, t=t), m, s, loss,
+                        None, sub_ws[k], loss_kind)
 
     t = 0
     for _ in range(args.warmup):
@@ -590,14 +599,15 @@ def main():
         key = "vjp_dw_gemm_reduce" if n_idx <= VJP_CHUNK else "vjp_rest (further chunks + dW GEMMs)"
         kernels[key] = {"ms": per["vjp_dw_gemm_reduce"], "TFLOP/s": f_dw / per["vjp_dw_gemm_reduce"] / 1e9}
     # projector: compulsory bytes = image once + sinogram out (+ y in, residual out)
-    proj_bytes = 4.0 * (g.n + 3 * g.m)
-    back_bytes = 4.0 * (g.n + g.m)
+    m_step = g.m // S                                # rays per step (a view subset when S > 1)
+    proj_bytes = 4.0 * (g.n + 3 * m_step)
+    back_bytes = 4.0 * (g.n + m_step)
     kernels["project_loss"] = {"ms": per["project_loss"],
                                "GB/s": proj_bytes / per["project_loss"] / 1e6,
-                               "GRays/s": g.m / per["project_loss"] / 1e6}
+                               "GRays/s": m_step / per["project_loss"] / 1e6}
     kernels["backproject"] = {"ms": per["backproject"],
                               "GB/s": back_bytes / per["backproject"] / 1e6,
-                              "GRays/s": g.m / per["backproject"] / 1e6}
+                              "GRays/s": m_step / per["backproject"] / 1e6}
     pair_ms = per["project_loss"] + per["backproject"]
     dominant = max(("eval_mlp_kernel", "vjp_mlp_kernel"), key=lambda k: per[k])
     flops = f_eval if dominant == "eval_mlp_kernel" else f_vjp
@@ -625,10 +635,10 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
                 "config": {"workload": w.name, "note": w.note, "batch": n_idx,
-                           "loss": args.loss, "precision": args.prec,
+                           "loss": args.loss, "precision": args.prec, "view_subsets": S,
                            "l2": "flushed between timed steps (untimed 258 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "gray_s_proj_backproj": g.m / pair_ms / 1e6 if pair_ms > 0 else None,
+                "gray_s_proj_backproj": m_step / pair_ms / 1e6 if pair_ms > 0 else None,
                 "stage_ms": per, "kernels": kernels, "roofline": roofline,
                 "e2e": {"value": e2e_value, "unit": "steps/s",
                         "h2d_bytes_per_step": int(idx_host[0].numel() * 4), "d2h_bytes_per_step": 8},

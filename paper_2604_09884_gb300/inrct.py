@@ -152,6 +152,23 @@ def grid_desc(d: int, N: int) -> Grid:
     return Grid(d, N)
 
 
+def view_subset(g: synth.GeomSpec, n_subsets: int, s: int) -> synth.GeomSpec:
+    """Subset s of n_subsets interleaved view subsets (views s, s + S, s + 2S, ...), for the
+    ordered-subsets use of Algorithm 1 (Sec. 3): the same scan with V/S views starting at
+    angle0 + span s / V and the same span.  V must be divisible by n_subsets."""
+    if n_subsets < 1 or g.V % n_subsets or not 0 <= s < n_subsets:
+        raise InrctError(1, f"{g.V} views cannot form subset {s} of {n_subsets}")
+    kw = g.as_dict()
+    kw.update(V=g.V // n_subsets, angle0=g.angle0 + g.span * s / g.V)
+    return synth.GeomSpec(**kw)
+
+
+def view_subset_rows(g: synth.GeomSpec, sino: torch.Tensor, n_subsets: int, s: int) -> torch.Tensor:
+    """The rows of a sinogram of g ([view][...]) that belong to view_subset(g, n_subsets, s)."""
+    per_view = g.m // g.V
+    return sino.view(g.V, per_view)[s::n_subsets].contiguous().view(-1)
+
+
 @dataclass
 class MlpHandle:
     """An inrct_mlp descriptor plus the device Fourier matrix it points to."""

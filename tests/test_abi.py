@@ -127,3 +127,12 @@ def test_batch_create_requires_its_workspace(L):
     rc = L.inrct_batch_create(ctypes.byref(h.desc), 0, arr, 1, ctypes.byref(inrct.adam()),
                               ctypes.c_void_p(256), ctypes.c_void_p(256), need - 1, ctypes.byref(out))
     assert rc == 3 and not out.value
+
+
+def test_view_subset_rejects_uneven_splits_and_keeps_the_scan():
+    g = synth.GeomSpec("fan2d", 32, 12, 45, sod=128.0, sdd=192.0, span=6.283185307179586, angle0=0.3)
+    with pytest.raises(inrct.InrctError):
+        inrct.view_subset(g, 5, 0)
+    s = inrct.view_subset(g, 4, 3)
+    assert (s.V, s.A, s.sod, s.span) == (3, 45, 128.0, g.span)
+    assert abs(s.angle0 - (0.3 + g.span * 3 / 12)) < 1e-15

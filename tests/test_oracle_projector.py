@@ -289,3 +289,30 @@ def test_ramp_filter_matrix_and_spectrum():
     L, Fd = O.fls_loss(g, r + 1.0, np.ones(g.m))
     want = 0.5 * sum(rr @ F @ rr for rr in r.reshape(2, A))
     assert abs(L - want) < 1e-9 * abs(want)
+
+
+@pytest.mark.parametrize("kind", ["par2d", "fan2d", "cone3d"])
+def test_view_subsets_partition_the_rays(kind):
+    """Ordered subsets of views (Sec. 3): interleaved subset s of S, written as a scan of V/S
+    views starting S-times-coarser at angle0 + span s / V, holds exactly the full scan's rays
+    of views s, s + S, ...; hence its residual backprojections sum to the full one."""
+    S, V = 3, 9
+    kw = dict(sod=40.0, sdd=60.0, span=2 * math.pi) if kind != "par2d" else dict(span=math.pi)
+    full = O.Geometry(kind, 12 if kind != "cone3d" else 8, V, 19, 11 if kind == "cone3d" else 1,
+                      angle0=0.2, **kw)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0, 1, full.n)
+    y = rng.uniform(0, 1, full.m)
+    rows = full.m // V
+    total = np.zeros(full.n)
+    for s in range(S):
+        sub = O.Geometry(kind, full.N, V // S, full.A, full.B, angle0=0.2 + full.span * s / V, **kw)
+        for kp in range(V // S):
+            for b in range(0, full.A, 6):
+                p_sub, e_sub = O.ray(sub, kp, 0, b)
+                p_full, e_full = O.ray(full, s + S * kp, 0, b)
+                assert np.allclose(p_sub, p_full, atol=1e-12) and np.allclose(e_sub, e_full, atol=1e-12)
+        ys = y.reshape(V, rows)[s::S].reshape(-1)
+        total += O.backproject(sub, O.project(sub, x) - ys)
+    ref = O.backproject(full, O.project(full, x) - y)
+    assert np.allclose(total, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
