@@ -559,12 +559,28 @@ __global__ void bp_sum_kernel(const float* __restrict__ part, int nsplit, int64_
   img[i] = acc;
 }
 
+// Cone adjoint, gather form with the per-ray factor sqrt(v_b^2 + |e_xy|^2) |s_a| (the ray's
+// step length per slice) applied once per ray by a pre-pass, and the z crossing of
+// consecutive rows stepped exactly in integers.
+__global__ void cone_prescale_kernel(GeomDev g, const int4* __restrict__ t0, const float* __restrict__ t2,
+                                     float pv_half, const float* __restrict__ sino, float* __restrict__ out) {
+  const int64_t m = (int64_t)g.V * g.B * g.A;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int a = (int)(i % g.A);
+  const int64_t kb = i / g.A;
+  const int b = (int)(kb % g.B), k = (int)(kb / g.B);
+  const size_t ci = (size_t)k * g.A + a;
+  const float sa = fabsf(__int_as_float(__ldg(t0 + ci).w));
+  const float vb = __fmul_rn((float)(2 * b - (g.B - 1)), pv_half);
+  out[i] = sino[i] * cone_scale(vb, __ldg(t2 + ci), sa);
+}
+
 template <int ZC>
 __global__ void __launch_bounds__(128)
     backproject3d_kernel(GeomDev g, const int4* __restrict__ t0, const int4* __restrict__ t1,
-                         const float* __restrict__ t2, const float2* __restrict__ views,
-                         float pv_half, int64_t CzF, const float* __restrict__ sino,
-                         float* __restrict__ vol) {
+                            const float2* __restrict__ views, int64_t CzF,
+                            const float* __restrict__ sino_s, float* __restrict__ vol) {
   extern __shared__ float2 sv[];
   for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < g.V; k += blockDim.x * blockDim.y)
     sv[k] = views[k];
@@ -580,8 +596,8 @@ __global__ void __launch_bounds__(128)
   const float cA = 0.5f * (float)(A - 1), Bm1 = (float)(B - 1);
   const float Cz = 0.5f * (float)N - 0.5f;
   const float R = (float)(g.sod * (2.0 / N));
-  const float kcol = (float)(g.sod / g.du);                   // columns per unit of (u / depth)
-  const float kha = (float)(1.3 * (2.0 / N) * g.sod / g.du);  // half window numerator
+  const float kcol = (float)(g.sod / g.du);
+  const float kha = (float)(1.3 * (2.0 / N) * g.sod / g.du);
   float acc[ZC];
 #pragma unroll
   for (int q = 0; q < ZC; ++q) acc[q] = 0.f;
@@ -599,18 +615,16 @@ __global__ void __launch_bounds__(128)
       const float sa = __int_as_float(P.w);
       const bool xd = sa > 0.f;
       const int j = xd ? ix : iy, q = xd ? iy : ix;
-      const float wq = tap_weight(ray_U0(P) + (int64_t)(j - jref) * slope_fx(P), q);
+      const int64_t dj = j - jref;
+      const float wq = tap_weight(ray_U0(P) + dj * slope_fx(P), q);
       if (wq == 0.f) continue;
       const int4 T1 = __ldg(t1 + ci);
-      const float L2 = __ldg(t2 + ci);
-      // (pv/2) G(j) in float, only to place the row window
       const int64_t Hh = ((int64_t)T1.y << 32) | (int64_t)(uint32_t)T1.x;
       const int64_t Kk = ((int64_t)T1.w << 32) | (int64_t)(uint32_t)T1.z;
-      const float hg = (float)(((double)Hh * 65536.0 + (double)(j - jref) * (double)Kk) *
-                               (1.0 / 281474976710656.0));
+      const float hg = (float)(((double)Hh * 65536.0 + (double)dj * (double)Kk) * (1.0 / 281474976710656.0));
       const float inv_hg = 1.f / hg;
       const float hb = 0.5f * fabsf(inv_hg) * 1.001f + 0.02f;
-      const float* scol = sino + (size_t)k * B * A + a;
+      const float* scol = sino_s + (size_t)k * B * A + a;
 #pragma unroll
       for (int zq = 0; zq < ZC; ++zq) {
         const int iz = z0 + zq;
@@ -618,12 +632,11 @@ __global__ void __launch_bounds__(128)
         const float bz = 0.5f * fmaf((float)iz - Cz, inv_hg, Bm1);
         const int bb0 = max(0, (int)ceilf(bz - hb));
         const int bb1 = min(B - 1, (int)floorf(bz + hb));
-        for (int b = bb0; b <= bb1; ++b) {
-          const ConeRay cr = cone_ray(T1, 2 * b - (B - 1), CzF, pv_half);
-          const float wz = tap_weight(cr.Z0 + (int64_t)(j - jref) * cr.Sz, iz);
-          if (wz != 0.f)
-            acc[zq] = fmaf(wq * wz * cone_scale(cr.vb, L2, fabsf(sa)), __ldg(scol + (size_t)b * A),
-                           acc[zq]);
+        int mr = 2 * bb0 - (B - 1);
+        int64_t Zb = CzF + (int64_t)mr * Hh, Pk = (int64_t)mr * Kk;
+        for (int b = bb0; b <= bb1; ++b, Zb += 2 * Hh, Pk += 2 * Kk) {
+          const float wz = tap_weight(Zb + dj * (Pk >> 16), iz);
+          if (wz != 0.f) acc[zq] = fmaf(wq * wz, __ldg(scol + (size_t)b * A), acc[zq]);
         }
       }
     }
@@ -634,6 +647,7 @@ __global__ void __launch_bounds__(128)
     if (iz < N) vol[((size_t)iz * N + iy) * N + ix] = acc[zq];
   }
 }
+
 
 // ---------------------------------------------------------------------------
 // host side
@@ -770,6 +784,7 @@ struct ProjWs {
   double* loss_part;
   float* bp_part;  // 2-D adjoint: partial images of the view splits (NULL: one split)
   int bp_splits;
+  float* sino_s;   // cone adjoint: the sinogram times each ray's step length
 };
 
 // Number of view splits of the 2-D adjoint (see backproject2d_tile_kernel).
@@ -793,6 +808,7 @@ static size_t proj_layout(const inrct_geom* geom, const inrct_grid* grid, void* 
   w.loss_part = forward ? c.take<double>(blocks) : nullptr;
   w.bp_splits = forward ? 1 : bp_splits(geom, grid);
   w.bp_part = w.bp_splits > 1 ? c.take<float>((size_t)w.bp_splits * grid_points(grid)) : nullptr;
+  w.sino_s = (!forward && cone) ? c.take<float>((size_t)num_rays(geom)) : nullptr;
   if (out) *out = w;
   if (ok) *ok = c.ok;
   return c.off + 256;
@@ -886,16 +902,18 @@ int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float
   } else {
     INRCT_TRY(build_tables(geom, grid, ws, ws_bytes, &w.t, st));  // same offsets as the layout
   }
-  const size_t shm = sizeof(float2) * g.V;
   if (g.kind == INRCT_CONE3D) {
     float pvh;
     int64_t CzF;
     cone_consts(g, &pvh, &CzF);
-    constexpr int ZC = 8;
+    const int64_t m = num_rays(geom);
+    cone_prescale_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(g, w.t.tab0, w.t.tab2, pvh, sino, w.sino_s);
+    INRCT_CHECK_LAUNCH("backproject3d (ray scale)");
+    constexpr int ZC = 8;  // voxels per thread along z (measured: 8 slightly ahead of 4)
     dim3 blk(32, 4);
     dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, ZC));
-    backproject3d_kernel<ZC><<<grd, blk, shm, st>>>(g, w.t.tab0, w.t.tab1, w.t.tab2, w.t.views, pvh, CzF,
-                                                    sino, image);
+    backproject3d_kernel<ZC><<<grd, blk, sizeof(float2) * g.V, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
+                                                                       w.sino_s, image);
     INRCT_CHECK_LAUNCH("backproject3d");
   } else {
     static bool attr_set = false;  // per process; the attribute is per function, all devices alike
