@@ -499,6 +499,11 @@ int inrct_profile_end(double* stage_ms, int n_stages, int* steps_out) {
 
 size_t inrct_gemm_tn_ws_bytes(int64_t K, int M, int N) { return gemm_tn_ws_bytes(K, M, N); }
 
+int inrct_sincospi(const float* x, float* s, float* c, int64_t n, cudaStream_t stream) {
+  clear_error();
+  return sincospi_diag(x, s, c, n, stream);
+}
+
 int inrct_gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int N, float* C,
                   void* ws, size_t ws_bytes, cudaStream_t stream) {
   clear_error();

@@ -58,6 +58,8 @@ int tc_vjp(const Net& net, const float* theta, int N, const int32_t* idx, int64_
 
 // split-K TN GEMM of the weight gradients, exposed for diagnostics
 size_t gemm_tn_ws_bytes(int64_t K, int M, int N);
+// sin(pi x), cos(pi x) by the tile kernel's feature polynomial, for diagnostics.
+int sincospi_diag(const float* x, float* s, float* c, int64_t n, cudaStream_t st);
 int gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int N, float* C, void* ws,
             size_t ws_bytes, cudaStream_t st);
 

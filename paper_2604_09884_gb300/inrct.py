@@ -103,6 +103,7 @@ def lib():
         "inrct_gemm_tn": ([_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, _P, _P, _SZ, _P], ctypes.c_int),
         "grad_step": ([g, gr, m, ctypes.c_int, _P, _P, _P, _I64, ctypes.c_double,
                        ctypes.POINTER(Adam), _P, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+        "inrct_sincospi": ([_P, _P, _P, _I64, _P], ctypes.c_int),
         "inrct_batch_ws_bytes": ([m, ctypes.POINTER(Problem), ctypes.c_int], _SZ),
         "inrct_batch_create": ([m, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                 ctypes.POINTER(Adam), _P, _P, _SZ, ctypes.POINTER(_P)], ctypes.c_int),
@@ -355,6 +356,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def sincospi(x: torch.Tensor, stream=None):
+    """Diagnostic: (sin(pi x), cos(pi x)) as the FFN feature code computes them (x in [-1, 1])."""
+    sn = torch.empty_like(x)
+    cs = torch.empty_like(x)
+    _check(lib().inrct_sincospi(_ptr(x, torch.float32), _ptr(sn), _ptr(cs), x.numel(), _stream(stream)))
+    return sn, cs
 
 
 def gemm_tn(X: torch.Tensor, Y: torch.Tensor | None, Y16: torch.Tensor | None, stream=None):
