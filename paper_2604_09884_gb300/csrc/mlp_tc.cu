@@ -62,6 +62,19 @@ constexpr int kMaxStages = 2 * kMaxLayers;
 constexpr int kMaxJobs = 24;
 constexpr int kMaxSplits = 16;   // split-K factor of the weight-gradient GEMM
 
+// FFN input columns are interleaved per 64-column panel: panel c holds cos(2 pi B_f x) for
+// f = 32c .. 32c+31 in its first 32 columns and sin(2 pi B_f x) of the same features in the
+// last 32, so that one sincospif gives both entries of a feature.  ffn_orig_col maps a
+// panel column back to the input column of gamma(x) = [cos 2 pi B x; sin 2 pi B x].
+__host__ __device__ inline int ffn_orig_col(int kp, int F) {
+  const int c = kp >> 6, j = kp & 63;
+  return j < 32 ? 32 * c + j : F + 32 * c + (j - 32);
+}
+__host__ __device__ inline int ffn_panel_col(int k, int F) {
+  return k < F ? 64 * (k >> 5) + (k & 31) : 64 * ((k - F) >> 5) + 32 + ((k - F) & 31);
+}
+
+
 // ---------------------------------------------------------------------------
 // host: tensor maps
 // ---------------------------------------------------------------------------
@@ -118,6 +131,7 @@ struct PrepTable {
   __nv_bfloat16* Wb[kMaxLayers];
   __nv_bfloat16* WbT[kMaxLayers];
   float* bias[kMaxLayers];
+  int permF;  // FFN: F, and entry 0 (layer 0) is stored with interleaved input columns; else 0
   // the row blockIdx.y == n fills the small tables the tile kernel reads through L1:
   // first-layer table (SIREN {w'_0, w'_1, w'_2, b'} per output; FFN {B_0, B_1, B_2, 0} per
   // feature) and an aligned copy of the output-layer weights
@@ -153,8 +167,9 @@ __global__ void prep_all_kernel(const float* __restrict__ theta, const __grid_co
        t += (int64_t)gridDim.x * blockDim.x) {
     const int o = (int)(t / in), k = (int)(t % in);
     const __nv_bfloat16 w = __float2bfloat16_rn(scale * theta[T.offW[l] + t]);
-    T.Wb[l][t] = w;
-    if (T.WbT[l]) T.WbT[l][(int64_t)k * out + o] = w;
+    const int kw = (l == 0 && T.permF > 0) ? ffn_panel_col(k, T.permF) : k;
+    T.Wb[l][(int64_t)o * in + kw] = w;
+    if (T.WbT[l]) T.WbT[l][(int64_t)kw * out + o] = w;
     if (t < out) T.bias[l][t] = scale * theta[T.offb[l] + t];
   }
 }
@@ -178,6 +193,7 @@ struct GemmJob {
   int w_cols;
   int64_t offb;  // gradient offset of the bias (or -1)
   double mult;   // omega0 for SIREN sine layers, else 1
+  int permF;     // FFN layer 0: main columns are interleaved panel columns of F features
 };
 
 struct GemmPlan {
@@ -354,7 +370,8 @@ __global__ void gemm_reduce_kernel(const __grid_constant__ GemmPlan plan, const 
   int64_t dst;
   if (c < J.w_cols) {
     col = J.w_src == 0 ? c : J.N + 16 + c;
-    dst = J.offW + (int64_t)m * J.ldW + J.n0 + c;
+    const int kc = J.permF > 0 ? ffn_orig_col(J.n0 + c, J.permF) : J.n0 + c;
+    dst = J.offW + (int64_t)m * J.ldW + kc;
   } else {
     col = J.N;  // first column of the ones block
     dst = J.offb + m;
@@ -451,11 +468,8 @@ __device__ __forceinline__ void load_row_bf16(const __nv_bfloat16* src, float* v
 // hardware approximations (those, 2^-21.4 absolute, moved the BF16 gradient of a 3-D FFN by
 // more than 1 % through flipped masks; measured).
 __device__ __forceinline__ void feat_sincos(float t, float* s, float* c) { sincospif(2.f * t, s, c); }
-__device__ __forceinline__ float four_feat(float ph, bool want_sin) {
-  const float t = __fsub_rn(ph, rintf(ph));
-  float s, c;
-  feat_sincos(t, &s, &c);
-  return want_sin ? s : c;
+__device__ __forceinline__ void four_feat2(float ph, float* s, float* c) {
+  feat_sincos(__fsub_rn(ph, rintf(ph)), s, c);
 }
 
 
@@ -720,16 +734,20 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
         for (int c = 0; c < P.in_panels; ++c) {
           const int col0 = 64 * c + CW * g;
           if (KIND == INRCT_FFN_RELU) {
-            const bool is_sin = col0 >= P.F;
-            const int f0 = is_sin ? col0 - P.F : col0;
+            // features f0 .. f0+7 of this thread: cos into panel columns 8g.., sin into 32+8g..
+            static_assert(NWG == 4, "the interleaved feature panels assume 4 column groups");
+            const int f0 = 32 * c + 8 * g;
 #pragma unroll
-            for (int i = 0; i < CW; ++i) {
+            for (int i = 0; i < 8; ++i) {
               const float4 bf = (kStage && P.first_staged) ? first_s[f0 + i] : __ldg(P.first + f0 + i);
               float ph = __fadd_rn(__fmul_rn(bf.x, xt[0]), __fmul_rn(bf.y, xt[1]));
               if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, xt[2]));
-              v[i] = four_feat(ph, is_sin);
+              four_feat2(ph, &v[8 + i], &v[i]);  // v[0..7] cos, v[8..15] sin
             }
-            if (MODE == 1 && store_t) store_row_bf16<CW>(P.E + prow_t * (2 * P.F) + col0, v);
+            if (MODE == 1 && store_t) {
+              store_row_bf16<8>(P.E + prow_t * (2 * P.F) + 64 * c + 8 * g, v);
+              store_row_bf16<8>(P.E + prow_t * (2 * P.F) + 64 * c + 32 + 8 * g, v + 8);
+            }
           } else {
             float cs[CW];
 #pragma unroll
@@ -756,7 +774,12 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
             if (!warp_wait(&a_empty[4 * t + as], (ae >> bit) & 1u, abort_flag, err, 401)) goto epi_done;
             ae ^= 1u << bit;
           }
-          st_panel_row<CW>(apan + (4 * t + as) * kPanelBytes, r, (CW / 8) * g, v);
+          if (KIND == INRCT_FFN_RELU) {
+            st_panel_row<8>(apan + (4 * t + as) * kPanelBytes, r, g, v);
+            st_panel_row<8>(apan + (4 * t + as) * kPanelBytes, r, 4 + g, v + 8);
+          } else {
+            st_panel_row<CW>(apan + (4 * t + as) * kPanelBytes, r, (CW / 8) * g, v);
+          }
           if (c == n0 - 1) {
             // panels 0 .. n0-1 written and (program order) this slot's accumulator drained
             fence_async_smem();
@@ -1025,6 +1048,7 @@ int prep_weights(const Net& n, const float* theta, const TcWeights& w, cudaStrea
     T.bias[i] = w.bias + (int64_t)l * n.W;
     most = std::max<int64_t>(most, (int64_t)n.in_dim[l] * n.out_dim[l]);
   }
+  T.permF = n.kind == INRCT_FFN_RELU ? n.F : 0;
   T.kind = n.kind;
   T.d = n.d;
   T.W = n.W;
@@ -1262,6 +1286,7 @@ GemmPlan plan_gemm(const Net& n, int64_t K, int64_t* part_floats, bool for_sizin
       J.w_cols = J.N;
       J.offb = n0 == 0 ? n.offb[l] : -1;
       J.mult = mult;
+      J.permF = (l == 0 && n.kind == INRCT_FFN_RELU) ? n.F : 0;
       add(J);
     }
   }
