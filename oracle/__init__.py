@@ -232,7 +232,11 @@ class Arch:
                   Linear(width, 1).
     kind 'siren': n_hidden layers h = sin(omega0 (W h + b)) (the first takes
                   x itself), then Linear(width, 1).
-    theta layout: for every layer in order, W row-major [out][in], then b [out].
+    kind 'hash':  multiresolution hash encoding (``hash_encode``: hash_levels levels of
+                  hash_feats features, tables of 2^hash_log2_T entries), then n_hidden
+                  layers Linear + ReLU and Linear(width, 1).
+    theta layout: the hash tables first (hash only, [level][entry][feature]), then for
+    every layer in order, W row-major [out][in], then b [out].
     """
     kind: str
     d: int
@@ -241,10 +245,21 @@ class Arch:
     n_feat: int = 0
     B: np.ndarray | None = None   # F x d, FFN only
     omega0: float = 30.0
+    hash_levels: int = 16
+    hash_feats: int = 2
+    hash_log2_T: int = 19
+    hash_base: int = 16
+    hash_growth: float = 1.5
 
     @property
     def d_in(self) -> int:
+        if self.kind == "hash":
+            return self.hash_levels * self.hash_feats
         return 2 * self.n_feat if self.kind == "ffn" else self.d
+
+    @property
+    def table_params(self) -> int:
+        return self.hash_levels * (1 << self.hash_log2_T) * self.hash_feats if self.kind == "hash" else 0
 
     def layer_shapes(self):
         shapes = [(self.width, self.d_in)]
@@ -254,13 +269,13 @@ class Arch:
 
     @property
     def p(self) -> int:
-        return sum(o * i + o for o, i in self.layer_shapes())
+        return self.table_params + sum(o * i + o for o, i in self.layer_shapes())
 
 
 def unpack(arch: Arch, theta):
-    """Split the flat theta into [(W_l, b_l)] views in layer order."""
+    """Split the flat theta into [(W_l, b_l)] views in layer order (after the hash tables)."""
     theta = np.asarray(theta, dtype=np.float64)
-    out, off = [], 0
+    out, off = [], arch.table_params
     for o, i in arch.layer_shapes():
         W = theta[off:off + o * i].reshape(o, i)
         off += o * i
@@ -271,8 +286,77 @@ def unpack(arch: Arch, theta):
     return out
 
 
-def encode(arch: Arch, X: np.ndarray) -> np.ndarray:
-    """Network input: gamma(x) for FFN (cos block first, then sin), x for SIREN."""
+# ----------------------------------------------------------------------------
+# Multiresolution hash encoding (the "Hash Enc." INR of Sec. 4; the paper gives no details,
+# the readings are the usual ones of multiresolution hash encodings): level l has
+# resolution N_l = floor(base * growth^l); a point's level coordinate is p = (x + 1)/2 * N_l
+# per axis; its 2^d surrounding vertices (integer coordinates in [0, N_l]) are looked up
+# densely (index sum_k c_k (N_l+1)^k) when (N_l+1)^d <= T, else by the spatial hash
+# (XOR over k of c_k * pi_k, in 32-bit unsigned arithmetic, pi = (1, 2654435761, 805459861))
+# modulo T = 2^log2_T; the level's features are the multilinear interpolation of the
+# vertices' table entries.
+# ----------------------------------------------------------------------------
+HASH_PRIMES = (1, 2654435761, 805459861)
+
+
+def hash_resolutions(arch: Arch) -> list[int]:
+    return [int(np.floor(arch.hash_base * arch.hash_growth ** l)) for l in range(arch.hash_levels)]
+
+
+def grid_index_of(X: np.ndarray, N: int) -> np.ndarray:
+    """Integer pixel indices k of pixel centres x = (2k + 1 - N)/N (exact)."""
+    return np.rint((np.asarray(X, dtype=np.float64) * N + N - 1) / 2).astype(np.int64)
+
+
+def hash_corners(arch: Arch, K: np.ndarray, N: int, l: int):
+    """Vertex table indices [n, 2^d] and interpolation weights [n, 2^d] of level l for points
+    with integer grid indices K [n, d] on an N^d grid.  The level coordinate of index k is
+    (2k + 1) N_l / (2N); its integer part and fraction are formed exactly from that ratio."""
+    Nl = hash_resolutions(arch)[l]
+    T = 1 << arch.hash_log2_T
+    num = (2 * K + 1) * Nl                       # level coordinate = num / (2N)
+    c0 = num // (2 * N)
+    fr = (num % (2 * N)) / (2.0 * N)
+    n, d = K.shape
+    dense = (Nl + 1) ** d <= T
+    idx = np.zeros((n, 1 << d), dtype=np.int64)
+    wts = np.ones((n, 1 << d))
+    for v in range(1 << d):
+        c = c0 + np.array([(v >> k) & 1 for k in range(d)])[None, :]
+        for k in range(d):
+            wts[:, v] *= np.where((v >> k) & 1, fr[:, k], 1.0 - fr[:, k])
+        if dense:
+            idx[:, v] = sum(c[:, k] * (Nl + 1) ** k for k in range(d))
+        else:
+            h = np.zeros(n, dtype=np.uint64)
+            for k in range(d):
+                h ^= (c[:, k].astype(np.uint64) * np.uint64(HASH_PRIMES[k])) & np.uint64(0xFFFFFFFF)
+            idx[:, v] = (h & np.uint64(T - 1)).astype(np.int64)
+    return idx, wts
+
+
+def hash_tables(arch: Arch, theta) -> np.ndarray:
+    """The tables as [level][entry][feature] (a view of theta)."""
+    T = 1 << arch.hash_log2_T
+    return np.asarray(theta, dtype=np.float64)[:arch.table_params].reshape(arch.hash_levels, T, arch.hash_feats)
+
+
+def hash_encode(arch: Arch, theta, X: np.ndarray, N: int) -> np.ndarray:
+    """Concatenated level features [n, levels * feats] of the pixel centres X of an N^d grid."""
+    K = grid_index_of(X, N)
+    tab = hash_tables(arch, theta)
+    out = []
+    for l in range(arch.hash_levels):
+        idx, wts = hash_corners(arch, K, N, l)
+        out.append(np.einsum("nv,nvf->nf", wts, tab[l][idx]))
+    return np.concatenate(out, axis=1)
+
+
+def encode(arch: Arch, X: np.ndarray, theta=None, N: int | None = None) -> np.ndarray:
+    """Network input: gamma(x) for FFN (cos block first, then sin), x for SIREN, the hash
+    encoding (needs theta and the grid side N) for hash."""
+    if arch.kind == "hash":
+        return hash_encode(arch, theta, X, N)
     X = np.asarray(X, dtype=np.float64)
     if arch.kind == "ffn":
         P = 2.0 * np.pi * (X @ np.asarray(arch.B, dtype=np.float64).T)
@@ -305,7 +389,7 @@ def _fp32_features(arch: Arch, X32: np.ndarray) -> np.ndarray:
 
 
 def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | None = None,
-            X32: np.ndarray | None = None):
+            X32: np.ndarray | None = None, N: int | None = None):
     """f_theta(x_i) for every row of X.  With keep=True also returns the
     per-layer inputs h_{l-1}, pre-activations z_l and ReLU masks used by ``vjp``.
 
@@ -318,7 +402,7 @@ def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | 
     X32 gives the FP32 coordinates of the decision chain (default: X rounded).
     """
     layers = unpack(arch, theta)
-    h = encode(arch, X)
+    h = encode(arch, X, theta, N)
     hd = None
     if decide == "bf16" and arch.kind == "ffn":
         X32 = np.asarray(X).astype(np.float32) if X32 is None else X32
@@ -329,7 +413,7 @@ def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | 
         zs.append(z)
         if li == len(layers) - 1:
             h = z
-        elif arch.kind == "ffn":
+        elif arch.kind in ("ffn", "hash"):
             if hd is not None:
                 zd = hd @ bf16_round(W).T + b
                 m = zd > 0.0
@@ -346,7 +430,7 @@ def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | 
 
 
 def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray, decide: str | None = None,
-        X32: np.ndarray | None = None) -> np.ndarray:
+        X32: np.ndarray | None = None, N: int | None = None) -> np.ndarray:
     """sum_i w_i grad_theta f_theta(x_i), by reverse mode written out layer by layer.
 
     This is the Jacobian-transpose product [d E{f}/d theta]^T w of Sec. 3.
@@ -354,7 +438,7 @@ def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray, decide: str | None = No
     ``forward``).
     """
     layers = unpack(arch, theta)
-    _, hs, zs, masks = forward(arch, theta, X, keep=True, decide=decide, X32=X32)
+    _, hs, zs, masks = forward(arch, theta, X, keep=True, decide=decide, X32=X32, N=N)
     w = np.asarray(w, dtype=np.float64)
     grads = [None] * len(layers)
     # df/dz_out = 1, weighted per point by w_i
@@ -363,15 +447,26 @@ def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray, decide: str | None = No
         W, _ = layers[li]
         h_in = hs[li]
         grads[li] = (delta.T @ h_in, delta.sum(axis=0))   # dW = delta^T h, db = sum delta
+        g_h = delta @ W                                 # dL/dh_{li}
         if li == 0:
             break
-        g_h = delta @ W                                 # dL/dh_{li}
         z_prev = zs[li - 1]
-        if arch.kind == "ffn":
+        if arch.kind in ("ffn", "hash"):
             delta = g_h * masks[li - 1]
         else:
             delta = g_h * (arch.omega0 * np.cos(arch.omega0 * z_prev))
     flat = []
+    if arch.kind == "hash":
+        # the encoding is linear in the table entries: each vertex entry receives its
+        # interpolation weight times the gradient of its level's feature
+        gt = np.zeros_like(hash_tables(arch, theta))
+        K = grid_index_of(X, N)
+        F = arch.hash_feats
+        for l in range(arch.hash_levels):
+            idx, wts = hash_corners(arch, K, N, l)
+            for v in range(idx.shape[1]):
+                np.add.at(gt[l], idx[:, v], wts[:, v:v + 1] * g_h[:, l * F:(l + 1) * F])
+        flat.append(gt.reshape(-1))
     for gW, gb in grads:
         flat.append(gW.reshape(-1))
         flat.append(gb.reshape(-1))
@@ -389,7 +484,7 @@ def ls_loss(z, y):
 
 def evaluate_image(arch: Arch, theta, g: Geometry) -> np.ndarray:
     """E{f_theta} = [f(x_1) .. f(x_n)] on the full grid (Sec. 3), flat."""
-    return forward(arch, theta, grid_coords(g.d, g.N))
+    return forward(arch, theta, grid_coords(g.d, g.N), N=g.N)
 
 
 def backprojected_residual(arch: Arch, theta, g: Geometry, y):
@@ -404,7 +499,7 @@ def backprojected_residual(arch: Arch, theta, g: Geometry, y):
 def full_gradient(arch: Arch, theta, g: Geometry, y):
     """grad L(theta) = sum_{i=1..n} v_i grad f(x_i) (Sec. 3).  Returns (L, grad, v)."""
     L, _, _, v = backprojected_residual(arch, theta, g, y)
-    grad = vjp(arch, theta, grid_coords(g.d, g.N), v)
+    grad = vjp(arch, theta, grid_coords(g.d, g.N), v, N=g.N)
     return L, grad, v
 
 
@@ -420,7 +515,7 @@ def estimator(arch: Arch, theta, g: Geometry, v, I, scale=None, decide=None) -> 
         scale = n / I.size
     X = grid_coords(g.d, g.N, I)
     return vjp(arch, theta, X, scale * np.asarray(v, dtype=np.float64)[I], decide=decide,
-               X32=grid_coords_fp32(g.d, g.N, I))
+               X32=grid_coords_fp32(g.d, g.N, I), N=g.N)
 
 
 def virtual_loss(arch: Arch, theta, g: Geometry, v, I, scale=None) -> float:
@@ -429,7 +524,7 @@ def virtual_loss(arch: Arch, theta, g: Geometry, v, I, scale=None) -> float:
     if scale is None:
         scale = g.n / I.size
     X = grid_coords(g.d, g.N, I)
-    return float(scale * (np.asarray(v, dtype=np.float64)[I] @ forward(arch, theta, X)))
+    return float(scale * (np.asarray(v, dtype=np.float64)[I] @ forward(arch, theta, X, N=g.N)))
 
 
 @dataclass
