@@ -34,6 +34,8 @@ METRIC = "INR-CT grad steps/s, proj+backproj GRays/s; BF16 vs FP32 at <=1e-2 gra
 L2_BYTES = 129 * 1024 * 1024
 BATCHED = "batched16_siren128"
 VJP_CHUNK = 1 << 20          # points per VJP chunk (the library's scratch unit)
+# FP32 FMA peak of the SIMT path: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -129,13 +131,15 @@ def oracle_sample(w, frac: float, seed: int = 0) -> float:
     og = O.Geometry(g.kind, g.N, Vs, g.A, g.B, g.du, g.dv, g.sod, g.sdd, g.angle0,
                     g.span * Vs / g.V)
     B = synth.fourier_matrix(a.n_feat, a.d, a.sigma, seed) if a.kind == "ffn" else None
-    oa = O.Arch(a.kind, a.d, a.width, a.n_hidden, a.n_feat, B, a.omega0)
+    oa = O.Arch(a.kind, a.d, a.width, a.n_hidden, a.n_feat, B, a.omega0, hash_levels=a.hash_levels,
+                hash_feats=a.hash_feats, hash_log2_T=a.hash_log2_T, hash_base=a.hash_base,
+                hash_growth=a.hash_growth)
     theta = synth.init_theta(a, seed)
     n_pts = max(1, int(g.n * frac))
     n_I = max(1, int(w.batch * frac))
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
-    f = O.forward(oa, theta, O.grid_coords(g.d, g.N, np.arange(n_pts)))
+    f = O.forward(oa, theta, O.grid_coords(g.d, g.N, np.arange(n_pts)), N=g.N)
     t1 = time.perf_counter()
     img = np.zeros(g.n)
     img[:n_pts] = f
@@ -144,7 +148,7 @@ def oracle_sample(w, frac: float, seed: int = 0) -> float:
     v = O.backproject(og, r)
     t2 = time.perf_counter()
     I = rng.choice(g.n, n_I, replace=False)
-    ghat = O.vjp(oa, theta, O.grid_coords(g.d, g.N, I), (g.n / w.batch) * v[I])
+    ghat = O.vjp(oa, theta, O.grid_coords(g.d, g.N, I), (g.n / w.batch) * v[I], N=g.N)
     t3 = time.perf_counter()
     st = O.AdamState(np.zeros_like(theta), np.zeros_like(theta))
     O.adam_step(theta, ghat, st, lr=w.lr)
@@ -398,6 +402,8 @@ def main():
         raise SystemExit(f"unknown workload {args.workload}; choose from {sorted(wl) + [BATCHED]}")
     else:
         w = wl[args.workload]
+    if not isinstance(w, list) and w.arch.kind == "hash":
+        args.prec = "fp32"                       # the hash-encoded INR has the FP32 path only
     if args.frac is not None and not isinstance(w, list):
         w.batch = max(1, int(round(args.frac * w.geom.n)))
 
@@ -619,8 +625,13 @@ def main():
                 "traffic": recorded_traffic("mlp_tile_kernel_" + ("eval" if dominant == "eval_mlp_kernel"
                                                                   else "vjp"), w.name)}
     if args.prec != "bf16":
-        roofline = {"kernel": "simt_fwd_kernel", "bound": "alu", "achieved": achieved, "peak": None,
-                    "unit": "TFLOP/s", "frac": None, "traffic": None}
+        # FP32 SIMT path: FMA-bound at best (nominal peak from unit counts and the maximum clock)
+        roofline = {"kernel": "simt_fwd_kernel + simt_bwd_kernel (" +
+                              ("grid evaluation" if dominant == "eval_mlp_kernel" else "VJP") + ")",
+                    "bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_SIMT_TFLOPS,
+                    "peak_source": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                    "traffic": None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -66,6 +66,7 @@ typedef struct CUstream_st* cudaStream_t;
 /* INR kinds and arithmetic of the MLP */
 #define INRCT_FFN_RELU 0 /* Gaussian Fourier features + ReLU MLP */
 #define INRCT_SIREN 1    /* sine-activated MLP */
+#define INRCT_HASH 2     /* multiresolution hash encoding + ReLU MLP (FP32 path only) */
 #define INRCT_FP32 0     /* SIMT FP32 path (the plain comparator) */
 #define INRCT_BF16 1     /* tcgen05 BF16 x BF16 -> FP32 tensor-core path */
 
@@ -100,20 +101,41 @@ typedef struct {
 } inrct_grid;
 
 /*
- * INR architecture (Sec. 4 uses FFN, SIREN and hash-encoded MLPs; FFN and
- * SIREN are implemented).  B: device pointer, n_feat x d FP32 row-major
- * Fourier matrix (FFN only; may be NULL for SIREN).  The FFN input is
+ * INR architecture (Sec. 4 trains FFN, SIREN and hash-encoded MLPs; all three
+ * are implemented).  B: device pointer, n_feat x d FP32 row-major Fourier
+ * matrix (FFN only; may be NULL otherwise).  The FFN input is
  * [cos(2 pi B x); sin(2 pi B x)] (cos block first).
+ *
+ * Hash encoding (INRCT_HASH; the paper names the encoding of Mueller et al.
+ * without parameters, so these are the usual ones): level l = 0..hash_levels-1
+ * has resolution N_l = floor(hash_base * hash_growth^l), computed on the host
+ * in double precision.  Grid point with integer index k (per axis) has level
+ * coordinate (2k + 1) N_l / (2N); its 2^d surrounding vertices c (integers in
+ * [0, N_l]) index the level's table of T = 2^hash_log2_T entries densely
+ * (sum_k c_k (N_l + 1)^k) when (N_l + 1)^d <= T, else by the spatial hash
+ * (c_0 * 1) xor (c_1 * 2654435761) xor (c_2 * 805459861) in 32-bit unsigned
+ * arithmetic, modulo T.  The level's hash_feats features are the multilinear
+ * interpolation of the vertices' entries; the MLP input is the concatenation
+ * over levels (level-major), followed by n_hidden Linear + ReLU layers and
+ * Linear(width, 1).  theta then begins with the tables, FP32
+ * [level][entry][feature], before the layers.  The table gradient is a
+ * scatter-add with FP64 atomics, so its last bits may differ between runs.
  */
 typedef struct {
-  int kind;    /* INRCT_FFN_RELU or INRCT_SIREN */
+  int kind;    /* INRCT_FFN_RELU, INRCT_SIREN or INRCT_HASH */
   int d;       /* input dimension, equals the grid's */
   int n_feat;  /* F, FFN only */
   const float* B;
   float omega0; /* SIREN only */
   int n_hidden; /* number of nonlinear layers */
   int width;    /* hidden width */
-  int prec;     /* INRCT_FP32 or INRCT_BF16 */
+  int prec;     /* INRCT_FP32 or INRCT_BF16 (hash: INRCT_FP32 only) */
+  /* hash encoding, INRCT_HASH only (zero otherwise) */
+  int hash_levels;    /* 1..16 */
+  int hash_feats;     /* features per level: 1, 2, 4 or 8; hash_levels * hash_feats <= 64 */
+  int hash_log2_T;    /* table size 2^hash_log2_T entries per level, 4..24 */
+  int hash_base;      /* coarsest resolution N_0, 1..65536 */
+  double hash_growth; /* per-level growth factor, 1 <= hash_growth <= 4, N_l <= 2^20 */
 } inrct_mlp;
 
 /* Adam hyper-parameters; t is the 1-based index of the step being taken. */

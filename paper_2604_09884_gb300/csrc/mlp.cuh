@@ -5,15 +5,22 @@
 namespace inrct {
 
 constexpr int kMaxLayers = 10;  // n_hidden + 1 <= kMaxLayers
+constexpr int kMaxHashLevels = 16;
+constexpr int kMaxHashInputs = 64;  // hash levels x features per level
 
 // Network description with theta offsets, built on the host from inrct_mlp.
 struct Net {
-  int kind;      // INRCT_FFN_RELU / INRCT_SIREN
+  int kind;      // INRCT_FFN_RELU / INRCT_SIREN / INRCT_HASH
   int d, F, W, L;  // input dim, Fourier features, width, nonlinear layers
   float omega0;
   const float* B;  // device F x d
-  int K0;          // input width of layer 1 (2F or d)
+  int K0;          // input width of layer 1 (2F, d, or hash levels x features)
   int64_t p;       // parameter count
+  // hash encoding: levels, features per level, log2 of the table size, the level
+  // resolutions, and the table parameters (theta[0, n_table) holds the tables)
+  int hL, hF, hlog2T;
+  int hres[kMaxHashLevels];
+  int64_t n_table;
   int64_t offW[kMaxLayers], offb[kMaxLayers];  // layer l = 0..L (L is the output layer)
   int in_dim[kMaxLayers], out_dim[kMaxLayers];
 };

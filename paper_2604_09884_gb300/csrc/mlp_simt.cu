@@ -14,6 +14,11 @@
 //   3. dW_l = sum_points delta_l a_{l-1}^T and db_l = sum delta_l as a split-K
 //      SIMT GEMM with FP32 partials per split;
 //   4. FP64 reduction of the partials into the gradient (accumulated over chunks).
+//
+// Hash-encoded INR (Sec. 4, "Hash Enc."): the layer-1 input is gathered from the
+// tables at theta[0, n_table) by the forward kernel; the backward kernel finishes
+// with g = W_1^T delta_1 per point and scatters w_v g into the 2^d vertex entries
+// of every level with FP64 atomics (the encoding is linear in the entries).
 #include <math.h>
 
 #include "mlp.cuh"
@@ -26,6 +31,9 @@ struct NetDev {
   int kind, d, F, W, L, K0, N;
   float omega0;
   const float* B;
+  int hL, hF, hlog2T;
+  unsigned hdense;  // bit l: level l is looked up densely
+  int hres[kMaxHashLevels];
 };
 
 struct LayerOffs {
@@ -43,6 +51,18 @@ NetDev dev_of(const Net& n, int N) {
   d.N = N;
   d.omega0 = n.omega0;
   d.B = n.B;
+  d.hL = n.hL;
+  d.hF = n.hF;
+  d.hlog2T = n.hlog2T;
+  d.hdense = 0;
+  for (int l = 0; l < kMaxHashLevels; ++l) {
+    d.hres[l] = l < n.hL ? n.hres[l] : 0;
+    if (l < n.hL) {
+      int64_t cells = 1;
+      for (int a = 0; a < n.d; ++a) cells *= (int64_t)n.hres[l] + 1;
+      if (cells <= ((int64_t)1 << n.hlog2T)) d.hdense |= 1u << l;
+    }
+  }
   return d;
 }
 
@@ -63,10 +83,78 @@ __device__ __forceinline__ int64_t grid_size(const NetDev& n) {
 }
 
 __device__ __forceinline__ float act(const NetDev& n, float z) {
-  return n.kind == INRCT_FFN_RELU ? fmaxf(z, 0.f) : sinf(n.omega0 * z);
+  return n.kind != INRCT_SIREN ? fmaxf(z, 0.f) : sinf(n.omega0 * z);
 }
 __device__ __forceinline__ float dact(const NetDev& n, float z) {
-  return n.kind == INRCT_FFN_RELU ? (z > 0.f ? 1.f : 0.f) : n.omega0 * cosf(n.omega0 * z);
+  return n.kind != INRCT_SIREN ? (z > 0.f ? 1.f : 0.f) : n.omega0 * cosf(n.omega0 * z);
+}
+
+// Level l of the hash encoding at the grid point with per-axis indices k[0..D): the
+// table entries of its 2^D surrounding vertices and their multilinear weights.  The
+// level coordinate (2k + 1) N_l / (2N) is split exactly in integers; its fraction is
+// one correctly rounded FP32 division of integers below 2^14.  D is a template
+// parameter so that every loop unrolls and the vertex state stays in registers.
+template <int D>
+__device__ __forceinline__ void hash_vertices(const NetDev& n, int l, const int* k, uint32_t (&ent)[1 << D],
+                                              float (&w)[1 << D]) {
+  const uint32_t Nl = (uint32_t)n.hres[l];
+  const int64_t twoN = 2 * (int64_t)n.N;
+  uint32_t c0[D];
+  float fr[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int64_t num = (2 * (int64_t)k[a] + 1) * (int64_t)Nl;
+    c0[a] = (uint32_t)(num / twoN);
+    fr[a] = __fdiv_rn((float)(num % twoN), (float)twoN);
+  }
+  const bool dense = (n.hdense >> l) & 1u;
+  const uint32_t mask = (1u << n.hlog2T) - 1u;
+  constexpr uint32_t kPrime[3] = {1u, 2654435761u, 805459861u};
+#pragma unroll
+  for (int v = 0; v < (1 << D); ++v) {
+    float wv = 1.f;
+    uint32_t lin = 0, stride = 1, h = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const uint32_t bit = (v >> a) & 1;
+      const uint32_t c = c0[a] + bit;
+      wv *= bit ? fr[a] : 1.f - fr[a];
+      lin += c * stride;  // dense levels have (N_l + 1)^D <= T <= 2^24 entries: no wrap
+      stride *= Nl + 1u;
+      h ^= c * kPrime[a];  // 32-bit unsigned, wraps by definition
+    }
+    ent[v] = dense ? lin : (h & mask);
+    w[v] = wv;
+  }
+}
+
+// Features of level l at the point: sum_v w_v table[ent_v][f], f < F.
+template <int D>
+__device__ __forceinline__ void hash_gather(const NetDev& n, const float* __restrict__ theta, int l,
+                                            const int* k, float* out) {
+  uint32_t ent[1 << D];
+  float w[1 << D];
+  hash_vertices<D>(n, l, k, ent, w);
+  const float* tab = theta + ((int64_t)l << n.hlog2T) * n.hF;
+  for (int f = 0; f < n.hF; ++f) {
+    float a = 0.f;
+#pragma unroll
+    for (int v = 0; v < (1 << D); ++v) a = fmaf(w[v], __ldg(tab + (int64_t)ent[v] * n.hF + f), a);
+    out[f] = a;
+  }
+}
+
+// Table gradient of level l at the point: entry ent_v, feature f receives w_v g[f].
+template <int D>
+__device__ __forceinline__ void hash_scatter(const NetDev& n, double* __restrict__ gtab, int l, const int* k,
+                                             const float* g) {
+  uint32_t ent[1 << D];
+  float w[1 << D];
+  hash_vertices<D>(n, l, k, ent, w);
+  double* gl = gtab + ((int64_t)l << n.hlog2T) * n.hF;
+#pragma unroll
+  for (int v = 0; v < (1 << D); ++v)
+    for (int f = 0; f < n.hF; ++f) atomicAdd(gl + (int64_t)ent[v] * n.hF + f, (double)w[v] * (double)g[f]);
 }
 
 __global__ void transpose_w_kernel(const float* __restrict__ theta, int64_t offW, int out, int in,
@@ -87,6 +175,7 @@ __global__ void __launch_bounds__(256)
                     float* __restrict__ out_f, float* __restrict__ E, float* __restrict__ Z) {
   extern __shared__ float sh[];
   __shared__ float xs[TP][3];
+  __shared__ int ks[TP][3];
   __shared__ float red[TP][8];
   const int W = net.W, K0 = net.K0;
   const int Kmax = K0 > W ? K0 : W;
@@ -103,9 +192,20 @@ __global__ void __launch_bounds__(256)
     xs[t][0] = x[0];
     xs[t][1] = x[1];
     xs[t][2] = x[2];
+    ks[t][0] = (int)(i % net.N);
+    ks[t][1] = (int)((i / net.N) % net.N);
+    ks[t][2] = net.d == 3 ? (int)(i / ((int64_t)net.N * net.N)) : 0;
   }
   __syncthreads();
-  if (net.kind == INRCT_FFN_RELU) {
+  if (net.kind == INRCT_HASH) {
+    // one thread per (point, level): interpolate the level's features
+    for (int e = t; e < TP * net.hL; e += W) {
+      const int p = e / net.hL, l = e % net.hL;
+      float* out = bufA + p * Kmax + l * net.hF;
+      if (net.d == 3) hash_gather<3>(net, theta, l, ks[p], out);
+      else hash_gather<2>(net, theta, l, ks[p], out);
+    }
+  } else if (net.kind == INRCT_FFN_RELU) {
     for (int e = t; e < TP * net.F; e += W) {
       const int p = e / net.F, f = e % net.F;
       const float* Bf = net.B + (int64_t)f * net.d;
@@ -176,7 +276,8 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     simt_bwd_kernel(NetDev net, LayerOffs lo, const float* __restrict__ theta, int64_t npts,
                     const int32_t* __restrict__ idx, const float* __restrict__ v, float scale,
-                    const float* __restrict__ Z, float* __restrict__ Dl, float* __restrict__ dout) {
+                    const float* __restrict__ Z, float* __restrict__ Dl, float* __restrict__ dout,
+                    double* __restrict__ gtab) {
   extern __shared__ float dsh[];  // [TP][W]
   __shared__ float dsc[TP];
   const int W = net.W, L = net.L;
@@ -227,6 +328,31 @@ __global__ void __launch_bounds__(256)
       dsh[p * W + t] = d;
     }
     __syncthreads();
+  }
+  if (gtab) {
+    // hash tables: g = W_1^T delta_1 is the gradient of the layer-1 input; each vertex
+    // entry of each level receives its weight times the level's slice of g
+    __shared__ float gsh[TP * kMaxHashInputs];
+    const int K0 = net.K0;
+    const float* W0 = theta + lo.W[0];  // [W][K0]
+    for (int e = t; e < TP * K0; e += W) {
+      const int p = e / K0, j = e % K0;
+      float a = 0.f;
+      for (int o = 0; o < W; ++o) a = fmaf(dsh[p * W + o], __ldg(W0 + (int64_t)o * K0 + j), a);
+      gsh[e] = a;
+    }
+    __syncthreads();
+    for (int e = t; e < TP * net.hL; e += W) {
+      const int p = e / net.hL, l = e % net.hL;
+      const int64_t q = p0 + p;
+      if (q >= npts || dsc[p] == 0.f) continue;  // no contribution
+      const int64_t i = idx ? (int64_t)idx[q] : q;
+      const int k[3] = {(int)(i % net.N), (int)((i / net.N) % net.N),
+                        net.d == 3 ? (int)(i / ((int64_t)net.N * net.N)) : 0};
+      const float* g = gsh + p * K0 + l * net.hF;
+      if (net.d == 3) hash_scatter<3>(net, gtab, l, k, g);
+      else hash_scatter<2>(net, gtab, l, k, g);
+    }
   }
 }
 
@@ -421,8 +547,15 @@ int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_
     if (c0 == 0) prof_mark(kMarkVjpKernel, st);
     simt_fwd_kernel<<<nb, n.W, fwd_smem(n), st>>>(nd, lo, theta, w.Wt, np, id, nullptr, w.E, w.Z);
     INRCT_CHECK_LAUNCH("simt vjp forward");
-    simt_bwd_kernel<<<nb, n.W, sizeof(float) * TP * n.W, st>>>(nd, lo, theta, np, id, v,
-                                                                (float)scale, w.Z, w.D, w.dout);
+    if (c0 == 0 && n.n_table > 0) {
+      const cudaError_t e = cudaMemsetAsync(grad_f64, 0, sizeof(double) * n.n_table, st);
+      if (e != cudaSuccess) {
+        set_error("hash table gradient clear: %s", cudaGetErrorString(e));
+        return INRCT_ERR_CUDA;
+      }
+    }
+    simt_bwd_kernel<<<nb, n.W, sizeof(float) * TP * n.W, st>>>(
+        nd, lo, theta, np, id, v, (float)scale, w.Z, w.D, w.dout, n.n_table > 0 ? grad_f64 : nullptr);
     INRCT_CHECK_LAUNCH("simt vjp backward");
     if (c0 == 0) prof_mark(kMarkVjpKernelDone, st);
     const int S = splits_for(np);
@@ -437,7 +570,7 @@ int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_
         ymode = 0;
       } else {
         Y = w.Z + (int64_t)(l - 1) * np * n.W;
-        ymode = n.kind == INRCT_FFN_RELU ? 1 : 2;
+        ymode = n.kind == INRCT_SIREN ? 2 : 1;
       }
       dim3 grd(ceil_div(O, GT), ceil_div(K + 1, GT), S);
       simt_dw_kernel<<<grd, 256, 0, st>>>(X, O, Y, K, ymode, n.omega0, np, per, w.part);

@@ -1142,6 +1142,10 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
 }  // namespace
 
 bool tc_supported(const Net& n, char* why, size_t len) {
+  if (n.kind == INRCT_HASH) {
+    snprintf(why, len, "the hash-encoded INR has no tensor-core path");
+    return false;
+  }
   if (n.W != 128 && n.W != 256) {
     snprintf(why, len, "width %d unsupported (128 or 256)", n.W);
     return false;

@@ -7,8 +7,8 @@ namespace inrct {
 
 int make_net(const inrct_mlp* mlp, const inrct_grid* grid, Net* n) {
   INRCT_REQUIRE(mlp, "mlp descriptor must not be NULL");
-  INRCT_REQUIRE(mlp->kind == INRCT_FFN_RELU || mlp->kind == INRCT_SIREN, "unknown INR kind %d",
-                mlp->kind);
+  INRCT_REQUIRE(mlp->kind == INRCT_FFN_RELU || mlp->kind == INRCT_SIREN || mlp->kind == INRCT_HASH,
+                "unknown INR kind %d", mlp->kind);
   INRCT_REQUIRE(mlp->d == 2 || mlp->d == 3, "input dimension d=%d must be 2 or 3", mlp->d);
   INRCT_REQUIRE(!grid || grid->d == mlp->d, "mlp d=%d differs from grid d=%d", mlp->d,
                 grid ? grid->d : 0);
@@ -22,8 +22,37 @@ int make_net(const inrct_mlp* mlp, const inrct_grid* grid, Net* n) {
     INRCT_REQUIRE(mlp->n_feat >= 1 && mlp->n_feat <= 2048, "n_feat=%d out of range (1..2048)",
                   mlp->n_feat);
     INRCT_REQUIRE(mlp->B != nullptr, "FFN needs the Fourier matrix B");
-  } else {
+  } else if (mlp->kind == INRCT_SIREN) {
     INRCT_REQUIRE(mlp->omega0 > 0.f, "SIREN needs omega0 > 0");
+  } else {
+    INRCT_REQUIRE(mlp->hash_levels >= 1 && mlp->hash_levels <= kMaxHashLevels,
+                  "hash_levels=%d out of range (1..%d)", mlp->hash_levels, kMaxHashLevels);
+    const int hf = mlp->hash_feats;
+    INRCT_REQUIRE(hf == 1 || hf == 2 || hf == 4 || hf == 8, "hash_feats=%d must be 1, 2, 4 or 8", hf);
+    INRCT_REQUIRE(mlp->hash_levels * hf <= kMaxHashInputs, "hash_levels x hash_feats = %d exceeds %d",
+                  mlp->hash_levels * hf, kMaxHashInputs);
+    INRCT_REQUIRE(mlp->hash_log2_T >= 4 && mlp->hash_log2_T <= 24, "hash_log2_T=%d out of range (4..24)",
+                  mlp->hash_log2_T);
+    INRCT_REQUIRE(mlp->hash_base >= 1 && mlp->hash_base <= 65536, "hash_base=%d out of range (1..65536)",
+                  mlp->hash_base);
+    INRCT_REQUIRE(mlp->hash_growth >= 1.0 && mlp->hash_growth <= 4.0,
+                  "hash_growth=%g out of range [1, 4]", mlp->hash_growth);
+    INRCT_REQUIRE(mlp->prec == INRCT_FP32, "the hash-encoded INR runs on the FP32 path only");
+  }
+  n->hL = n->hF = n->hlog2T = 0;
+  n->n_table = 0;
+  if (mlp->kind == INRCT_HASH) {
+    n->hL = mlp->hash_levels;
+    n->hF = mlp->hash_feats;
+    n->hlog2T = mlp->hash_log2_T;
+    for (int l = 0; l < n->hL; ++l) {
+      // N_l = floor(base * growth^l), in double precision as the definition reads
+      const double r = std::floor((double)mlp->hash_base * std::pow(mlp->hash_growth, (double)l));
+      INRCT_REQUIRE(r >= 1.0 && r <= (double)(1 << 20), "hash level %d resolution %g out of range (1..2^20)",
+                    l, r);
+      n->hres[l] = (int)r;
+    }
+    n->n_table = (int64_t)n->hL * ((int64_t)1 << n->hlog2T) * n->hF;
   }
   n->kind = mlp->kind;
   n->d = mlp->d;
@@ -32,8 +61,10 @@ int make_net(const inrct_mlp* mlp, const inrct_grid* grid, Net* n) {
   n->L = mlp->n_hidden;
   n->omega0 = mlp->omega0;
   n->B = mlp->B;
-  n->K0 = mlp->kind == INRCT_FFN_RELU ? 2 * mlp->n_feat : mlp->d;
-  int64_t off = 0;
+  n->K0 = mlp->kind == INRCT_FFN_RELU ? 2 * mlp->n_feat
+          : mlp->kind == INRCT_HASH    ? n->hL * n->hF
+                                       : mlp->d;
+  int64_t off = n->n_table;
   for (int l = 0; l <= n->L; ++l) {
     n->in_dim[l] = l == 0 ? n->K0 : n->W;
     n->out_dim[l] = l == n->L ? 1 : n->W;

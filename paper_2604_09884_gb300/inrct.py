@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libinrct.so")
 
 PAR2D, FAN2D, CONE3D = 0, 1, 2
-FFN_RELU, SIREN = 0, 1
+FFN_RELU, SIREN, HASH = 0, 1, 2
 FP32, BF16 = 0, 1
 LOSS_LS, LOSS_FLS = 0, 1
 _GKIND = {"par2d": PAR2D, "fan2d": FAN2D, "cone3d": CONE3D}
@@ -48,7 +48,10 @@ class Grid(ctypes.Structure):
 class Mlp(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("d", ctypes.c_int), ("n_feat", ctypes.c_int),
                 ("B", ctypes.c_void_p), ("omega0", ctypes.c_float), ("n_hidden", ctypes.c_int),
-                ("width", ctypes.c_int), ("prec", ctypes.c_int)]
+                ("width", ctypes.c_int), ("prec", ctypes.c_int),
+                ("hash_levels", ctypes.c_int), ("hash_feats", ctypes.c_int),
+                ("hash_log2_T", ctypes.c_int), ("hash_base", ctypes.c_int),
+                ("hash_growth", ctypes.c_double)]
 
 
 class Adam(ctypes.Structure):
@@ -187,8 +190,12 @@ def mlp_desc(a: synth.ArchSpec, prec: int, B=None, device="cuda") -> MlpHandle:
     if a.kind == "ffn":
         Bt = torch.as_tensor(B, dtype=torch.float32, device=device).contiguous()
         assert Bt.shape == (a.n_feat, a.d)
-    desc = Mlp(FFN_RELU if a.kind == "ffn" else SIREN, a.d, a.n_feat,
-               Bt.data_ptr() if Bt is not None else None, a.omega0, a.n_hidden, a.width, prec)
+    kind = {"ffn": FFN_RELU, "siren": SIREN, "hash": HASH}[a.kind]
+    desc = Mlp(kind, a.d, a.n_feat, Bt.data_ptr() if Bt is not None else None, a.omega0,
+               a.n_hidden, a.width, prec)
+    if a.kind == "hash":
+        desc.hash_levels, desc.hash_feats, desc.hash_log2_T = a.hash_levels, a.hash_feats, a.hash_log2_T
+        desc.hash_base, desc.hash_growth = a.hash_base, a.hash_growth
     return MlpHandle(desc, Bt, a)
 
 

@@ -51,17 +51,28 @@ class GeomSpec:
 
 @dataclass
 class ArchSpec:
-    kind: str          # 'ffn' | 'siren'
+    kind: str          # 'ffn' | 'siren' | 'hash'
     d: int
     width: int
     n_hidden: int
     n_feat: int = 0
     sigma: float = 10.0
     omega0: float = 30.0
+    hash_levels: int = 16
+    hash_feats: int = 2
+    hash_log2_T: int = 19
+    hash_base: int = 16
+    hash_growth: float = 1.5
 
     @property
     def d_in(self):
+        if self.kind == "hash":
+            return self.hash_levels * self.hash_feats
         return 2 * self.n_feat if self.kind == "ffn" else self.d
+
+    @property
+    def table_params(self):
+        return self.hash_levels * (1 << self.hash_log2_T) * self.hash_feats if self.kind == "hash" else 0
 
     def layer_shapes(self):
         s = [(self.width, self.d_in)] + [(self.width, self.width)] * (self.n_hidden - 1)
@@ -69,7 +80,7 @@ class ArchSpec:
 
     @property
     def p(self):
-        return sum(o * i + o for o, i in self.layer_shapes())
+        return self.table_params + sum(o * i + o for o, i in self.layer_shapes())
 
 
 @dataclass
@@ -86,7 +97,7 @@ class Workload:
 
 
 def workloads() -> dict[str, Workload]:
-    """The five synthetic workloads (sizes from the paper's 2-D/3-D studies, Sec. 4)."""
+    """The synthetic workloads (sizes from the paper's 2-D/3-D studies, Sec. 4)."""
     w = {}
     g1 = GeomSpec("par2d", 128, 60, 183, span=math.pi)
     w["par2d_128_ffn64"] = Workload(
@@ -98,6 +109,12 @@ def workloads() -> dict[str, Workload]:
         "fan2d_512_siren256", g2, ArchSpec("siren", 2, 256, 5, omega0=30.0),
         n_shapes=20, noise=0.01, batch=g2.n // 4, lr=1e-4, seed=2,
         note="2-D fan 512^2, 90 views/360deg, 729 curved bins, SOD/SDD 1000/1500; SIREN 5x256 w0=30")
+    w["fan2d_512_hash64"] = Workload(
+        "fan2d_512_hash64", g2, ArchSpec("hash", 2, 64, 2, hash_levels=16, hash_feats=2, hash_log2_T=19,
+                                         hash_base=16, hash_growth=1.26),
+        n_shapes=20, noise=0.01, batch=g2.n // 4, lr=1e-3, seed=6,
+        note="2-D fan 512^2 as above; hash encoding 16 levels x 2 features, T=2^19, N_l=16..512 "
+             "(growth 1.26), 2x64 ReLU; FP32")
     g3 = GeomSpec("cone3d", 256, 40, 384, 384, sod=1000.0, sdd=1500.0, span=2 * math.pi)
     w["cone3d_256_ffn256"] = Workload(
         "cone3d_256_ffn256", g3, ArchSpec("ffn", 3, 256, 4, n_feat=256, sigma=8.0),
@@ -180,16 +197,20 @@ def fourier_matrix(F: int, d: int, sigma: float, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).normal(0.0, sigma, size=(F, d))
 
 
-def init_theta(arch: ArchSpec, seed: int) -> np.ndarray:
-    """Flat theta in the layer order [W_1, b_1, ..., W_out, b_out] (W row-major [out][in]).
+def init_theta(arch: ArchSpec, seed: int, table_scale: float = 1e-4) -> np.ndarray:
+    """Flat theta in the layer order [W_1, b_1, ..., W_out, b_out] (W row-major [out][in]),
+    preceded by the hash tables [level][entry][feature] for the hash-encoded INR.
 
-    FFN: Xavier-uniform weights, zero biases.  SIREN: first layer U(-1/d, 1/d),
-    later layers U(+-sqrt(6/fan_in)/omega0); biases U(+-1/sqrt(fan_in))."""
+    FFN and hash: Xavier-uniform weights, zero biases; hash tables U(+-table_scale).
+    SIREN: first layer U(-1/d, 1/d), later layers U(+-sqrt(6/fan_in)/omega0); biases
+    U(+-1/sqrt(fan_in))."""
     rng = np.random.default_rng(seed)
     parts = []
+    if arch.kind == "hash":
+        parts.append(rng.uniform(-table_scale, table_scale, size=arch.table_params))
     shapes = arch.layer_shapes()
     for li, (o, i) in enumerate(shapes):
-        if arch.kind == "ffn":
+        if arch.kind in ("ffn", "hash"):
             a = math.sqrt(6.0 / (i + o))
             W = rng.uniform(-a, a, size=(o, i))
             b = np.zeros(o)

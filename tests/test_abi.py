@@ -35,11 +35,11 @@ def test_exports_every_declared_symbol(L):
 
 def test_param_and_ray_counts(L):
     for w in synth.workloads().values():
-        B_ = torch.zeros(max(w.arch.n_feat, 1), w.arch.d)
-        h = inrct.MlpHandle(inrct.Mlp(0 if w.arch.kind == "ffn" else 1, w.arch.d, w.arch.n_feat,
-                                      ctypes.c_void_p(256).value, w.arch.omega0, w.arch.n_hidden,
-                                      w.arch.width, inrct.FP32), None, w.arch)
-        assert inrct.num_params(h) == w.arch.p
+        a = w.arch
+        m = inrct.Mlp({"ffn": 0, "siren": 1, "hash": 2}[a.kind], a.d, a.n_feat, ctypes.c_void_p(256).value,
+                      a.omega0, a.n_hidden, a.width, inrct.FP32, a.hash_levels, a.hash_feats, a.hash_log2_T,
+                      a.hash_base, a.hash_growth)
+        assert inrct.num_params(inrct.MlpHandle(m, None, a)) == a.p
         assert inrct.num_rays(w.geom) == w.geom.m
 
 
@@ -136,3 +136,25 @@ def test_view_subset_rejects_uneven_splits_and_keeps_the_scan():
     s = inrct.view_subset(g, 4, 3)
     assert (s.V, s.A, s.sod, s.span) == (3, 45, 128.0, g.span)
     assert abs(s.angle0 - (0.3 + g.span * 3 / 12)) < 1e-15
+
+
+def test_hash_descriptor_is_validated_on_the_host(L):
+    grd = inrct.grid_desc(2, 64)
+
+    def mlp(**kw):
+        f = dict(levels=4, feats=2, log2T=10, base=4, growth=1.5, prec=inrct.FP32, width=64)
+        f.update(kw)
+        return inrct.Mlp(inrct.HASH, 2, 0, None, 0.0, 2, f["width"], f["prec"], f["levels"], f["feats"],
+                         f["log2T"], f["base"], f["growth"])
+
+    good = mlp()
+    assert L.inrct_num_params(ctypes.byref(good)) == 4 * 1024 * 2 + (64 * 8 + 64) + (64 * 64 + 64) + 65
+    assert L.inrct_vjp_ws_bytes(ctypes.byref(good), ctypes.byref(grd), 1000) > 0
+    bad = [mlp(levels=0), mlp(levels=17), mlp(feats=3), mlp(levels=16, feats=8), mlp(log2T=3),
+           mlp(log2T=25), mlp(base=0), mlp(growth=0.9), mlp(growth=4.5), mlp(prec=inrct.BF16),
+           mlp(levels=16, base=65536, growth=4.0)]          # finest resolution above 2^20
+    for m in bad:
+        assert L.inrct_num_params(ctypes.byref(m)) == 0
+        rc = L.inr_eval_grid(ctypes.byref(m), _fake(), ctypes.byref(grd), _fake(), _fake(), 1 << 30, None)
+        assert rc == 1, (m.hash_levels, m.hash_feats, m.hash_log2_T, m.hash_base, m.hash_growth, m.prec)
+        assert b"hash" in L.inrct_last_error()

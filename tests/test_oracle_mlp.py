@@ -59,9 +59,13 @@ def _torch_model(arch, theta, X):
 
 def test_layer_sizes_match_workloads():
     want = {"par2d_128_ffn64": 16641, "fan2d_512_siren256": 264193,
-            "cone3d_256_ffn256": 328961, "cone3d_501_ffn512": 525825}
+            "cone3d_256_ffn256": 328961, "cone3d_501_ffn512": 525825,
+            "fan2d_512_hash64": 16 * 2 ** 19 * 2 + (64 * 32 + 64) + (64 * 64 + 64) + 65}
     for name, w in synth.workloads().items():
-        a = O.Arch(w.arch.kind, w.arch.d, w.arch.width, w.arch.n_hidden, w.arch.n_feat)
+        s = w.arch
+        a = O.Arch(s.kind, s.d, s.width, s.n_hidden, s.n_feat, hash_levels=s.hash_levels,
+                   hash_feats=s.hash_feats, hash_log2_T=s.hash_log2_T, hash_base=s.hash_base,
+                   hash_growth=s.hash_growth)
         assert a.p == want[name] == w.arch.p
 
 
