@@ -118,8 +118,9 @@ typedef struct {
  * interpolation of the vertices' entries; the MLP input is the concatenation
  * over levels (level-major), followed by n_hidden Linear + ReLU layers and
  * Linear(width, 1).  theta then begins with the tables, FP32
- * [level][entry][feature], before the layers.  The table gradient is a
- * scatter-add with FP64 atomics, so its last bits may differ between runs.
+ * [level][entry][feature], before the layers, and must be 8-byte aligned
+ * (INRCT_ERR_INVALID_ARG otherwise).  The table gradient is a scatter-add
+ * with FP64 atomics, so its last bits may differ between runs.
  */
 typedef struct {
   int kind;    /* INRCT_FFN_RELU, INRCT_SIREN or INRCT_HASH */

@@ -98,14 +98,24 @@ template <int D>
 __device__ __forceinline__ void hash_vertices(const NetDev& n, int l, const int* k, uint32_t (&ent)[1 << D],
                                               float (&w)[1 << D]) {
   const uint32_t Nl = (uint32_t)n.hres[l];
-  const int64_t twoN = 2 * (int64_t)n.N;
+  const uint32_t twoN = 2u * (uint32_t)n.N;
   uint32_t c0[D];
   float fr[D];
+  // (2k + 1) N_l < 2N N_l: 32-bit division when that product fits, else 64-bit
+  const bool narrow = (uint64_t)twoN * Nl <= 0xFFFFFFFFull;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const int64_t num = (2 * (int64_t)k[a] + 1) * (int64_t)Nl;
-    c0[a] = (uint32_t)(num / twoN);
-    fr[a] = __fdiv_rn((float)(num % twoN), (float)twoN);
+    uint32_t rem;
+    if (narrow) {
+      const uint32_t num = (2u * (uint32_t)k[a] + 1u) * Nl;
+      c0[a] = num / twoN;
+      rem = num - c0[a] * twoN;
+    } else {
+      const uint64_t num = (2ull * (uint32_t)k[a] + 1ull) * Nl;
+      c0[a] = (uint32_t)(num / twoN);
+      rem = (uint32_t)(num - (uint64_t)c0[a] * twoN);
+    }
+    fr[a] = __fdiv_rn((float)rem, (float)twoN);
   }
   const bool dense = (n.hdense >> l) & 1u;
   const uint32_t mask = (1u << n.hlog2T) - 1u;
@@ -136,6 +146,20 @@ __device__ __forceinline__ void hash_gather(const NetDev& n, const float* __rest
   float w[1 << D];
   hash_vertices<D>(n, l, k, ent, w);
   const float* tab = theta + ((int64_t)l << n.hlog2T) * n.hF;
+  if (n.hF == 2) {
+    // both features of a vertex in one 8-byte load (theta is 256-byte aligned and every
+    // table and entry offset is even)
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int v = 0; v < (1 << D); ++v) {
+      const float2 e = __ldg(reinterpret_cast<const float2*>(tab) + ent[v]);
+      a0 = fmaf(w[v], e.x, a0);
+      a1 = fmaf(w[v], e.y, a1);
+    }
+    out[0] = a0;
+    out[1] = a1;
+    return;
+  }
   for (int f = 0; f < n.hF; ++f) {
     float a = 0.f;
 #pragma unroll
@@ -170,10 +194,11 @@ constexpr int TP = 16;  // points per block
 // Forward at npts points (grid order when idx == NULL).  Optional outputs:
 // out_f[q] = f(x_q); E[q][K0] = layer-1 input; Z[l][q][W] = pre-activations.
 __global__ void __launch_bounds__(256)
-    simt_fwd_kernel(NetDev net, LayerOffs lo, const float* __restrict__ theta,
+    simt_fwd_kernel(const __grid_constant__ NetDev net, const __grid_constant__ LayerOffs lo,
+                    const float* __restrict__ theta,
                     const float* __restrict__ Wt, int64_t npts, const int32_t* __restrict__ idx,
                     float* __restrict__ out_f, float* __restrict__ E, float* __restrict__ Z) {
-  extern __shared__ float sh[];
+  extern __shared__ __align__(16) float sh[];
   __shared__ float xs[TP][3];
   __shared__ int ks[TP][3];
   __shared__ float red[TP][8];
@@ -234,7 +259,23 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int p = 0; p < TP; ++p) acc[p] = bias;
     const float* wt = Wt + lo.Wt[l];
-    for (int k = 0; k < K; ++k) {
+    int k = 0;
+    if ((ld_in & 3) == 0) {
+      // four inputs per 16-byte shared load (a broadcast: every lane reads the same row)
+      for (; k + 4 <= K; k += 4) {
+        const float w0 = __ldg(wt + (int64_t)k * W + t), w1 = __ldg(wt + (int64_t)(k + 1) * W + t);
+        const float w2 = __ldg(wt + (int64_t)(k + 2) * W + t), w3 = __ldg(wt + (int64_t)(k + 3) * W + t);
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+          const float4 x = *reinterpret_cast<const float4*>(in + p * ld_in + k);
+          acc[p] = fmaf(x.x, w0, acc[p]);
+          acc[p] = fmaf(x.y, w1, acc[p]);
+          acc[p] = fmaf(x.z, w2, acc[p]);
+          acc[p] = fmaf(x.w, w3, acc[p]);
+        }
+      }
+    }
+    for (; k < K; ++k) {
       const float w = __ldg(wt + (int64_t)k * W + t);
 #pragma unroll
       for (int p = 0; p < TP; ++p) acc[p] = fmaf(in[p * ld_in + k], w, acc[p]);
@@ -274,12 +315,14 @@ __global__ void __launch_bounds__(256)
 // Backward chain at the chunk: delta_out = scale v_i, delta_{L-1} = delta_out w_out
 // sigma'(z_{L-1}), delta_{l-1} = (W_l^T delta_l) sigma'(z_{l-1}).
 __global__ void __launch_bounds__(256)
-    simt_bwd_kernel(NetDev net, LayerOffs lo, const float* __restrict__ theta, int64_t npts,
+    simt_bwd_kernel(const __grid_constant__ NetDev net, const __grid_constant__ LayerOffs lo,
+                    const float* __restrict__ theta, int64_t npts,
                     const int32_t* __restrict__ idx, const float* __restrict__ v, float scale,
                     const float* __restrict__ Z, float* __restrict__ Dl, float* __restrict__ dout,
                     double* __restrict__ gtab) {
-  extern __shared__ float dsh[];  // [TP][W]
+  extern __shared__ __align__(16) float dsh[];  // [TP][W]
   __shared__ float dsc[TP];
+  __shared__ int ksh[TP][3];  // per-axis grid indices (hash encoding)
   const int W = net.W, L = net.L;
   const int t = threadIdx.x;
   const int64_t p0 = (int64_t)blockIdx.x * TP;
@@ -290,6 +333,11 @@ __global__ void __launch_bounds__(256)
       const int64_t i = idx ? (int64_t)idx[q] : q;
       s = (i >= 0 && i < grid_size(net)) ? scale * v[i] : 0.f;
       dout[q] = s;
+      if (gtab && s != 0.f) {
+        ksh[t][0] = (int)(i % net.N);
+        ksh[t][1] = (int)((i / net.N) % net.N);
+        ksh[t][2] = net.d == 3 ? (int)(i / ((int64_t)net.N * net.N)) : 0;
+      }
     }
     dsc[t] = s;
   }
@@ -311,10 +359,17 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int p = 0; p < TP; ++p) acc[p] = 0.f;
     const float* Wl = theta + lo.W[l];  // [W][W], row o holds the weights of output o
-    for (int o = 0; o < W; ++o) {
-      const float w = __ldg(Wl + (int64_t)o * W + t);
+    for (int o = 0; o < W; o += 4) {    // W is a multiple of 64
+      const float w0 = __ldg(Wl + (int64_t)o * W + t), w1 = __ldg(Wl + (int64_t)(o + 1) * W + t);
+      const float w2 = __ldg(Wl + (int64_t)(o + 2) * W + t), w3 = __ldg(Wl + (int64_t)(o + 3) * W + t);
 #pragma unroll
-      for (int p = 0; p < TP; ++p) acc[p] = fmaf(dsh[p * W + o], w, acc[p]);
+      for (int p = 0; p < TP; ++p) {
+        const float4 x = *reinterpret_cast<const float4*>(dsh + p * W + o);
+        acc[p] = fmaf(x.x, w0, acc[p]);
+        acc[p] = fmaf(x.y, w1, acc[p]);
+        acc[p] = fmaf(x.z, w2, acc[p]);
+        acc[p] = fmaf(x.w, w3, acc[p]);
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -344,14 +399,10 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     for (int e = t; e < TP * net.hL; e += W) {
       const int p = e / net.hL, l = e % net.hL;
-      const int64_t q = p0 + p;
-      if (q >= npts || dsc[p] == 0.f) continue;  // no contribution
-      const int64_t i = idx ? (int64_t)idx[q] : q;
-      const int k[3] = {(int)(i % net.N), (int)((i / net.N) % net.N),
-                        net.d == 3 ? (int)(i / ((int64_t)net.N * net.N)) : 0};
+      if (p0 + p >= npts || dsc[p] == 0.f) continue;  // no contribution (ksh unset)
       const float* g = gsh + p * K0 + l * net.hF;
-      if (net.d == 3) hash_scatter<3>(net, gtab, l, k, g);
-      else hash_scatter<2>(net, gtab, l, k, g);
+      if (net.d == 3) hash_scatter<3>(net, gtab, l, ksh[p], g);
+      else hash_scatter<2>(net, gtab, l, ksh[p], g);
     }
   }
 }
@@ -359,51 +410,70 @@ __global__ void __launch_bounds__(256)
 // C[o][k] (k <= K; column K is the bias) partial sums over one split of points:
 //   C[o][k] = sum_q X[q][o] * Y'(q, k),  Y'(q, k) = f(Y[q][k]) for k < K, 1 for k = K,
 // with f the identity (ymode 0), ReLU (1) or sin(omega0 .) (2).
-constexpr int GT = 64, GK = 16;
+constexpr int GT = 64, GK = 32;
+constexpr int kDwLoads = GK * GT / 256;  // slab elements of X (and of Y) per thread
+
+// One slab of GK points: X[q][o] and Y'(q, k) of this tile into registers (zero outside).
+__device__ __forceinline__ void dw_load_slab(const float* __restrict__ X, int O, const float* __restrict__ Y,
+                                             int K, int ymode, float omega0, int to, int tk, int64_t qb,
+                                             int64_t q1, float (&xr)[kDwLoads], float (&yr)[kDwLoads]) {
+#pragma unroll
+  for (int r = 0; r < kDwLoads; ++r) {
+    const int e = threadIdx.x + 256 * r;
+    const int qq = e / GT, c = e % GT;
+    const int64_t q = qb + qq;
+    const int o = to * GT + c, k = tk * GT + c;
+    float xv = 0.f, yv = 0.f;
+    if (q < q1) {
+      if (o < O) xv = __ldg(X + q * O + o);
+      if (k < K) {
+        yv = __ldg(Y + q * K + k);
+        if (ymode == 1) yv = fmaxf(yv, 0.f);
+        else if (ymode == 2) yv = sinf(omega0 * yv);
+      } else if (k == K) {
+        yv = 1.f;
+      }
+    }
+    xr[r] = xv;
+    yr[r] = yv;
+  }
+}
+
+// The slabs are double-buffered: while the FMAs of slab s read shared memory, the
+// loads of slab s + 1 are in flight into registers; one barrier per slab.
 __global__ void __launch_bounds__(256)
     simt_dw_kernel(const float* __restrict__ X, int O, const float* __restrict__ Y, int K, int ymode,
                    float omega0, int64_t npts, int64_t per_split, float* __restrict__ part) {
-  __shared__ float xs[GK][GT + 1];
-  __shared__ float ys[GK][GT + 1];
+  __shared__ __align__(16) float xs[2][GK][GT];
+  __shared__ __align__(16) float ys[2][GK][GT];
   const int to = blockIdx.x, tk = blockIdx.y, sp = blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t q0 = (int64_t)sp * per_split;
   const int64_t q1 = min(npts, q0 + per_split);
   float acc[4][4] = {};
+  float xr[kDwLoads], yr[kDwLoads];
+  dw_load_slab(X, O, Y, K, ymode, omega0, to, tk, q0, q1, xr, yr);
+  int buf = 0;
   for (int64_t qb = q0; qb < q1; qb += GK) {
-    for (int e = threadIdx.x; e < GK * GT; e += 256) {
-      const int qq = e / GT, c = e % GT;
-      const int64_t q = qb + qq;
-      const int o = to * GT + c, k = tk * GT + c;
-      float xv = 0.f, yv = 0.f;
-      if (q < q1) {
-        if (o < O) xv = X[q * O + o];
-        if (k < K) {
-          yv = Y[q * K + k];
-          if (ymode == 1) yv = fmaxf(yv, 0.f);
-          else if (ymode == 2) yv = sinf(omega0 * yv);
-        } else if (k == K) {
-          yv = 1.f;
-        }
-      }
-      xs[qq][c] = xv;
-      ys[qq][c] = yv;
+#pragma unroll
+    for (int r = 0; r < kDwLoads; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      xs[buf][e / GT][e % GT] = xr[r];
+      ys[buf][e / GT][e % GT] = yr[r];
     }
     __syncthreads();
-#pragma unroll
+    if (qb + GK < q1) dw_load_slab(X, O, Y, K, ymode, omega0, to, tk, qb + GK, q1, xr, yr);
+#pragma unroll 8
     for (int qq = 0; qq < GK; ++qq) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = xs[qq][ty * 4 + i];
-        b[i] = ys[qq][tx * 4 + i];
-      }
+      const float4 a = *reinterpret_cast<const float4*>(&xs[buf][qq][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&ys[buf][qq][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    __syncthreads();
+    buf ^= 1;  // the next slab goes to the other buffer: no barrier needed before its stores
   }
   const int ld = K + 1;
 #pragma unroll
@@ -416,18 +486,33 @@ __global__ void __launch_bounds__(256)
 }
 
 // grad[offW + o*K + k] (+)= sum_s part[s][o][k];  grad[offb + o] (+)= sum_s part[s][o][K].
-__global__ void reduce_layer_kernel(const float* __restrict__ part, int S, int O, int K,
-                                    int64_t offW, int64_t offb, double mult, int accumulate,
-                                    double* __restrict__ grad) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// A block takes 32 consecutive entries; its 32 warps sum interleaved subsets of the
+// splits (coalesced 128-byte rows, independent loads in flight), then warp 0 adds the
+// 32 partial sums in warp order, so the result does not depend on timing.
+constexpr int kRedWarps = 32;
+__global__ void __launch_bounds__(32 * kRedWarps)
+    reduce_layer_kernel(const float* __restrict__ part, int S, int O, int K, int64_t offW, int64_t offb,
+                        double mult, int accumulate, double* __restrict__ grad) {
+  __shared__ double red[kRedWarps][32];
   const int ld = K + 1;
-  if (e >= (int64_t)O * ld) return;
+  const int64_t ent = (int64_t)O * ld;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int q = 0; q < S; ++q) s += (double)part[(int64_t)q * O * ld + e];
-  s *= mult;
+  if (e < ent) {
+#pragma unroll 4
+    for (int q = warp; q < S; q += kRedWarps) s += (double)part[(int64_t)q * ent + e];
+  }
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp != 0 || e >= ent) return;
+  double tot = 0.0;
+#pragma unroll
+  for (int w = 0; w < kRedWarps; ++w) tot += red[w][lane];
+  tot *= mult;
   const int o = (int)(e / ld), k = (int)(e % ld);
   const int64_t dst = k < K ? offW + (int64_t)o * K + k : offb + o;
-  grad[dst] = accumulate ? grad[dst] + s : s;
+  grad[dst] = accumulate ? grad[dst] + tot : tot;
 }
 
 struct VjpWs {
@@ -437,14 +522,23 @@ struct VjpWs {
   float* D;
   float* dout;
   float* part;
-  int S;
 };
 
-int splits_for(int64_t npts) {
-  int S = (int)((npts + 4095) / 4096);
-  if (S > 16) S = 16;
-  if (S < 1) S = 1;
-  return S;
+// Point splits of one layer's dW: enough (tile, split) blocks for about four per SM of
+// a 152-SM part, at least two slabs of points per split, at most kMaxDwSplits partials
+// per entry.
+// A fixed count (not the live SM count) keeps the workspace size a function of the
+// network and the chunk alone.
+constexpr int kMaxDwSplits = 1024;
+constexpr int kDwTargetBlocks = 4 * 152;
+int64_t dw_tiles(const Net& n, int l) {
+  return (int64_t)ceil_div(n.out_dim[l], GT) * ceil_div(n.in_dim[l] + 1, GT);
+}
+int splits_for(const Net& n, int l, int64_t npts) {
+  int64_t S = ceil_div(kDwTargetBlocks, dw_tiles(n, l));
+  S = std::min<int64_t>(S, ceil_div(npts, 2 * GK));
+  S = std::min<int64_t>(S, kMaxDwSplits);
+  return (int)std::max<int64_t>(S, 1);
 }
 
 size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, VjpWs* out, bool* ok) {
@@ -456,10 +550,11 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, VjpWs* out,
   w.Z = c.take<float>(chunk * n.L * n.W);
   w.D = c.take<float>(chunk * n.L * n.W);
   w.dout = c.take<float>(chunk);
-  w.S = splits_for(chunk);
+  // partials of the largest layer at its split count (split counts grow with the chunk)
   int64_t pe = 0;
-  for (int l = 0; l <= n.L; ++l) pe = std::max<int64_t>(pe, (int64_t)n.out_dim[l] * (n.in_dim[l] + 1));
-  w.part = c.take<float>(pe * w.S);
+  for (int l = 0; l <= n.L; ++l)
+    pe = std::max<int64_t>(pe, (int64_t)n.out_dim[l] * (n.in_dim[l] + 1) * splits_for(n, l, chunk));
+  w.part = c.take<float>(pe);
   if (out) *out = w;
   if (ok) *ok = c.ok;
   return c.off + 256;
@@ -501,8 +596,18 @@ size_t simt_eval_ws_bytes(const Net& n) {
   return align_up(sizeof(float) * wt_layout(n, &lo), 256) + 256;
 }
 
+// The hash gather reads both features of a vertex in one 8-byte load.
+int check_theta_alignment(const Net& n, const float* theta, const char* who) {
+  if (n.kind == INRCT_HASH && (reinterpret_cast<uintptr_t>(theta) & 7) != 0) {
+    set_error("%s: theta must be 8-byte aligned for the hash-encoded INR", who);
+    return INRCT_ERR_INVALID_ARG;
+  }
+  return INRCT_OK;
+}
+
 int simt_eval(const Net& n, const float* theta, int N, int64_t npts, float* image, void* ws,
               size_t ws_bytes, cudaStream_t st) {
+  INRCT_TRY(check_theta_alignment(n, theta, "inr_eval_grid"));
   const size_t need = simt_eval_ws_bytes(n);
   if (!ws || ws_bytes < need) {
     set_error("inr_eval_grid (fp32): workspace of %zu bytes too small (need %zu)", ws_bytes, need);
@@ -528,6 +633,7 @@ size_t simt_vjp_ws_bytes(const Net& n, int64_t n_idx) {
 int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t n_idx,
              const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
              size_t ws_bytes, cudaStream_t st) {
+  INRCT_TRY(check_theta_alignment(n, theta, "inr_weighted_vjp"));
   const int64_t chunk = n_idx < kVjpChunk ? n_idx : kVjpChunk;
   VjpWs w;
   bool ok;
@@ -558,10 +664,10 @@ int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_
         nd, lo, theta, np, id, v, (float)scale, w.Z, w.D, w.dout, n.n_table > 0 ? grad_f64 : nullptr);
     INRCT_CHECK_LAUNCH("simt vjp backward");
     if (c0 == 0) prof_mark(kMarkVjpKernelDone, st);
-    const int S = splits_for(np);
-    const int64_t per = (np + S - 1) / S;
     for (int l = 0; l <= n.L; ++l) {
       const int O = n.out_dim[l], K = n.in_dim[l];
+      const int S = splits_for(n, l, np);
+      const int64_t per = (np + S - 1) / S;
       const float* X = l < n.L ? w.D + (int64_t)l * np * n.W : w.dout;
       const float* Y;
       int ymode;
@@ -576,7 +682,7 @@ int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_
       simt_dw_kernel<<<grd, 256, 0, st>>>(X, O, Y, K, ymode, n.omega0, np, per, w.part);
       INRCT_CHECK_LAUNCH("simt dW");
       const int64_t ent = (int64_t)O * (K + 1);
-      reduce_layer_kernel<<<ceil_div(ent, 256), 256, 0, st>>>(w.part, S, O, K, n.offW[l], n.offb[l],
+      reduce_layer_kernel<<<ceil_div(ent, 32), 32 * kRedWarps, 0, st>>>(w.part, S, O, K, n.offW[l], n.offb[l],
                                                               1.0, c0 > 0, grad_f64);
       INRCT_CHECK_LAUNCH("simt reduce");
     }
