@@ -33,6 +33,7 @@ struct NetDev {
   const float* B;
   int hL, hF, hlog2T;
   unsigned hdense;  // bit l: level l is looked up densely
+  float rcp2N;      // 1 / (2N) rounded to FP32
   int hres[kMaxHashLevels];
 };
 
@@ -55,6 +56,7 @@ NetDev dev_of(const Net& n, int N) {
   d.hF = n.hF;
   d.hlog2T = n.hlog2T;
   d.hdense = 0;
+  d.rcp2N = 1.0f / (2.0f * (float)N);
   for (int l = 0; l < kMaxHashLevels; ++l) {
     d.hres[l] = l < n.hL ? n.hres[l] : 0;
     if (l < n.hL) {
@@ -91,9 +93,12 @@ __device__ __forceinline__ float dact(const NetDev& n, float z) {
 
 // Level l of the hash encoding at the grid point with per-axis indices k[0..D): the
 // table entries of its 2^D surrounding vertices and their multilinear weights.  The
-// level coordinate (2k + 1) N_l / (2N) is split exactly in integers; its fraction is
-// one correctly rounded FP32 division of integers below 2^14.  D is a template
-// parameter so that every loop unrolls and the vertex state stays in registers.
+// level coordinate (2k + 1) N_l / (2N) is split exactly into its integer part c0 and
+// remainder r: while the numerator stays below 2^24 (exact in FP32) the quotient from
+// the FP32 reciprocal is within one of the floor, and one integer correction makes it
+// exact; larger numerators divide in 32 or 64-bit integers.  The fraction is r / (2N)
+// in FP32 (exact when 2N is a power of two).  D is a template parameter so that every
+// loop unrolls and the vertex state stays in registers.
 template <int D>
 __device__ __forceinline__ void hash_vertices(const NetDev& n, int l, const int* k, uint32_t (&ent)[1 << D],
                                               float (&w)[1 << D]) {
@@ -101,12 +106,26 @@ __device__ __forceinline__ void hash_vertices(const NetDev& n, int l, const int*
   const uint32_t twoN = 2u * (uint32_t)n.N;
   uint32_t c0[D];
   float fr[D];
-  // (2k + 1) N_l < 2N N_l: 32-bit division when that product fits, else 64-bit
-  const bool narrow = (uint64_t)twoN * Nl <= 0xFFFFFFFFull;
+  // (2k + 1) N_l < 2N N_l
+  const uint64_t bound = (uint64_t)twoN * Nl;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     uint32_t rem;
-    if (narrow) {
+    if (bound <= (1u << 24)) {
+      // |num * fl(1/2N) - num / 2N| < 2 num 2^-24 / 2N < 1: truncation is off by at most one
+      const uint32_t num = (2u * (uint32_t)k[a] + 1u) * Nl;
+      uint32_t q = (uint32_t)((float)num * n.rcp2N);
+      int r = (int)num - (int)(q * twoN);
+      if (r < 0) {
+        q -= 1;
+        r += (int)twoN;
+      } else if (r >= (int)twoN) {
+        q += 1;
+        r -= (int)twoN;
+      }
+      c0[a] = q;
+      rem = (uint32_t)r;
+    } else if (bound <= 0xFFFFFFFFull) {
       const uint32_t num = (2u * (uint32_t)k[a] + 1u) * Nl;
       c0[a] = num / twoN;
       rem = num - c0[a] * twoN;
@@ -115,7 +134,7 @@ __device__ __forceinline__ void hash_vertices(const NetDev& n, int l, const int*
       c0[a] = (uint32_t)(num / twoN);
       rem = (uint32_t)(num - (uint64_t)c0[a] * twoN);
     }
-    fr[a] = __fdiv_rn((float)rem, (float)twoN);
+    fr[a] = (float)rem * n.rcp2N;
   }
   const bool dense = (n.hdense >> l) & 1u;
   const uint32_t mask = (1u << n.hlog2T) - 1u;
@@ -168,17 +187,52 @@ __device__ __forceinline__ void hash_gather(const NetDev& n, const float* __rest
   }
 }
 
-// Table gradient of level l at the point: entry ent_v, feature f receives w_v g[f].
+// Table gradient of level l at one point per lane: entry ent_v, feature f receives
+// w_v g[f].  Called by all 32 lanes of a warp together (ok = false: the lane adds
+// nothing).  Runs of consecutive lanes whose vertex is the same (level, entry) are summed
+// by a segmented scan (5 shuffle steps, no divergence) and the last lane of each run
+// issues the one atomic: neighbouring points of a sorted index set share vertices at
+// coarse levels.  A key that recurs after another key simply starts a new run, so the
+// result holds for any order of the points.
 template <int D>
-__device__ __forceinline__ void hash_scatter(const NetDev& n, double* __restrict__ gtab, int l, const int* k,
-                                             const float* g) {
+__device__ __forceinline__ void hash_scatter_warp(const NetDev& n, double* __restrict__ gtab, int l, const int* k,
+                                                  const float* g, bool ok) {
+  const unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   uint32_t ent[1 << D];
   float w[1 << D];
-  hash_vertices<D>(n, l, k, ent, w);
-  double* gl = gtab + ((int64_t)l << n.hlog2T) * n.hF;
+  if (ok) hash_vertices<D>(n, l, k, ent, w);
+  double* gl = gtab + ((int64_t)(ok ? l : 0) << n.hlog2T) * n.hF;
 #pragma unroll
-  for (int v = 0; v < (1 << D); ++v)
-    for (int f = 0; f < n.hF; ++f) atomicAdd(gl + (int64_t)ent[v] * n.hF + f, (double)w[v] * (double)g[f]);
+  for (int v = 0; v < (1 << D); ++v) {
+    const unsigned long long key = ok ? ((unsigned long long)l << 32) | ent[v] : ~0ull - lane;
+    const unsigned long long kprev = __shfl_up_sync(kFull, key, 1);
+    const bool head = lane == 0 || kprev != key;
+    const bool next_head = __shfl_down_sync(kFull, (int)head, 1) != 0;  // lane 31: its own
+    const bool tail = lane == 31 || next_head;
+    // which of the five steps add the value of lane - 2^s (segmented scan: a lane stops
+    // taking once the run's head has reached it)
+    unsigned take = 0;
+    bool f = head;
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+      const int off = 1 << st;
+      const bool fu = __shfl_up_sync(kFull, (int)f, off) != 0;
+      if (lane >= off && !f) {
+        take |= 1u << st;
+        f = fu;
+      }
+    }
+    for (int ff = 0; ff < n.hF; ++ff) {
+      float val = ok ? w[v] * g[ff] : 0.f;
+#pragma unroll
+      for (int st = 0; st < 5; ++st) {
+        const float up = __shfl_up_sync(kFull, val, 1 << st);
+        if (take & (1u << st)) val += up;
+      }
+      if (ok && tail) atomicAdd(gl + (int64_t)ent[v] * n.hF + ff, (double)val);
+    }
+  }
 }
 
 __global__ void transpose_w_kernel(const float* __restrict__ theta, int64_t offW, int out, int in,
@@ -314,8 +368,9 @@ __global__ void __launch_bounds__(256)
 
 // Backward chain at the chunk: delta_out = scale v_i, delta_{L-1} = delta_out w_out
 // sigma'(z_{L-1}), delta_{l-1} = (W_l^T delta_l) sigma'(z_{l-1}).
-__global__ void __launch_bounds__(256)
-    simt_bwd_kernel(const __grid_constant__ NetDev net, const __grid_constant__ LayerOffs lo,
+// No launch bound: with one, ptxas caps this kernel's registers and spills (it needs
+// about 72; any register count fits the largest block, 256 threads).
+__global__ void simt_bwd_kernel(const __grid_constant__ NetDev net, const __grid_constant__ LayerOffs lo,
                     const float* __restrict__ theta, int64_t npts,
                     const int32_t* __restrict__ idx, const float* __restrict__ v, float scale,
                     const float* __restrict__ Z, float* __restrict__ Dl, float* __restrict__ dout,
@@ -385,24 +440,42 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
   }
   if (gtab) {
-    // hash tables: g = W_1^T delta_1 is the gradient of the layer-1 input; each vertex
-    // entry of each level receives its weight times the level's slice of g
+    // hash tables: g = W_1^T delta_1 is the gradient of the layer-1 input (thread j < K0
+    // computes column j for the block's points); each vertex entry of each level receives
+    // its weight times the level's slice of g
     __shared__ float gsh[TP * kMaxHashInputs];
     const int K0 = net.K0;
-    const float* W0 = theta + lo.W[0];  // [W][K0]
-    for (int e = t; e < TP * K0; e += W) {
-      const int p = e / K0, j = e % K0;
-      float a = 0.f;
-      for (int o = 0; o < W; ++o) a = fmaf(dsh[p * W + o], __ldg(W0 + (int64_t)o * K0 + j), a);
-      gsh[e] = a;
+    if (t < K0) {  // K0 <= 64 <= W
+      const float* W0 = theta + lo.W[0];  // [W][K0]
+      float acc[TP];
+#pragma unroll
+      for (int p = 0; p < TP; ++p) acc[p] = 0.f;
+      for (int o = 0; o < W; o += 4) {
+        const float w0 = __ldg(W0 + (int64_t)o * K0 + t), w1 = __ldg(W0 + (int64_t)(o + 1) * K0 + t);
+        const float w2 = __ldg(W0 + (int64_t)(o + 2) * K0 + t), w3 = __ldg(W0 + (int64_t)(o + 3) * K0 + t);
+#pragma unroll
+        for (int p = 0; p < TP; ++p) {
+          const float4 x = *reinterpret_cast<const float4*>(dsh + p * W + o);
+          acc[p] = fmaf(x.x, w0, acc[p]);
+          acc[p] = fmaf(x.y, w1, acc[p]);
+          acc[p] = fmaf(x.z, w2, acc[p]);
+          acc[p] = fmaf(x.w, w3, acc[p]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < TP; ++p) gsh[p * K0 + t] = acc[p];
     }
     __syncthreads();
-    for (int e = t; e < TP * net.hL; e += W) {
-      const int p = e / net.hL, l = e % net.hL;
-      if (p0 + p >= npts || dsc[p] == 0.f) continue;  // no contribution (ksh unset)
-      const float* g = gsh + p * K0 + l * net.hF;
-      if (net.d == 3) hash_scatter<3>(net, gtab, l, ksh[p], g);
-      else hash_scatter<2>(net, gtab, l, ksh[p], g);
+    // level-major items (a warp holds TP points of one level, two levels per warp); the
+    // item count is rounded up to whole warps so that every lane of a warp takes part
+    const int n_items = TP * net.hL;
+    const int n_round = (n_items + 31) & ~31;
+    for (int e = t; e < n_round; e += W) {  // W is a multiple of 32: warps stay whole
+      const int l = e / TP, p = e % TP;
+      const bool ok = e < n_items && p0 + p < npts && dsc[p] != 0.f;  // else ksh[p] is unset
+      const float* g = gsh + p * K0 + (ok ? l : 0) * net.hF;
+      if (net.d == 3) hash_scatter_warp<3>(net, gtab, l, ksh[p], g, ok);
+      else hash_scatter_warp<2>(net, gtab, l, ksh[p], g, ok);
     }
   }
 }
@@ -430,8 +503,6 @@ __device__ __forceinline__ void dw_load_slab(const float* __restrict__ X, int O,
         yv = __ldg(Y + q * K + k);
         if (ymode == 1) yv = fmaxf(yv, 0.f);
         else if (ymode == 2) yv = sinf(omega0 * yv);
-      } else if (k == K) {
-        yv = 1.f;
       }
     }
     xr[r] = xv;
@@ -440,7 +511,9 @@ __device__ __forceinline__ void dw_load_slab(const float* __restrict__ X, int O,
 }
 
 // The slabs are double-buffered: while the FMAs of slab s read shared memory, the
-// loads of slab s + 1 are in flight into registers; one barrier per slab.
+// loads of slab s + 1 are in flight into registers; one barrier per slab.  The bias
+// column (k = K) is a running sum of X kept by the blocks of k-tile 0, so K = 64 needs
+// one k-tile, not two.
 __global__ void __launch_bounds__(256)
     simt_dw_kernel(const float* __restrict__ X, int O, const float* __restrict__ Y, int K, int ymode,
                    float omega0, int64_t npts, int64_t per_split, float* __restrict__ part) {
@@ -451,6 +524,7 @@ __global__ void __launch_bounds__(256)
   const int64_t q0 = (int64_t)sp * per_split;
   const int64_t q1 = min(npts, q0 + per_split);
   float acc[4][4] = {};
+  float accb[4] = {};
   float xr[kDwLoads], yr[kDwLoads];
   dw_load_slab(X, O, Y, K, ymode, omega0, to, tk, q0, q1, xr, yr);
   int buf = 0;
@@ -472,6 +546,10 @@ __global__ void __launch_bounds__(256)
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      if (tk == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) accb[i] += av[i];
+      }
     }
     buf ^= 1;  // the next slab goes to the other buffer: no barrier needed before its stores
   }
@@ -481,14 +559,63 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int o = to * GT + ty * 4 + i, k = tk * GT + tx * 4 + j;
-      if (o < O && k <= K) part[((int64_t)sp * O + o) * ld + k] = acc[i][j];
+      if (o < O && k < K) part[((int64_t)sp * O + o) * ld + k] = acc[i][j];
     }
+  if (tk == 0 && tx == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int o = to * GT + ty * 4 + i;
+      if (o < O) part[((int64_t)sp * O + o) * ld + K] = accb[i];
+    }
+  }
+}
+
+// dW of a one-row layer (the scalar output): part[s][0][k] = sum_q X[q] Y'(q, k) for
+// k < K and part[s][0][K] = sum_q X[q].  Thread k streams the split's points: the Y
+// rows are coalesced across threads, X[q] is one broadcast.
+constexpr int kRowMinPoints = 32;
+__global__ void __launch_bounds__(288)
+    simt_dw_row_kernel(const float* __restrict__ X, const float* __restrict__ Y, int K, int ymode, float omega0,
+                       int64_t npts, int64_t per_split, float* __restrict__ part) {
+  const int k = threadIdx.x, sp = blockIdx.x;
+  if (k > K) return;
+  const int64_t q0 = (int64_t)sp * per_split;
+  const int64_t q1 = min(npts, q0 + per_split);
+  float acc0 = 0.f, acc1 = 0.f;
+  int64_t q = q0;
+  for (; q + 2 <= q1; q += 2) {
+    float y0 = 1.f, y1 = 1.f;
+    if (k < K) {
+      y0 = __ldg(Y + q * K + k);
+      y1 = __ldg(Y + (q + 1) * K + k);
+      if (ymode == 1) {
+        y0 = fmaxf(y0, 0.f);
+        y1 = fmaxf(y1, 0.f);
+      } else if (ymode == 2) {
+        y0 = sinf(omega0 * y0);
+        y1 = sinf(omega0 * y1);
+      }
+    }
+    acc0 = fmaf(__ldg(X + q), y0, acc0);
+    acc1 = fmaf(__ldg(X + q + 1), y1, acc1);
+  }
+  if (q < q1) {
+    float y = 1.f;
+    if (k < K) {
+      y = __ldg(Y + q * K + k);
+      if (ymode == 1) y = fmaxf(y, 0.f);
+      else if (ymode == 2) y = sinf(omega0 * y);
+    }
+    acc0 = fmaf(__ldg(X + q), y, acc0);
+  }
+  part[(int64_t)sp * (K + 1) + k] = acc0 + acc1;
 }
 
 // grad[offW + o*K + k] (+)= sum_s part[s][o][k];  grad[offb + o] (+)= sum_s part[s][o][K].
 // A block takes 32 consecutive entries; its 32 warps sum interleaved subsets of the
-// splits (coalesced 128-byte rows, independent loads in flight), then warp 0 adds the
-// 32 partial sums in warp order, so the result does not depend on timing.
+// splits (coalesced 128-byte rows, independent loads in flight) in FP32, then warp 0
+// adds the 32 warp sums in FP64 in warp order, so the result does not depend on timing.
+// (FP64 arithmetic is slow on this part: one FP64 add per partial would dominate.)
 constexpr int kRedWarps = 32;
 __global__ void __launch_bounds__(32 * kRedWarps)
     reduce_layer_kernel(const float* __restrict__ part, int S, int O, int K, int64_t offW, int64_t offb,
@@ -498,12 +625,16 @@ __global__ void __launch_bounds__(32 * kRedWarps)
   const int64_t ent = (int64_t)O * ld;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * 32 + lane;
-  double s = 0.0;
+  float s0 = 0.f, s1 = 0.f;
   if (e < ent) {
-#pragma unroll 4
-    for (int q = warp; q < S; q += kRedWarps) s += (double)part[(int64_t)q * ent + e];
+    int q = warp;
+    for (; q + kRedWarps < S; q += 2 * kRedWarps) {
+      s0 += part[(int64_t)q * ent + e];
+      s1 += part[(int64_t)(q + kRedWarps) * ent + e];
+    }
+    if (q < S) s0 += part[(int64_t)q * ent + e];
   }
-  red[warp][lane] = s;
+  red[warp][lane] = (double)s0 + (double)s1;
   __syncthreads();
   if (warp != 0 || e >= ent) return;
   double tot = 0.0;
@@ -532,11 +663,13 @@ struct VjpWs {
 constexpr int kMaxDwSplits = 1024;
 constexpr int kDwTargetBlocks = 4 * 152;
 int64_t dw_tiles(const Net& n, int l) {
-  return (int64_t)ceil_div(n.out_dim[l], GT) * ceil_div(n.in_dim[l] + 1, GT);
+  return (int64_t)ceil_div(n.out_dim[l], GT) * ceil_div(n.in_dim[l], GT);
 }
+// One-row layers go to simt_dw_row_kernel (one block per split, kRowMinPoints or more each).
 int splits_for(const Net& n, int l, int64_t npts) {
-  int64_t S = ceil_div(kDwTargetBlocks, dw_tiles(n, l));
-  S = std::min<int64_t>(S, ceil_div(npts, 2 * GK));
+  const bool row = n.out_dim[l] == 1;
+  int64_t S = row ? kMaxDwSplits : ceil_div(kDwTargetBlocks, dw_tiles(n, l));
+  S = std::min<int64_t>(S, ceil_div(npts, row ? kRowMinPoints : 2 * GK));
   S = std::min<int64_t>(S, kMaxDwSplits);
   return (int)std::max<int64_t>(S, 1);
 }
@@ -678,8 +811,12 @@ int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_
         Y = w.Z + (int64_t)(l - 1) * np * n.W;
         ymode = n.kind == INRCT_SIREN ? 2 : 1;
       }
-      dim3 grd(ceil_div(O, GT), ceil_div(K + 1, GT), S);
-      simt_dw_kernel<<<grd, 256, 0, st>>>(X, O, Y, K, ymode, n.omega0, np, per, w.part);
+      if (O == 1) {
+        simt_dw_row_kernel<<<S, (K + 1 + 31) / 32 * 32, 0, st>>>(X, Y, K, ymode, n.omega0, np, per, w.part);
+      } else {
+        dim3 grd(ceil_div(O, GT), ceil_div(K, GT), S);
+        simt_dw_kernel<<<grd, 256, 0, st>>>(X, O, Y, K, ymode, n.omega0, np, per, w.part);
+      }
       INRCT_CHECK_LAUNCH("simt dW");
       const int64_t ent = (int64_t)O * (K + 1);
       reduce_layer_kernel<<<ceil_div(ent, 32), 32 * kRedWarps, 0, st>>>(w.part, S, O, K, n.offW[l], n.offb[l],

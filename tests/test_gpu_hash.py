@@ -114,6 +114,27 @@ def test_vjp_over_several_chunks_matches_oracle():
     assert rel(got, want) <= 1e-4
 
 
+@pytest.mark.parametrize("N,levels,growth", [(64, 2, 2.5), (2100, 3, 4.0)], ids=["32bit", "64bit"])
+def test_fine_levels_split_their_coordinates_exactly(N, levels, growth):
+    """Level coordinates (2k + 1) N_l / (2N) whose numerator exceeds 2^24 (and 2^32) are split
+    by the integer paths of the kernel; the VJP (which also carries the forward's layer-1
+    input into dW_1) matches the oracle."""
+    base = 60000 if N == 64 else 65536
+    spec = hash_spec(hash_levels=levels, hash_log2_T=10, hash_base=base, hash_growth=growth)
+    n = N * N
+    oa = oarch(spec)
+    top = O.hash_resolutions(oa)[-1]
+    assert 2 * N * top > (1 << 24) and (N < 1000 or 2 * N * top > (1 << 32))
+    theta = synth.init_theta(spec, 14, table_scale=0.5).astype(np.float32)
+    idx = synth.index_set(n, 800, 15)
+    idx = idx[kink_free(oa, theta, O.grid_coords(2, N, idx), N)].astype(np.int32)
+    v = np.random.default_rng(16).normal(size=n).astype(np.float32)
+    got = inrct.inr_weighted_vjp(inrct.mlp_desc(spec, inrct.FP32), cuda(theta), N, cuda(idx, torch.int32),
+                                 cuda(v), 1.0).cpu().numpy()
+    want = O.vjp(oa, theta.astype(np.float64), O.grid_coords(2, N, idx), v.astype(np.float64)[idx], N=N)
+    assert rel(got, want) <= 1e-4
+
+
 def test_out_of_range_indices_contribute_nothing():
     """Indices outside [0, n) add nothing.  The two lists differ in length, so the dW
     point splits (and the grouping of their FP32 partial sums) may differ: the bar is
