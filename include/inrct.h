@@ -7,8 +7,8 @@
  * (arXiv 2604.09884):
  *
  *   min_theta L(P E{f_theta}, y)                         (Sec. 2, Eq. 1)
- *   z = P E{f_theta},  v = P^T dL/dz                     (Sec. 3; Algorithm 1, steps 1-2)
- *   g = (n/|I|) sum_{i in I} v_i grad_theta f_theta(x_i)  (Sec. 3, Eq. 2; Algorithm 1, steps 3-5)
+ *   z = P E{f_theta},  v = P^T dL/dz                     (Sec. 3; Algorithm 1)
+ *   g = (n/|I|) sum_{i in I} v_i grad_theta f_theta(x_i)  (Sec. 3, Eq. 2; Algorithm 1)
  *
  * Conventions shared by every call
  * --------------------------------
@@ -158,7 +158,7 @@ int64_t inrct_num_rays(const inrct_geom* geom);
 
 /* ------------------------------------------------------------------------ */
 /*
- * project -- z = P x (Sec. 3; Algorithm 1, step 1, "no gradient tracking").
+ * project -- z = P x (Sec. 3; Algorithm 1, evaluated without gradient tracking).
  *   image[n] FP32 in, sino[m] FP32 out (overwritten).
  *   Optional loss epilogue (Sec. 2, LS loss): if y != NULL, also writes
  *   resid[m] = z - y and loss_out[0] = 1/2 sum (z - y)^2 (one FP64 device
@@ -197,7 +197,7 @@ int project_noalloc(const inrct_geom* geom, const inrct_grid* grid, const float*
                     const float* y, float* resid, double* loss_out, cudaStream_t stream);
 
 /*
- * backproject -- v = P^T r (Sec. 3, v = P^T r; Algorithm 1, step 2), the exact
+ * backproject -- v = P^T r (Sec. 3; Algorithm 1), the exact
  * adjoint of project (same interpolation weights), in gather form: every
  * pixel sums its own contributions, so the result is deterministic.
  *   sino[m] FP32 in, image[n] FP32 out (overwritten, not accumulated).

@@ -488,7 +488,7 @@ def evaluate_image(arch: Arch, theta, g: Geometry) -> np.ndarray:
 
 
 def backprojected_residual(arch: Arch, theta, g: Geometry, y):
-    """Algorithm 1, steps 1-2: z = P E{f}, v = P^T dL/dz.  Returns (L, z, r, v)."""
+    """Algorithm 1, its projection and backprojection: z = P E{f}, v = P^T dL/dz.  Returns (L, z, r, v)."""
     x = evaluate_image(arch, theta, g)
     z = project(g, x)
     L, r = ls_loss(z, y)

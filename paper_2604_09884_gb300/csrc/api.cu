@@ -255,7 +255,7 @@ static int step_impl(const inrct_geom* geom, const inrct_grid* grid, const inrct
   prof_step_begin();
   prof_mark(kMarkStart, stream);
   if (w.wprep) INRCT_TRY(tc_prepare(n, theta, w.wprep, w.wprep_bytes, stream));
-  // Algorithm 1, step 1: z = P E{f_theta} (no gradient tracking); loss epilogue
+  // Algorithm 1: z = P E{f_theta}, computed without gradient tracking; loss epilogue
   INRCT_TRY(eval_dispatch(mlp, n, theta, grid->N, grid_points(grid), w.x, w.stage, w.stage_bytes,
                           stream, w.wprep));
   ProjTables tabs;
@@ -263,7 +263,7 @@ static int step_impl(const inrct_geom* geom, const inrct_grid* grid, const inrct
   double* L = loss_out ? loss_out : w.loss;  // the loss at the incoming theta, written in place
   INRCT_TRY(project_impl(geom, grid, w.x, w.z, y, w.r, L, w.stage, w.stage_bytes, stream, &tabs));
   prof_mark(kMarkProjDone, stream);
-  // Algorithm 1, step 2: v = P^T dL/dz  (LS: z - y; FLS: F (z - y), Sec. 3)
+  // Algorithm 1: v = P^T dL/dz  (LS: z - y; FLS: F (z - y), Sec. 3)
   if (loss == INRCT_LOSS_FLS) {
     INRCT_TRY(ramp_filter_impl(geom, grid, w.r, w.z, L, w.stage, w.stage_bytes, stream));
     INRCT_TRY(backproject_impl(geom, grid, w.z, w.v, w.stage, w.stage_bytes, stream, &tabs));

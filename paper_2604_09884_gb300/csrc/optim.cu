@@ -133,33 +133,78 @@ __host__ __device__ inline void adam_folded(double lr, double b1, double b2, dou
   *eps_t = (float)rn_mul(eps, rb2);
 }
 
+// One Adam element on values in registers (every kernel below uses this arithmetic, so
+// all of them give the same bits).
+__device__ __forceinline__ void adam_math(float& th, double g, float& m, float& s, float b1, float b2,
+                                          float lr_t, float eps_t) {
+  const float gi = (float)g;
+  m = fmaf(b1, m, (1.f - b1) * gi);
+  s = fmaf(b2, s, (1.f - b2) * gi * gi);
+  th -= lr_t * m / (sqrtf(s) + eps_t);
+}
+
 __device__ __forceinline__ void adam_elem(float* theta, const double* g, float* m, float* s, int64_t i,
                                           float b1, float b2, float lr_t, float eps_t) {
-  const float gi = (float)g[i];
-  const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
-  const float si = fmaf(b2, s[i], (1.f - b2) * gi * gi);
+  float th = theta[i], mi = m[i], si = s[i];
+  adam_math(th, g[i], mi, si, b1, b2, lr_t, eps_t);
   m[i] = mi;
   s[i] = si;
-  theta[i] -= lr_t * mi / (sqrtf(si) + eps_t);
+  theta[i] = th;
 }
+
+// Four consecutive elements 4j .. 4j+3 with 16-byte accesses (the caller checked alignment).
+__device__ __forceinline__ void adam_elem4(float* theta, const double* g, float* m, float* s, int64_t j,
+                                           float b1, float b2, float lr_t, float eps_t) {
+  float4 th = reinterpret_cast<float4*>(theta)[j];
+  float4 mv = reinterpret_cast<float4*>(m)[j];
+  float4 sv = reinterpret_cast<float4*>(s)[j];
+  const double2 g01 = reinterpret_cast<const double2*>(g)[2 * j];
+  const double2 g23 = reinterpret_cast<const double2*>(g)[2 * j + 1];
+  adam_math(th.x, g01.x, mv.x, sv.x, b1, b2, lr_t, eps_t);
+  adam_math(th.y, g01.y, mv.y, sv.y, b1, b2, lr_t, eps_t);
+  adam_math(th.z, g23.x, mv.z, sv.z, b1, b2, lr_t, eps_t);
+  adam_math(th.w, g23.y, mv.w, sv.w, b1, b2, lr_t, eps_t);
+  reinterpret_cast<float4*>(m)[j] = mv;
+  reinterpret_cast<float4*>(s)[j] = sv;
+  reinterpret_cast<float4*>(theta)[j] = th;
+}
+
+// Element range of thread i: vector path (elements 4i .. 4i+3) when vec, then the scalar tail.
+__device__ __forceinline__ void adam_thread(float* theta, const double* g, float* m, float* s, int64_t p,
+                                            bool vec, float b1, float b2, float lr_t, float eps_t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!vec) {
+    if (i < p) adam_elem(theta, g, m, s, i, b1, b2, lr_t, eps_t);
+    return;
+  }
+  const int64_t nv = p / 4;
+  if (i < nv) adam_elem4(theta, g, m, s, i, b1, b2, lr_t, eps_t);
+  else if (i - nv < p % 4) adam_elem(theta, g, m, s, 4 * nv + (i - nv), b1, b2, lr_t, eps_t);
+}
+
+bool adam_vec_ok(const float* theta, const double* g, const float* m, const float* s) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(theta) | reinterpret_cast<uintptr_t>(g) |
+                      reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(s);
+  return (a & 15) == 0;
+}
+
+int64_t adam_threads(int64_t p, bool vec) { return vec ? p / 4 + p % 4 : p; }
 }  // namespace
 
 __global__ void adam_kernel(float* __restrict__ theta, const double* __restrict__ g,
-                            float* __restrict__ m, float* __restrict__ s, int64_t p, float b1,
+                            float* __restrict__ m, float* __restrict__ s, int64_t p, int vec, float b1,
                             float b2, float lr_t, float eps_t) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < p) adam_elem(theta, g, m, s, i, b1, b2, lr_t, eps_t);
+  adam_thread(theta, g, m, s, p, vec != 0, b1, b2, lr_t, eps_t);
 }
 
 // Adam with the step index read from device memory (*t, already advanced for this step).
 __global__ void adam_devt_kernel(float* __restrict__ theta, const double* __restrict__ g,
-                                 float* __restrict__ m, float* __restrict__ s, int64_t p, double lr,
+                                 float* __restrict__ m, float* __restrict__ s, int64_t p, int vec, double lr,
                                  double b1, double b2, double eps, const long long* __restrict__ t) {
   __shared__ float fold[2];
   if (threadIdx.x == 0) adam_folded(lr, b1, b2, eps, *t, &fold[0], &fold[1]);
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < p) adam_elem(theta, g, m, s, i, (float)b1, (float)b2, fold[0], fold[1]);
+  adam_thread(theta, g, m, s, p, vec != 0, (float)b1, (float)b2, fold[0], fold[1]);
 }
 
 __global__ void step_counter_kernel(long long* t) { *t += 1; }
@@ -170,8 +215,9 @@ int adam_update(float* theta, const double* grad, float* m, float* s, int64_t p,
   INRCT_REQUIRE(m && s, "Adam moments must not be NULL");
   float lr_t, eps_t;
   adam_folded(a->lr, a->beta1, a->beta2, a->eps, a->t, &lr_t, &eps_t);
-  adam_kernel<<<ceil_div(p, 256), 256, 0, st>>>(theta, grad, m, s, p, (float)a->beta1,
-                                                (float)a->beta2, lr_t, eps_t);
+  const bool vec = adam_vec_ok(theta, grad, m, s);
+  adam_kernel<<<ceil_div(adam_threads(p, vec), 256), 256, 0, st>>>(theta, grad, m, s, p, vec, (float)a->beta1,
+                                                                   (float)a->beta2, lr_t, eps_t);
   INRCT_CHECK_LAUNCH("adam");
   return INRCT_OK;
 }
@@ -179,8 +225,9 @@ int adam_update(float* theta, const double* grad, float* m, float* s, int64_t p,
 int adam_update_devt(float* theta, const double* grad, float* m, float* s, int64_t p,
                      const inrct_adam* a, const long long* t_dev, cudaStream_t st) {
   INRCT_REQUIRE(m && s && t_dev, "Adam moments and the step counter must not be NULL");
-  adam_devt_kernel<<<ceil_div(p, 256), 256, 0, st>>>(theta, grad, m, s, p, a->lr, a->beta1, a->beta2,
-                                                     a->eps, t_dev);
+  const bool vec = adam_vec_ok(theta, grad, m, s);
+  adam_devt_kernel<<<ceil_div(adam_threads(p, vec), 256), 256, 0, st>>>(theta, grad, m, s, p, vec, a->lr,
+                                                                        a->beta1, a->beta2, a->eps, t_dev);
   INRCT_CHECK_LAUNCH("adam (device step index)");
   return INRCT_OK;
 }

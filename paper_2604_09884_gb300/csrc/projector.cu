@@ -1,7 +1,7 @@
 // Joseph ray-driven projector P and its exactly matched adjoint P^T on sm_103a.
 //
 // The paper factorises the projection as z = P E{f} with a discrete projector
-// P in R^{m x n} and needs v = P^T r (Sec. 3; Algorithm 1, steps 1-2).  The
+// P in R^{m x n} and needs v = P^T r (Sec. 3; Algorithm 1).  The
 // model implemented here is Joseph's: a ray picks the grid axis along which it
 // advances fastest (the driving axis), crosses every slice of that axis, and
 // linearly (2-D) or bilinearly (3-D) interpolates the image at the crossing,
