@@ -455,6 +455,8 @@ def main():
     sub_y = [inrct.view_subset_rows(g, y, S, k) for k in range(S)] if S > 1 else [y]
     sub_ws = [ws] if S == 1 else [torch.empty(inrct.step_ws_bytes(q, mlp, n_idx), dtype=torch.uint8, device=dev)
                                   for q in sub_g]
+    # projector launch shapes: the library's autotuner, once per geometry, before any timing
+    plans = [inrct.tune(q, device=dev) for q in sub_g]
 
     def step(t, idx):
         k = t % S
@@ -647,6 +649,7 @@ def main():
                 "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
                 "config": {"workload": w.name, "note": w.note, "batch": n_idx,
                            "loss": args.loss, "precision": args.prec, "view_subsets": S,
+                           "projector_plan": {k: plans[0][k] for k in ("seg", "bp_splits", "zc")},
                            "l2": "flushed between timed steps (untimed 258 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gray_s_proj_backproj": m_step / pair_ms / 1e6 if pair_ms > 0 else None,

@@ -275,7 +275,10 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
  * many small ones together is this library's own addition, so that problems far
  * smaller than the GPU still fill it.
  *
- * inrct_batch_create records the whole batched step once as a CUDA graph with
+ * inrct_batch_create first tunes the projector launch shapes of every geometry
+ * that has no tuned plan yet (inrct_tune, using that problem's part of ws and an
+ * internal stream, synchronously), then records the whole batched step once as
+ * a CUDA graph with
  * one branch per problem (branches run concurrently on internal streams); each
  * grad_step_batched call launches that graph on `stream`.  Every pointer in the
  * problem table is captured: the caller keeps the buffers alive and at the same
@@ -316,6 +319,37 @@ int inrct_batch_create(const inrct_mlp* mlp, int loss, const inrct_problem* prob
                        inrct_batch** out);
 int grad_step_batched(inrct_batch* batch, cudaStream_t stream);
 int inrct_batch_destroy(inrct_batch* batch);
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Autotuning of the projector launch shapes.  The paper fixes no projector
+ * implementation; this is a calling convention of this library only.
+ *
+ * A plan is the launch shape of project()/backproject() for one geometry: the
+ * ray segments per block of the forward projector (2-D: 4, 8 or 16; cone: 2, 4
+ * or 8), the view splits of the 2-D adjoint (1 up to twice the default, at most
+ * n_views / 8) and the voxels per thread along z of the cone adjoint (4 or 8).
+ * Every plan computes the same operator; plans differ only in the order of FP32
+ * additions (results agree to rounding).
+ *
+ * inrct_tune times every candidate plan for (geom, grid) on `stream` (5 calls
+ * each after one untimed call, on synthetic data in ws) and keeps the fastest
+ * in a process-wide table keyed by the geometry kind, N, n_views, n_bins_u and
+ * n_bins_v; project, project_noalloc, backproject, grad_step and the batched
+ * step consult that table from then on (defaults without an entry).  The call
+ * synchronises `stream` and must not run during stream capture
+ * (INRCT_ERR_INVALID_ARG).  ws: at least inrct_tune_ws_bytes(geom, grid) bytes
+ * of device memory, overwritten.  Workspace sizes of the other calls already
+ * cover every candidate plan, so no workspace needs to grow after tuning.
+ * inrct_tune_plan writes the plan in use (tuned = 1 when it came from the
+ * table, 0 for the defaults); inrct_tune_reset empties the table.
+ */
+size_t inrct_tune_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
+int inrct_tune(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes,
+               cudaStream_t stream);
+int inrct_tune_plan(const inrct_geom* geom, const inrct_grid* grid, int* seg, int* bp_splits,
+                    int* zc, int* tuned);
+int inrct_tune_reset(void);
 
 /* ------------------------------------------------------------------------ */
 /* Instrumentation (host-side, not part of the method) */

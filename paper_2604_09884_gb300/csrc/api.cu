@@ -133,6 +133,37 @@ int backproject(const inrct_geom* geom, const inrct_grid* grid, const float* sin
   return backproject_impl(geom, grid, sino, image, ws, ws_bytes, stream);
 }
 
+size_t inrct_tune_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) { return tune_ws_bytes(geom, grid); }
+
+int inrct_tune(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (g_capturing || (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)) {
+    set_error("inrct_tune: the stream is being captured");
+    return INRCT_ERR_INVALID_ARG;
+  }
+  return tune_impl(geom, grid, ws, ws_bytes, stream, nullptr);
+}
+
+int inrct_tune_plan(const inrct_geom* geom, const inrct_grid* grid, int* seg, int* bp_splits, int* zc,
+                    int* tuned) {
+  clear_error();
+  INRCT_TRY(check_geom(geom, grid));
+  INRCT_REQUIRE(seg && bp_splits && zc && tuned, "output pointers must not be NULL");
+  ProjPlan p;
+  *tuned = plan_lookup(geom, grid, &p) ? 1 : 0;
+  *seg = p.seg;
+  *bp_splits = p.bp_splits;
+  *zc = p.zc;
+  return INRCT_OK;
+}
+
+int inrct_tune_reset(void) {
+  clear_error();
+  plan_reset();
+  return INRCT_OK;
+}
+
 size_t inrct_ramp_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
   if (check_geom(geom, grid) != INRCT_OK) return 0;
   return ramp_ws_bytes(geom);
@@ -383,6 +414,27 @@ int inrct_batch_create(const inrct_mlp* mlp, int loss, const inrct_problem* prob
     b->events.push_back(ev);
   }
   cudaStream_t s0 = b->streams[0];
+  // projector launch shapes: tune every geometry without a tuned plan, each in its own
+  // problem's part of the workspace (nothing lives there before the first launch)
+  {
+    char* tp = static_cast<char*>(ws);
+    for (int i = 0; i < n_probs; ++i) {
+      const inrct_problem& q = probs[i];
+      const size_t nb = batch_problem_ws(mlp, q);
+      ProjPlan p;
+      if (!plan_lookup(&q.geom, &q.grid, &p) && tune_ws_bytes(&q.geom, &q.grid) <= nb) {
+        const int rc = tune_impl(&q.geom, &q.grid, tp, nb, s0, nullptr);
+        if (rc != INRCT_OK) {
+          char why[400];
+          snprintf(why, sizeof(why), "%s", inrct_last_error());
+          set_error("problem %d: tuning: %s", i, why);
+          batch_free(b);
+          return rc;
+        }
+      }
+      tp += nb;
+    }
+  }
   cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return fail("begin capture", e);
   g_capturing = true;

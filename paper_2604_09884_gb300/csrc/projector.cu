@@ -27,6 +27,9 @@
 //   table and sums locally: deterministic, no atomics.
 #include <math.h>
 
+#include <algorithm>
+#include <map>
+#include <vector>
 #include <mutex>
 
 #include "common.cuh"
@@ -787,13 +790,80 @@ struct ProjWs {
   float* sino_s;   // cone adjoint: the sinogram times each ray's step length
 };
 
-// Number of view splits of the 2-D adjoint (see backproject2d_tile_kernel).
-static int bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
+// Default number of view splits of the 2-D adjoint (see backproject2d_tile_kernel).
+static int default_bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
   if (geom->kind == INRCT_CONE3D) return 1;
   const int tiles = ceil_div(grid->N, kBpTile) * ceil_div(grid->N, kBpTile);
   const int want = ceil_div(kBpTargetBlocks, tiles);
   const int most = std::max(1, geom->n_views / kBpWarps);
   return std::max(1, std::min(want, most));
+}
+
+// ---------------------------------------------------------------------------
+// Launch plans and the autotuner (inrct_tune)
+//
+// A plan fixes the launch shape of P and P^T for one geometry: the ray segments per
+// block of the forward (2-D 4, 8 or 16; cone 2, 4 or 8), the view splits of the 2-D
+// adjoint (1 up to twice the default, at most one split per 8 views) and the voxels per
+// thread along z of the cone adjoint (4 or 8).  Without tuning the defaults above apply;
+// tune_impl times every candidate on the caller's stream and keeps the fastest in a
+// process-wide table keyed by the geometry's kind and sizes, which every later call
+// consults.  Workspaces are sized for the largest candidate, so a workspace sized before
+// tuning stays valid after it.
+// ---------------------------------------------------------------------------
+static int max_bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
+  if (geom->kind == INRCT_CONE3D) return 1;
+  const int most = std::max(1, geom->n_views / kBpWarps);
+  return std::max(1, std::min(most, 2 * default_bp_splits(geom, grid)));
+}
+
+static ProjPlan default_plan(const inrct_geom* geom, const inrct_grid* grid) {
+  ProjPlan p;
+  p.seg = geom->kind == INRCT_CONE3D ? 4 : 8;
+  p.bp_splits = default_bp_splits(geom, grid);
+  p.zc = 8;
+  return p;
+}
+
+struct PlanKey {
+  int kind, N, V, A, B;
+  bool operator<(const PlanKey& o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (N != o.N) return N < o.N;
+    if (V != o.V) return V < o.V;
+    if (A != o.A) return A < o.A;
+    return B < o.B;
+  }
+};
+
+static PlanKey plan_key(const inrct_geom* geom, const inrct_grid* grid) {
+  return PlanKey{geom->kind, grid->N, geom->n_views, geom->n_bins_u,
+                 geom->kind == INRCT_CONE3D ? geom->n_bins_v : 1};
+}
+
+static std::mutex g_plan_mu;
+static std::map<PlanKey, ProjPlan> g_plans;
+
+bool plan_lookup(const inrct_geom* geom, const inrct_grid* grid, ProjPlan* out) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto it = g_plans.find(plan_key(geom, grid));
+  if (it == g_plans.end()) {
+    *out = default_plan(geom, grid);
+    return false;
+  }
+  *out = it->second;
+  return true;
+}
+
+void plan_reset() {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  g_plans.clear();
+}
+
+static ProjPlan plan_for(const inrct_geom* geom, const inrct_grid* grid) {
+  ProjPlan p;
+  plan_lookup(geom, grid, &p);
+  return p;
 }
 
 static size_t proj_layout(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t cap,
@@ -806,8 +876,9 @@ static size_t proj_layout(const inrct_geom* geom, const inrct_grid* grid, void* 
   const int64_t blocks = cone ? (int64_t)ceil_div(geom->n_bins_u, 32) * geom->n_bins_v * geom->n_views
                               : (int64_t)ceil_div(num_rays(geom), 32);
   w.loss_part = forward ? c.take<double>(blocks) : nullptr;
-  w.bp_splits = forward ? 1 : bp_splits(geom, grid);
-  w.bp_part = w.bp_splits > 1 ? c.take<float>((size_t)w.bp_splits * grid_points(grid)) : nullptr;
+  const int bp_max = forward ? 1 : max_bp_splits(geom, grid);  // any plan's split count fits
+  w.bp_splits = 1;
+  w.bp_part = bp_max > 1 ? c.take<float>((size_t)bp_max * grid_points(grid)) : nullptr;
   w.sino_s = (!forward && cone) ? c.take<float>((size_t)num_rays(geom)) : nullptr;
   if (out) *out = w;
   if (ok) *ok = c.ok;
@@ -832,9 +903,9 @@ static void cone_consts(const GeomDev& g, float* pv_half, int64_t* CzF) {
   *CzF = (int64_t)llrint((0.5 * g.N - 0.5) * 4294967296.0);
 }
 
-int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
-                 const float* y, float* resid, double* loss_out, void* ws, size_t ws_bytes,
-                 cudaStream_t st, const ProjTables* pre) {
+static int project_run(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
+                       const float* y, float* resid, double* loss_out, void* ws, size_t ws_bytes,
+                       cudaStream_t st, const ProjTables* pre, const ProjPlan& plan) {
   INRCT_TRY(check_geom(geom, grid));
   INRCT_REQUIRE(image && sino, "image and sino must not be NULL");
   INRCT_REQUIRE(!y || (resid && loss_out), "y given: resid and loss_out must not be NULL");
@@ -860,22 +931,29 @@ int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* im
     float pvh;
     int64_t CzF;
     cone_consts(g, &pvh, &CzF);
-    constexpr int SEG = 4;
     dim3 grd(ceil_div(g.A, 32), g.B, g.V);
-    project3d_kernel<SEG><<<grd, dim3(32, SEG), 0, st>>>(w.t.tab0, w.t.tab1, w.t.tab2, g.A, g.B, N, pvh,
-                                                         CzF, image, w.imgT, sino, y, resid,
-                                                         w.loss_part);
+#define INRCT_P3(SEG)                                                                                  \
+  project3d_kernel<SEG><<<grd, dim3(32, SEG), 0, st>>>(w.t.tab0, w.t.tab1, w.t.tab2, g.A, g.B, N, pvh, CzF, \
+                                                       image, w.imgT, sino, y, resid, w.loss_part)
+    if (plan.seg == 2) INRCT_P3(2);
+    else if (plan.seg == 8) INRCT_P3(8);
+    else INRCT_P3(4);
+#undef INRCT_P3
     INRCT_CHECK_LAUNCH("project3d");
     if (y) {
       reduce_f64_kernel<<<1, 1024, 0, st>>>(w.loss_part, (int64_t)grd.x * grd.y * grd.z, loss_out);
       INRCT_CHECK_LAUNCH("loss reduce");
     }
   } else {
-    constexpr int SEG = 8;
     const int64_t m = num_rays(geom);
     const unsigned nb = ceil_div(m, 32);
-    project2d_kernel<SEG><<<nb, dim3(32, SEG), 0, st>>>(w.t.tab0, (int)m, N, image, w.imgT, sino, y,
-                                                        resid, w.loss_part);
+#define INRCT_P2(SEG)                                                                                       \
+  project2d_kernel<SEG><<<nb, dim3(32, SEG), 0, st>>>(w.t.tab0, (int)m, N, image, w.imgT, sino, y, resid, \
+                                                      w.loss_part)
+    if (plan.seg == 4) INRCT_P2(4);
+    else if (plan.seg == 16) INRCT_P2(16);
+    else INRCT_P2(8);
+#undef INRCT_P2
     INRCT_CHECK_LAUNCH("project2d");
     if (y) {
       reduce_f64_kernel<<<1, 1024, 0, st>>>(w.loss_part, nb, loss_out);
@@ -885,8 +963,15 @@ int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* im
   return INRCT_OK;
 }
 
-int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
-                     void* ws, size_t ws_bytes, cudaStream_t st, const ProjTables* pre) {
+int project_impl(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,
+                 const float* y, float* resid, double* loss_out, void* ws, size_t ws_bytes,
+                 cudaStream_t st, const ProjTables* pre) {
+  return project_run(geom, grid, image, sino, y, resid, loss_out, ws, ws_bytes, st, pre, plan_for(geom, grid));
+}
+
+static int backproject_run(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
+                           void* ws, size_t ws_bytes, cudaStream_t st, const ProjTables* pre,
+                           const ProjPlan& plan) {
   INRCT_TRY(check_geom(geom, grid));
   INRCT_REQUIRE(image && sino, "image and sino must not be NULL");
   ProjWs w;
@@ -909,11 +994,16 @@ int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float
     const int64_t m = num_rays(geom);
     cone_prescale_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(g, w.t.tab0, w.t.tab2, pvh, sino, w.sino_s);
     INRCT_CHECK_LAUNCH("backproject3d (ray scale)");
-    constexpr int ZC = 8;  // voxels per thread along z (measured: 8 slightly ahead of 4)
     dim3 blk(32, 4);
-    dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, ZC));
-    backproject3d_kernel<ZC><<<grd, blk, sizeof(float2) * g.V, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
-                                                                       w.sino_s, image);
+    if (plan.zc == 4) {
+      dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, 4));
+      backproject3d_kernel<4><<<grd, blk, sizeof(float2) * g.V, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
+                                                                      w.sino_s, image);
+    } else {
+      dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, 8));
+      backproject3d_kernel<8><<<grd, blk, sizeof(float2) * g.V, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
+                                                                      w.sino_s, image);
+    }
     INRCT_CHECK_LAUNCH("backproject3d");
   } else {
     static bool attr_set = false;  // per process; the attribute is per function, all devices alike
@@ -925,6 +1015,11 @@ int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float
         return INRCT_ERR_CUDA;
       }
       attr_set = true;
+    }
+    w.bp_splits = plan.bp_splits;
+    if (w.bp_splits < 1 || w.bp_splits > max_bp_splits(geom, grid)) {
+      set_error("backproject: %d view splits out of range (1..%d)", w.bp_splits, max_bp_splits(geom, grid));
+      return INRCT_ERR_INVALID_ARG;
     }
     dim3 blk(32, kBpWarps);
     dim3 grd(ceil_div(g.N, kBpTile), ceil_div(g.N, kBpTile), w.bp_splits);
@@ -940,6 +1035,110 @@ int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float
   return INRCT_OK;
 }
 
+int backproject_impl(const inrct_geom* geom, const inrct_grid* grid, const float* sino, float* image,
+                     void* ws, size_t ws_bytes, cudaStream_t st, const ProjTables* pre) {
+  return backproject_run(geom, grid, sino, image, ws, ws_bytes, st, pre, plan_for(geom, grid));
+}
+
+// ---------------------------------------------------------------------------
+// The tuner: times every candidate plan of one geometry (see "Launch plans" above)
+// ---------------------------------------------------------------------------
+__global__ void tune_fill_kernel(float* __restrict__ a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = 1.0f + 0.001f * (float)(i % 7);
+}
+
+size_t tune_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) {
+  if (check_geom(geom, grid) != INRCT_OK) return 0;
+  const size_t pw = std::max(project_ws_bytes(geom, grid, true), backproject_ws_bytes(geom, grid, true));
+  return align_up(sizeof(float) * grid_points(grid), 256) + align_up(sizeof(float) * num_rays(geom), 256) + pw + 512;
+}
+
+int tune_impl(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes, cudaStream_t st,
+              ProjPlan* out) {
+  INRCT_TRY(check_geom(geom, grid));
+  const size_t need = tune_ws_bytes(geom, grid);
+  if (!ws || ws_bytes < need) {
+    set_error("inrct_tune: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  Carver c(ws, ws_bytes);
+  const int64_t n = grid_points(grid), m = num_rays(geom);
+  float* image = c.take<float>(n);
+  float* sino = c.take<float>(m);
+  const size_t rest_off = align_up(c.off, 256);  // need leaves at least the projection scratch here
+  void* rest = static_cast<char*>(ws) + rest_off;
+  const size_t rest_bytes = ws_bytes - rest_off;
+  tune_fill_kernel<<<ceil_div(n, 256), 256, 0, st>>>(image, n);
+  INRCT_CHECK_LAUNCH("tune fill");
+  tune_fill_kernel<<<ceil_div(m, 256), 256, 0, st>>>(sino, m);
+  INRCT_CHECK_LAUNCH("tune fill");
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    set_error("inrct_tune: event creation failed");
+    return INRCT_ERR_CUDA;
+  }
+  constexpr int kReps = 5;
+  int rc = INRCT_OK;
+  // mean time of kReps calls after one untimed call (which also builds the ray tables)
+  auto timed = [&](auto&& call, float* ms) -> int {
+    INRCT_TRY(call());
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < kReps; ++r) INRCT_TRY(call());
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) {
+      set_error("inrct_tune: timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return INRCT_ERR_CUDA;
+    }
+    return INRCT_OK;
+  };
+  const bool cone = geom->kind == INRCT_CONE3D;
+  ProjPlan best = default_plan(geom, grid);
+  float best_ms = 0.f;
+  const int segs2[3] = {4, 8, 16}, segs3[3] = {2, 4, 8};
+  for (int i = 0; i < 3 && rc == INRCT_OK; ++i) {
+    ProjPlan p = best;
+    p.seg = cone ? segs3[i] : segs2[i];
+    float ms = 0.f;
+    rc = timed([&] { return project_run(geom, grid, image, sino, nullptr, nullptr, nullptr, rest, rest_bytes, st,
+                                        nullptr, p); }, &ms);
+    if (rc == INRCT_OK && (i == 0 || ms < best_ms)) {
+      best.seg = p.seg;
+      best_ms = ms;
+    }
+  }
+  std::vector<int> cands;
+  if (cone) {
+    cands = {4, 8};
+  } else {
+    const int mx = max_bp_splits(geom, grid), df = default_bp_splits(geom, grid);
+    for (int k = 1; k < mx; k *= 2) cands.push_back(k);
+    cands.push_back(mx);
+    if (std::find(cands.begin(), cands.end(), df) == cands.end()) cands.push_back(df);
+  }
+  float best_bp_ms = 0.f;
+  for (size_t i = 0; i < cands.size() && rc == INRCT_OK; ++i) {
+    ProjPlan p = best;
+    if (cone) p.zc = cands[i];
+    else p.bp_splits = cands[i];
+    float ms = 0.f;
+    rc = timed([&] { return backproject_run(geom, grid, sino, image, rest, rest_bytes, st, nullptr, p); }, &ms);
+    if (rc == INRCT_OK && (i == 0 || ms < best_bp_ms)) {
+      best.zc = p.zc;
+      best.bp_splits = p.bp_splits;
+      best_bp_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != INRCT_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[plan_key(geom, grid)] = best;
+  }
+  if (out) *out = best;
+  return INRCT_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free projection

@@ -29,6 +29,20 @@ struct ProjTables {
   double2* btrig;
 };
 
+// Launch shape of P and P^T for one geometry (see "Launch plans" in projector.cu).
+struct ProjPlan {
+  int seg;        // forward: ray segments per block
+  int bp_splits;  // 2-D adjoint: view splits
+  int zc;         // cone adjoint: voxels per thread along z
+};
+// The plan in use for a geometry; true when it came from the tuner.
+bool plan_lookup(const inrct_geom* geom, const inrct_grid* grid, ProjPlan* out);
+void plan_reset();
+size_t tune_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
+// Times every candidate plan on st (synchronises it) and keeps the fastest.
+int tune_impl(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes, cudaStream_t st,
+              ProjPlan* out);
+
 int check_geom(const inrct_geom* geom, const inrct_grid* grid);
 size_t tables_bytes(const inrct_geom* geom);
 int build_tables(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes,

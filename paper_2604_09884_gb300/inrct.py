@@ -112,6 +112,10 @@ def lib():
                                 ctypes.POINTER(Adam), _P, _P, _SZ, ctypes.POINTER(_P)], ctypes.c_int),
         "grad_step_batched": ([_P, _P], ctypes.c_int),
         "inrct_batch_destroy": ([_P], ctypes.c_int),
+        "inrct_tune_ws_bytes": ([g, gr], _SZ),
+        "inrct_tune": ([g, gr, _P, _SZ, _P], ctypes.c_int),
+        "inrct_tune_plan": ([g, gr] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
+        "inrct_tune_reset": ([], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -252,6 +256,32 @@ def backproject(g: synth.GeomSpec, sino: torch.Tensor, stream=None) -> torch.Ten
     _check(L.backproject(ctypes.byref(gd), ctypes.byref(grd), _ptr(sino, torch.float32), _ptr(v),
                          _ptr(ws), nb, _stream(stream)))
     return v
+
+
+def tune(g: synth.GeomSpec, device="cuda", stream=None) -> dict:
+    """Time the projector launch-shape candidates of this geometry and keep the fastest
+    (inrct_tune); returns the plan now in use."""
+    L = lib()
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    nb = L.inrct_tune_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
+    if nb == 0:
+        _check(L.inrct_tune(ctypes.byref(gd), ctypes.byref(grd), None, 0, _stream(stream)))
+    ws = _ws(nb, torch.device(device))
+    _check(L.inrct_tune(ctypes.byref(gd), ctypes.byref(grd), _ptr(ws), nb, _stream(stream)))
+    return tune_plan(g)
+
+
+def tune_plan(g: synth.GeomSpec) -> dict:
+    """The projector launch plan in use for this geometry (inrct_tune_plan)."""
+    L = lib()
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(L.inrct_tune_plan(ctypes.byref(gd), ctypes.byref(grd), *[ctypes.byref(x) for x in v]))
+    return {"seg": v[0].value, "bp_splits": v[1].value, "zc": v[2].value, "tuned": bool(v[3].value)}
+
+
+def tune_reset() -> None:
+    _check(lib().inrct_tune_reset())
 
 
 def ramp_filter(g: synth.GeomSpec, r: torch.Tensor, stream=None):

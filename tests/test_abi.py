@@ -158,3 +158,23 @@ def test_hash_descriptor_is_validated_on_the_host(L):
         rc = L.inr_eval_grid(ctypes.byref(m), _fake(), ctypes.byref(grd), _fake(), _fake(), 1 << 30, None)
         assert rc == 1, (m.hash_levels, m.hash_feats, m.hash_log2_T, m.hash_base, m.hash_growth, m.prec)
         assert b"hash" in L.inrct_last_error()
+
+
+def test_projector_plans_default_without_tuning(L):
+    """Without inrct_tune the plans are the built-in defaults (host-side lookup, no GPU)."""
+    assert inrct.tune_reset() is None
+    g2 = synth.GeomSpec("fan2d", 64, 90, 91, sod=100.0, sdd=150.0, span=6.283)
+    p = inrct.tune_plan(g2)
+    # 2-D: 8 segments; view splits = min(ceil(456 / tiles), views / 8) = min(114, 11)
+    assert p == {"seg": 8, "bp_splits": 11, "zc": 8, "tuned": False}
+    g3 = synth.GeomSpec("cone3d", 64, 10, 96, 96, sod=200.0, sdd=300.0)
+    assert inrct.tune_plan(g3) == {"seg": 4, "bp_splits": 1, "zc": 8, "tuned": False}
+    gd, grd = inrct.geom_desc(g2), inrct.grid_desc(2, 64)
+    nb = L.inrct_tune_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
+    assert nb > 0
+    # too small a workspace is refused before any launch
+    assert L.inrct_tune(ctypes.byref(gd), ctypes.byref(grd), _fake(), nb - 1024, None) == 3
+    assert b"workspace" in L.inrct_last_error()
+    # a mismatched grid is refused
+    grd3 = inrct.grid_desc(3, 64)
+    assert L.inrct_tune_ws_bytes(ctypes.byref(gd), ctypes.byref(grd3)) == 0
