@@ -455,8 +455,9 @@ constexpr int kBpTile = 32, kBpWarps = 8;
 constexpr int kBpTargetBlocks = 3 * 152;
 constexpr size_t kBpSmem = sizeof(float) * ((size_t)kBpWarps * 2 * kBpTile * kBpTile + kBpTile * (kBpTile + 1));
 
-__global__ void __launch_bounds__(32 * kBpWarps)
-    backproject2d_tile_kernel(GeomDev g, const int4* __restrict__ tab, const float2* __restrict__ views,
+// No launch bound (with one ptxas caps the registers and spills; 48 suffice, and the shared
+// memory already limits the SM to three blocks).
+__global__ void backproject2d_tile_kernel(GeomDev g, const int4* __restrict__ tab, const float2* __restrict__ views,
                               const float* __restrict__ sino, float* __restrict__ out, int nsplit) {
   // view split blockIdx.z of nsplit writes its own partial image (the image itself if nsplit == 1)
   float* img = out + (size_t)blockIdx.z * g.N * g.N;
@@ -579,9 +580,10 @@ __global__ void cone_prescale_kernel(GeomDev g, const int4* __restrict__ t0, con
   out[i] = sino[i] * cone_scale(vb, __ldg(t2 + ci), sa);
 }
 
+// No launch bound: with one, ptxas caps the registers and spills (56 suffice; blocks are
+// 128 threads, so any register count fits).
 template <int ZC>
-__global__ void __launch_bounds__(128)
-    backproject3d_kernel(GeomDev g, const int4* __restrict__ t0, const int4* __restrict__ t1,
+__global__ void backproject3d_kernel(GeomDev g, const int4* __restrict__ t0, const int4* __restrict__ t1,
                             const float2* __restrict__ views, int64_t CzF,
                             const float* __restrict__ sino_s, float* __restrict__ vol) {
   extern __shared__ float2 sv[];
@@ -624,8 +626,14 @@ __global__ void __launch_bounds__(128)
       const int4 T1 = __ldg(t1 + ci);
       const int64_t Hh = ((int64_t)T1.y << 32) | (int64_t)(uint32_t)T1.x;
       const int64_t Kk = ((int64_t)T1.w << 32) | (int64_t)(uint32_t)T1.z;
-      const float hg = (float)(((double)Hh * 65536.0 + (double)dj * (double)Kk) * (1.0 / 281474976710656.0));
-      const float inv_hg = 1.f / hg;
+      // z pitch of this column's rows at slice j, (Hh 2^16 + dj Kk) / 2^48, from the 32-bit
+      // halves in FP32: it only bounds the rows searched below (with a 0.1 % + 0.02-row
+      // margin), the weights come from the exact fixed-point crossings
+      const float hg = fmaf((float)dj,
+                            fmaf(__uint2float_rn((uint32_t)T1.z), 3.552713678800501e-15f,
+                                 __int2float_rn(T1.w) * 1.52587890625e-05f),
+                            fmaf(__uint2float_rn((uint32_t)T1.x), 2.3283064365386963e-10f, __int2float_rn(T1.y)));
+      const float inv_hg = __frcp_rn(hg);
       const float hb = 0.5f * fabsf(inv_hg) * 1.001f + 0.02f;
       const float* scol = sino_s + (size_t)k * B * A + a;
 #pragma unroll
