@@ -633,7 +633,8 @@ def main():
                     "bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP32_SIMT_TFLOPS,
                     "peak_source": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2 x 2.07 GHz)",
-                    "traffic": None}
+                    "traffic": recorded_traffic("simt_" + ("eval" if dominant == "eval_mlp_kernel" else "vjp"),
+                                                w.name)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
