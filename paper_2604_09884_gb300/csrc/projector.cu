@@ -351,7 +351,9 @@ __global__ void __launch_bounds__(32 * SEG)
                      float* __restrict__ resid, double* __restrict__ loss_part) {
   __shared__ float part[SEG][33];
   const int lane = threadIdx.x, s = threadIdx.y;
-  const int a = blockIdx.x * 32 + lane, row = blockIdx.y, k = blockIdx.z;
+  // grid (column groups, views, rows): the blocks of one detector row run together for all
+  // views; their rays cross nearly the same z-band of the volume, which then stays in L2
+  const int a = blockIdx.x * 32 + lane, k = blockIdx.y, row = blockIdx.z;
   const int jref = N / 2;
   float sum = 0.f, sc = 0.f;
   if (a < A) {
@@ -939,7 +941,7 @@ static int project_run(const inrct_geom* geom, const inrct_grid* grid, const flo
     float pvh;
     int64_t CzF;
     cone_consts(g, &pvh, &CzF);
-    dim3 grd(ceil_div(g.A, 32), g.B, g.V);
+    dim3 grd(ceil_div(g.A, 32), g.V, g.B);
 #define INRCT_P3(SEG)                                                                                  \
   project3d_kernel<SEG><<<grd, dim3(32, SEG), 0, st>>>(w.t.tab0, w.t.tab1, w.t.tab2, g.A, g.B, N, pvh, CzF, \
                                                        image, w.imgT, sino, y, resid, w.loss_part)
