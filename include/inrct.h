@@ -328,7 +328,7 @@ int inrct_batch_destroy(inrct_batch* batch);
  * A plan is the launch shape of project()/backproject() for one geometry: the
  * ray segments per block of the forward projector (2-D: 4, 8 or 16; cone: 2, 4
  * or 8), the view splits of the 2-D adjoint (1 up to twice the default, at most
- * n_views / 8) and the voxels per thread along z of the cone adjoint (4, 8 or 16).
+ * n_views / 8) and the voxels per thread along z of the cone adjoint (4, 8, 16 or 32).
  * Every plan computes the same operator; plans differ only in the order of FP32
  * additions (results agree to rounding).
  *

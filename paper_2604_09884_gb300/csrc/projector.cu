@@ -859,7 +859,7 @@ static int default_bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
 // A plan fixes the launch shape of P and P^T for one geometry: the ray segments per
 // block of the forward (2-D 4, 8 or 16; cone 2, 4 or 8), the view splits of the 2-D
 // adjoint (1 up to twice the default, at most one split per 8 views) and the voxels per
-// thread along z of the cone adjoint (4, 8 or 16).  Without tuning the defaults above apply;
+// thread along z of the cone adjoint (4, 8, 16 or 32).  Without tuning the defaults above apply;
 // tune_impl times every candidate on the caller's stream and keeps the fastest in a
 // process-wide table keyed by the geometry's kind and sizes, which every later call
 // consults.  Workspaces are sized for the largest candidate, so a workspace sized before
@@ -1053,6 +1053,10 @@ static int backproject_run(const inrct_geom* geom, const inrct_grid* grid, const
       dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, 4));
       backproject3d_kernel<4><<<grd, blk, sizeof(float2) * g.V, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
                                                                       w.sino_s, image);
+    } else if (plan.zc == 32) {
+      dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, 32));
+      backproject3d_kernel<32><<<grd, blk, sizeof(float2) * g.V, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
+                                                                       w.sino_s, image);
     } else if (plan.zc == 16) {
       dim3 grd(ceil_div(g.N, 32), ceil_div(g.N, 4), ceil_div(g.N, 16));
       backproject3d_kernel<16><<<grd, blk, sizeof(float2) * g.V, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
@@ -1167,7 +1171,7 @@ int tune_impl(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t w
   }
   std::vector<int> cands;
   if (cone) {
-    cands = {4, 8, 16};
+    cands = {4, 8, 16, 32};
   } else {
     const int mx = max_bp_splits(geom, grid), df = default_bp_splits(geom, grid);
     for (int k = 1; k < mx; k *= 2) cands.push_back(k);
