@@ -288,7 +288,8 @@ int grad_step(const inrct_geom* geom, const inrct_grid* grid, const inrct_mlp* m
  * The Adam step index lives in device memory: *step_counter (one int64, device)
  * is advanced by one at the start of every launch and read by the Adam update,
  * which therefore sees t = (previous value) + 1.  Set it to 0 before the first
- * launch.  The update is bit-identical to grad_step with adam->t equal to that t.
+ * launch.  The update is bit-identical to grad_step with adam->t equal to that t
+ * (for the hash-encoded INR up to the order of its table-gradient atomics).
  *
  * Problem table entries (inrct_problem) are copied; theta, y, idx, adam_m,
  * adam_s, loss_out (nullable) have the meaning and layout of grad_step.
