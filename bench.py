@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-fp32", action="store_true", help="skip the FP32 path and the BF16/FP32 gradient check")
     p.add_argument("--fp32-steps", type=int, default=10)
     p.add_argument("--no-fractions", action="store_true", help="skip the |I|/n = 1.0 and 0.05 step rates")
+    p.add_argument("--ref-seconds", type=float, default=120.0,
+                   help="--impl reference: host seconds the timed oracle samples take in total")
     p.add_argument("--subsets", type=int, default=1,
                    help="ordered subsets: step t uses interleaved view subset t mod S (Sec. 3)")
     return p.parse_args()
@@ -185,13 +187,30 @@ def oracle_rate(w, budget_s: float, frac_max: float):
 
 
 # ----------------------------------------------------------------------------
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (the slowest rank's time); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, seconds: float, world: int, device):
+    """Whole-job throughput: every rank's units over the slowest rank's time.
+    Returns (rate, slowest seconds)."""
+    slowest = max_over_ranks(seconds, world, device)
+    return world * units_per_rank / slowest, slowest
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
     # each step is one oracle sample of a fraction of the step (extrapolated to the whole
     # step part by part), sized so that the whole --steps run takes about two minutes
     steps = max(1, args.steps)
-    frac = oracle_frac(w, 4.0 * 120.0 / (steps + 2), 1 / 16)
+    frac = oracle_frac(w, 4.0 * args.ref_seconds / (steps + 2), 1 / 16)
     for _ in range(max(1, min(args.warmup, 2))):
         oracle_sample_any(w, frac)
     total = 0.0
@@ -300,13 +319,9 @@ def run_batched(args, probs, rank, world, local, dev):
             ends[k].record(stream)
         torch.cuda.synchronize()
     launches = inrct.launch_count() - l0
-    total_ms = sum(st.elapsed_time(en) for st, en in zip(starts, ends))
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value, total_s = job_rate(args.steps, sum(st.elapsed_time(en) for st, en in zip(starts, ends)) / 1000.0,
+                              world, dev)
+    ms_per_step = 1000.0 * total_s / args.steps
 
     # end to end: index sets from pinned host memory, losses back to the host
     loss_host = torch.zeros(len(state), dtype=torch.float64).pin_memory()
@@ -491,13 +506,8 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     step_ms = [st.elapsed_time(en) for st, en in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value, total_s = job_rate(args.steps, sum(step_ms) / 1000.0, world, dev)
+    ms_per_step = 1000.0 * total_s / args.steps
 
     # ---- end to end through the public API, host buffers, copies inside the timed region ----
     loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
@@ -513,12 +523,7 @@ def main():
         step(t, idx_stage)
         loss_host.copy_(loss, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = world * e2e_steps / e2e_s
+    e2e_value, e2e_s = job_rate(e2e_steps, time.perf_counter() - t0, world, dev)
     peak_mem = torch.cuda.max_memory_allocated(dev)
 
     # ---- reconstruction error of the trained INR, and other subsampling fractions ----
