@@ -554,6 +554,7 @@ def main():
     # ---- the plain FP32 path (|I| = n) and the BF16 / FP32 gradient agreement ----
     fp32 = None
     if args.prec == "bf16" and not args.no_fp32:
+        torch.cuda.reset_peak_memory_stats(dev)
         mlp32 = inrct.mlp_desc(a, inrct.FP32, B, device=dev)
         idx_all = torch.arange(g.n, dtype=torch.int32, device=dev)
         ws32 = torch.empty(inrct.step_ws_bytes(g, mlp32, g.n), dtype=torch.uint8, device=dev)
@@ -572,6 +573,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms32 = e0.elapsed_time(e1) / k32
+        ws32_bytes = ws32.numel()
+        peak32 = torch.cuda.max_memory_allocated(dev)
         del ws32
         # one estimator at the current theta: v = P^T r of its own image, the same index set
         img = inrct.inr_eval_grid(mlp32, theta, g.N)
@@ -582,6 +585,9 @@ def main():
         rel = float(torch.linalg.norm(g16 - g32) / torch.linalg.norm(g32))
         cos = float(torch.dot(g16, g32) / (torch.linalg.norm(g16) * torch.linalg.norm(g32)))
         fp32 = {"steps_per_s": 1000.0 / ms32, "ms_per_step": ms32, "batch": g.n, "steps": k32,
+                "step_ws_bytes": int(ws32_bytes),
+                "peak_mem_bytes": int(peak32),
+                "peak_mem_note": "device peak during the FP32 steps, the BF16 run's buffers still allocated",
                 "grad_bf16_vs_fp32": {"rel_l2": rel, "cosine": cos, "batch": n_idx,
                                       "v": "P^T (P f_theta - y) at the current theta"}}
 
@@ -663,7 +669,8 @@ def main():
                 "e2e": {"value": e2e_value, "unit": "steps/s",
                         "h2d_bytes_per_step": int(idx_host[0].numel() * 4), "d2h_bytes_per_step": 8},
                 "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": cpu,
-                "peak_mem_bytes": int(peak_mem), "fp32_path": fp32, "fractions": fractions,
+                "peak_mem_bytes": int(peak_mem), "step_ws_bytes": int(ws.numel()),
+                "fp32_path": fp32, "fractions": fractions,
                 "mse_vs_x_true": mse,
                 "loss_last": float(loss_host.item())}
         print(json.dumps(line), flush=True)

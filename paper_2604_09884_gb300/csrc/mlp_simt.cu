@@ -12,8 +12,10 @@
 //      pre-activations Z_l (scratch grows with the chunk, never with the grid);
 //   2. backward chain delta_l = (W_{l+1}^T delta_{l+1}) * sigma'(z_l), stored;
 //   3. dW_l = sum_points delta_l a_{l-1}^T and db_l = sum delta_l as a split-K
-//      SIMT GEMM with FP32 partials per split;
-//   4. FP64 reduction of the partials into the gradient (accumulated over chunks).
+//      SIMT GEMM with FP32 partials per split (64x64 tiles; the scalar output layer
+//      by a one-thread-per-column kernel);
+//   4. reduction of the partials into the FP64 gradient: FP32 within a warp, FP64
+//      across warps in a fixed order (accumulated over chunks).
 //
 // Hash-encoded INR (Sec. 4, "Hash Enc."): the layer-1 input is gathered from the
 // tables at theta[0, n_table) by the forward kernel; the backward kernel finishes
