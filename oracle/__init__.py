@@ -403,10 +403,10 @@ def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | 
     """
     layers = unpack(arch, theta)
     h = encode(arch, X, theta, N)
-    hd = None
+    zds = None
     if decide == "bf16" and arch.kind == "ffn":
         X32 = np.asarray(X).astype(np.float32) if X32 is None else X32
-        hd = bf16_round(_fp32_features(arch, X32))
+        zds = bf16_decision_preacts(arch, theta, X32)
     hs, zs, masks = [h], [], []
     for li, (W, b) in enumerate(layers):
         z = h @ W.T + b
@@ -414,12 +414,7 @@ def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | 
         if li == len(layers) - 1:
             h = z
         elif arch.kind in ("ffn", "hash"):
-            if hd is not None:
-                zd = hd @ bf16_round(W).T + b
-                m = zd > 0.0
-                hd = bf16_round(np.where(m, zd, 0.0))
-            else:
-                m = z > 0.0
+            m = zds[li] > 0.0 if zds is not None else z > 0.0
             masks.append(m)
             h = np.where(m, z, 0.0)
         else:
@@ -427,6 +422,33 @@ def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | 
         hs.append(h)
     f = h[:, 0]
     return (f, hs, zs, masks) if keep else f
+
+
+def bf16_decision_preacts(arch: Arch, theta, X32: np.ndarray) -> list:
+    """The pre-activations on which a BF16 tensor-core kernel decides the ReLU masks of an
+    FFN (``forward``'s decide='bf16'): layer inputs and weights rounded to BF16, products
+    accumulated wide, bias added unrounded, starting from the FP32 features of
+    ``_fp32_features``; returns one [points, width] array per hidden layer."""
+    layers = unpack(arch, theta)
+    hd = bf16_round(_fp32_features(arch, np.asarray(X32, dtype=np.float32)))
+    out = []
+    for W, b in layers[:-1]:
+        zd = hd @ bf16_round(W).T + b
+        out.append(zd)
+        hd = bf16_round(np.where(zd > 0.0, zd, 0.0))
+    return out
+
+
+def bf16_decision_margins(arch: Arch, theta, X32: np.ndarray) -> np.ndarray:
+    """Per point, the smallest |pre-activation| of the BF16 decision chain over all hidden
+    units, in units of its layer's RMS over the given points.  Where it is tiny, sums of the
+    same BF16 operands accumulated in another order (FP32 tensor cores against FP64 here)
+    can round a value differently and flip a mask: both decisions are then valid."""
+    m = None
+    for zd in bf16_decision_preacts(arch, theta, X32):
+        r = (np.abs(zd) / np.sqrt((zd ** 2).mean())).min(axis=1)
+        m = r if m is None else np.minimum(m, r)
+    return m
 
 
 def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray, decide: str | None = None,

@@ -1,0 +1,111 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py times.
+
+The grid evaluation runs on the whole grid and is checked at sampled points against the
+oracle's forward at those coordinates.  The VJP runs over the workload's whole index set
+(|I| = n/4, 2^20 or 2^22 points, chunked exactly as in the benchmark) with v zero except at
+2000 listed points: every other term of Eq. 2 is then exactly zero, so the result must equal
+the oracle's VJP over those 2000 points.  Bars: BF16 evaluation 2e-2 relative L2 (as on
+small grids), BF16 gradient 1e-2 with cosine >= 0.999 (ReLU masks decided in BF16 on both
+sides, weight only on points whose BF16 decisions clear zero by 1e-3 of their layer's RMS),
+FP32 gradient 1e-4 (points within rounding of a ReLU kink are not given weight)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2604_09884_gb300 import inrct, synth
+
+pytestmark = pytest.mark.gpu
+
+N_SAMPLE = 2000
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def cos(a, b):
+    a = np.asarray(a, np.float64)
+    return float(a @ b / np.linalg.norm(a) / np.linalg.norm(b))
+
+
+def setup(name, seed=11):
+    w = synth.workloads()[name]
+    a = w.arch
+    B = synth.fourier_matrix(a.n_feat, a.d, a.sigma, seed) if a.kind == "ffn" else None
+    B32 = B.astype(np.float32) if B is not None else None
+    oa = O.Arch(a.kind, a.d, a.width, a.n_hidden, a.n_feat, B32.astype(np.float64) if B32 is not None else None,
+                a.omega0, hash_levels=a.hash_levels, hash_feats=a.hash_feats, hash_log2_T=a.hash_log2_T,
+                hash_base=a.hash_base, hash_growth=a.hash_growth)
+    theta = synth.init_theta(a, seed + 1, **({"table_scale": 0.5} if a.kind == "hash" else {}))
+    return w, oa, B32, theta.astype(np.float32)
+
+
+def kink_free(oa, theta, X, N):
+    _, _, zs, _ = O.forward(oa, np.asarray(theta, np.float64), X, keep=True, N=N)
+    ok = np.ones(len(X), bool)
+    for z in zs[:-1]:
+        ok &= (np.abs(z) >= 1e-4 * np.sqrt((z ** 2).mean())).all(axis=1)
+    return ok
+
+
+CASES = [("fan2d_512_siren256", inrct.BF16), ("cone3d_256_ffn256", inrct.BF16),
+         ("cone3d_501_ffn512", inrct.BF16), ("fan2d_512_siren256", inrct.FP32),
+         ("fan2d_512_hash64", inrct.FP32)]
+
+
+def ids(c):
+    return f"{c[0]}_{'bf16' if c[1] == inrct.BF16 else 'fp32'}"
+
+
+@pytest.mark.parametrize("case", CASES, ids=ids)
+def test_full_grid_evaluation_at_sampled_points(case):
+    name, prec = case
+    w, oa, B32, theta = setup(name)
+    g = w.geom
+    h = inrct.mlp_desc(w.arch, prec, B32)
+    img = inrct.inr_eval_grid(h, torch.tensor(theta, device="cuda"), g.N)
+    sel = synth.index_set(g.n, N_SAMPLE, 21)
+    got = img[torch.from_numpy(sel.astype(np.int64)).cuda()].cpu().numpy()
+    del img
+    want = O.forward(oa, theta.astype(np.float64), O.grid_coords(g.d, g.N, sel), N=g.N)
+    assert rel(got, want) <= (2e-2 if prec == inrct.BF16 else 1e-5)
+
+
+@pytest.mark.parametrize("case", CASES, ids=ids)
+def test_full_index_set_vjp_with_sampled_weights(case):
+    name, prec = case
+    w, oa, B32, theta = setup(name)
+    g = w.geom
+    n_idx = g.n if (prec == inrct.FP32 and w.arch.kind == "siren") else w.batch  # FP32 path: |I| = n
+    idx = synth.index_set(g.n, n_idx, 31)
+    relu = w.arch.kind != "siren"
+    n_cand = 4 * N_SAMPLE if (relu and prec == inrct.BF16) else N_SAMPLE
+    pick = np.sort(np.random.default_rng(32).choice(n_idx, n_cand, replace=False))
+    live = idx[pick].astype(np.int64)
+    X = O.grid_coords(g.d, g.N, live)
+    if relu and prec == inrct.FP32:
+        live = live[kink_free(oa, theta, X, g.N)]
+    elif relu:
+        # BF16 masks: the kernel sums the BF16 operands on tensor cores, the oracle in FP64;
+        # where a pre-activation lies within rounding of zero (or a rounding difference
+        # upstream moves it across) both masks are valid, so those points get no weight
+        mg = O.bf16_decision_margins(oa, theta, O.grid_coords_fp32(g.d, g.N, live))
+        live = live[mg >= 1e-3][:N_SAMPLE]
+        assert live.size >= N_SAMPLE // 2
+    X = O.grid_coords(g.d, g.N, live)
+    vals = np.random.default_rng(33).normal(size=live.size)
+    v = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+    v[torch.from_numpy(live).cuda()] = torch.tensor(vals, dtype=torch.float32, device="cuda")
+    scale = g.n / n_idx
+    h = inrct.mlp_desc(w.arch, prec, B32)
+    got = inrct.inr_weighted_vjp(h, torch.tensor(theta, device="cuda"), g.N,
+                                 torch.from_numpy(idx).cuda(), v, scale).cpu().numpy()
+    wv = scale * vals.astype(np.float32).astype(np.float64)
+    if prec == inrct.BF16:
+        want = O.vjp(oa, theta.astype(np.float64), X, wv, decide="bf16", X32=O.grid_coords_fp32(g.d, g.N, live),
+                     N=g.N)
+        assert rel(got, want) <= 1e-2 and cos(got, want) >= 0.999, (rel(got, want), cos(got, want))
+    else:
+        want = O.vjp(oa, theta.astype(np.float64), X, wv, N=g.N)
+        assert rel(got, want) <= 1e-4, rel(got, want)
