@@ -343,13 +343,16 @@ int inrct_batch_destroy(inrct_batch* batch);
  * of device memory, overwritten.  Workspace sizes of the other calls already
  * cover every candidate plan, so no workspace needs to grow after tuning.
  * inrct_tune_plan writes the plan in use (tuned = 1 when it came from the
- * table, 0 for the defaults); inrct_tune_reset empties the table.
+ * table, 0 for the defaults); inrct_tune_set pins a plan of the caller's choice
+ * (INRCT_ERR_INVALID_ARG unless every field is a candidate for the geometry);
+ * inrct_tune_reset empties the table.
  */
 size_t inrct_tune_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
 int inrct_tune(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes,
                cudaStream_t stream);
 int inrct_tune_plan(const inrct_geom* geom, const inrct_grid* grid, int* seg, int* bp_splits,
                     int* zc, int* tuned);
+int inrct_tune_set(const inrct_geom* geom, const inrct_grid* grid, int seg, int bp_splits, int zc);
 int inrct_tune_reset(void);
 
 /* ------------------------------------------------------------------------ */

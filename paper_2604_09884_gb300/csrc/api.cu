@@ -158,6 +158,15 @@ int inrct_tune_plan(const inrct_geom* geom, const inrct_grid* grid, int* seg, in
   return INRCT_OK;
 }
 
+int inrct_tune_set(const inrct_geom* geom, const inrct_grid* grid, int seg, int bp_splits, int zc) {
+  clear_error();
+  ProjPlan p;
+  p.seg = seg;
+  p.bp_splits = bp_splits;
+  p.zc = zc;
+  return plan_set(geom, grid, p);
+}
+
 int inrct_tune_reset(void) {
   clear_error();
   plan_reset();

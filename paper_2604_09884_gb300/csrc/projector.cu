@@ -914,6 +914,21 @@ void plan_reset() {
   g_plans.clear();
 }
 
+int plan_set(const inrct_geom* geom, const inrct_grid* grid, const ProjPlan& p) {
+  INRCT_TRY(check_geom(geom, grid));
+  const bool cone = geom->kind == INRCT_CONE3D;
+  const bool seg_ok = cone ? (p.seg == 2 || p.seg == 4 || p.seg == 8)
+                           : (p.seg == 4 || p.seg == 8 || p.seg == 16);
+  INRCT_REQUIRE(seg_ok, "segments per ray %d not a candidate for this geometry", p.seg);
+  INRCT_REQUIRE(p.bp_splits >= 1 && p.bp_splits <= max_bp_splits(geom, grid), "view splits %d out of range (1..%d)",
+                p.bp_splits, max_bp_splits(geom, grid));
+  INRCT_REQUIRE(p.zc == 4 || p.zc == 8 || p.zc == 16 || p.zc == 32, "voxels per thread along z %d not 4, 8, 16 or 32",
+                p.zc);
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  g_plans[plan_key(geom, grid)] = p;
+  return INRCT_OK;
+}
+
 static ProjPlan plan_for(const inrct_geom* geom, const inrct_grid* grid) {
   ProjPlan p;
   plan_lookup(geom, grid, &p);

@@ -38,6 +38,8 @@ struct ProjPlan {
 // The plan in use for a geometry; true when it came from the tuner.
 bool plan_lookup(const inrct_geom* geom, const inrct_grid* grid, ProjPlan* out);
 void plan_reset();
+// Pins a plan for a geometry after checking it is one of the candidates.
+int plan_set(const inrct_geom* geom, const inrct_grid* grid, const ProjPlan& p);
 size_t tune_ws_bytes(const inrct_geom* geom, const inrct_grid* grid);
 // Times every candidate plan on st (synchronises it) and keeps the fastest.
 int tune_impl(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes, cudaStream_t st,

@@ -116,6 +116,7 @@ def lib():
         "inrct_tune": ([g, gr, _P, _SZ, _P], ctypes.c_int),
         "inrct_tune_plan": ([g, gr] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
         "inrct_tune_reset": ([], ctypes.c_int),
+        "inrct_tune_set": ([g, gr, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -278,6 +279,12 @@ def tune_plan(g: synth.GeomSpec) -> dict:
     v = [ctypes.c_int() for _ in range(4)]
     _check(L.inrct_tune_plan(ctypes.byref(gd), ctypes.byref(grd), *[ctypes.byref(x) for x in v]))
     return {"seg": v[0].value, "bp_splits": v[1].value, "zc": v[2].value, "tuned": bool(v[3].value)}
+
+
+def tune_set(g: synth.GeomSpec, seg: int, bp_splits: int, zc: int) -> None:
+    """Pin a projector launch plan for this geometry (inrct_tune_set)."""
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    _check(lib().inrct_tune_set(ctypes.byref(gd), ctypes.byref(grd), seg, bp_splits, zc))
 
 
 def tune_reset() -> None:

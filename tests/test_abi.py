@@ -178,3 +178,19 @@ def test_projector_plans_default_without_tuning(L):
     # a mismatched grid is refused
     grd3 = inrct.grid_desc(3, 64)
     assert L.inrct_tune_ws_bytes(ctypes.byref(gd), ctypes.byref(grd3)) == 0
+
+
+def test_pinned_plans_are_validated_on_the_host(L):
+    inrct.tune_reset()
+    g2 = synth.GeomSpec("fan2d", 64, 90, 91, sod=100.0, sdd=150.0, span=6.283)
+    inrct.tune_set(g2, 16, 3, 8)                        # 16 segments per ray, 3 view splits
+    assert inrct.tune_plan(g2) == {"seg": 16, "bp_splits": 3, "zc": 8, "tuned": True}
+    g3 = synth.GeomSpec("cone3d", 64, 10, 96, 96, sod=200.0, sdd=300.0)
+    big = synth.GeomSpec("par2d", 2048, 30, 2900)
+    for g, plan in [(g2, (3, 1, 8)), (g2, (1, 1, 8)), (g2, (8, 0, 8)), (g2, (8, 12, 8)), (g2, (8, 1, 5)),
+                    (g3, (1, 1, 8)), (g3, (16, 1, 8)), (big, (8, 1, 64))]:
+        with pytest.raises(inrct.InrctError) as e:
+            inrct.tune_set(g, *plan)
+        assert e.value.code == 1
+    inrct.tune_reset()
+    assert not inrct.tune_plan(g2)["tuned"]

@@ -92,3 +92,28 @@ def test_batch_creation_tunes_every_geometry():
     torch.cuda.synchronize()
     assert all(np.isfinite(q["loss"].item()) for q in probs)
     batch.close()
+
+
+@pytest.mark.parametrize("g", GEOMS, ids=lambda g: f"{g.kind}_{g.N}")
+def test_every_candidate_plan_matches_the_oracle(g):
+    """Each launch shape the tuner may choose, pinned in turn with inrct_tune_set."""
+    x = synth.phantom(g.d, g.N, 5, 7).reshape(-1)
+    r = np.random.default_rng(8).normal(size=g.m)
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    rd = torch.tensor(r, dtype=torch.float32, device="cuda")
+    zw = O.project(og(g), x)
+    vw = O.backproject(og(g), r)
+    cone = g.kind == "cone3d"
+    plans = []
+    if cone:
+        plans += [(s, 1, 8) for s in (2, 4, 8)] + [(4, 1, z) for z in (4, 8, 16, 32)]
+    else:
+        inrct.tune_reset()
+        default = inrct.tune_plan(g)["bp_splits"]
+        most = max(1, min(g.V // 8, 2 * default))  # view splits go up to twice the default
+        plans += [(s, 1, 8) for s in (4, 8, 16)] + [(8, b, 8) for b in sorted({1, 2, default, most}) if b <= most]
+    for plan in plans:
+        inrct.tune_set(g, *plan)
+        assert rel(inrct.project(g, xd).cpu().numpy(), zw) <= 1e-5, plan
+        assert rel(inrct.backproject(g, rd).cpu().numpy(), vw) <= 1e-5, plan
+    inrct.tune_reset()
