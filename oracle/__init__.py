@@ -102,6 +102,7 @@ class Geometry:
     sdd: float = 1500.0
     angle0: float = 0.0
     span: float = float(np.pi)
+    fov: int = 0   # 0: the whole grid; 1: the inscribed disk (2-D) / cylinder (3-D), see fov_mask
 
     @property
     def d(self) -> int:
@@ -205,6 +206,25 @@ def grid_coords(d: int, N: int, idx=None) -> np.ndarray:
     if d == 3:
         cols.append(c(idx // (N * N)))
     return np.stack(cols, axis=1)
+
+
+def fov_mask(d: int, N: int, idx=None) -> np.ndarray:
+    """Field of view (Sec. 3 samples the INR on the grid points inside a FOV mask; its shape
+    is not given, the reading is the inscribed disk, a cylinder along z in 3-D): pixel centre
+    (x, y) inside iff x^2 + y^2 <= 1, tested exactly in integers as
+    (2 k_x + 1 - N)^2 + (2 k_y + 1 - N)^2 <= N^2 (x = (2 k_x + 1 - N) / N)."""
+    if idx is None:
+        idx = np.arange(N ** d, dtype=np.int64)
+    idx = np.asarray(idx, dtype=np.int64)
+    a = 2 * (idx % N) + 1 - N
+    b = 2 * ((idx // N) % N) + 1 - N
+    return a * a + b * b <= N * N
+
+
+def fov_indices(g) -> np.ndarray:
+    """Flat indices of the grid points the method samples: all of them, or those in the FOV."""
+    idx = np.arange(g.n, dtype=np.int64)
+    return idx[fov_mask(g.d, g.N, idx)] if g.fov else idx
 
 
 def grid_coords_fp32(d: int, N: int, idx=None) -> np.ndarray:
@@ -505,8 +525,10 @@ def ls_loss(z, y):
 
 
 def evaluate_image(arch: Arch, theta, g: Geometry) -> np.ndarray:
-    """E{f_theta} = [f(x_1) .. f(x_n)] on the full grid (Sec. 3), flat."""
-    return forward(arch, theta, grid_coords(g.d, g.N), N=g.N)
+    """E{f_theta} = [f(x_1) .. f(x_n)] on the grid (Sec. 3), flat; zero outside the FOV
+    when the geometry has one."""
+    x = forward(arch, theta, grid_coords(g.d, g.N), N=g.N)
+    return x * fov_mask(g.d, g.N) if g.fov else x
 
 
 def backprojected_residual(arch: Arch, theta, g: Geometry, y):
@@ -519,9 +541,11 @@ def backprojected_residual(arch: Arch, theta, g: Geometry, y):
 
 
 def full_gradient(arch: Arch, theta, g: Geometry, y):
-    """grad L(theta) = sum_{i=1..n} v_i grad f(x_i) (Sec. 3).  Returns (L, grad, v)."""
+    """grad L(theta) = sum_{i=1..n} v_i grad f(x_i) over the sampled grid points (Sec. 3).
+    Returns (L, grad, v)."""
     L, _, _, v = backprojected_residual(arch, theta, g, y)
-    grad = vjp(arch, theta, grid_coords(g.d, g.N), v, N=g.N)
+    I = fov_indices(g)
+    grad = vjp(arch, theta, grid_coords(g.d, g.N, I), np.asarray(v, dtype=np.float64)[I], N=g.N)
     return L, grad, v
 
 
@@ -532,9 +556,11 @@ def estimator(arch: Arch, theta, g: Geometry, v, I, scale=None, decide=None) -> 
     ``decide`` picks how ReLU masks are decided (see ``forward``).
     """
     I = np.asarray(I, dtype=np.int64)
-    n = g.n
+    n = fov_indices(g).size          # the number of sampled points (all, or those in the FOV)
     if scale is None:
         scale = n / I.size
+    if g.fov:                        # listed points outside the FOV contribute nothing
+        I = I[fov_mask(g.d, g.N, I)]
     X = grid_coords(g.d, g.N, I)
     return vjp(arch, theta, X, scale * np.asarray(v, dtype=np.float64)[I], decide=decide,
                X32=grid_coords_fp32(g.d, g.N, I), N=g.N)
@@ -544,7 +570,9 @@ def virtual_loss(arch: Arch, theta, g: Geometry, v, I, scale=None) -> float:
     """Eq. (3): (n/|I|) sum_{i in I} v_i f(x_i), with v held constant."""
     I = np.asarray(I, dtype=np.int64)
     if scale is None:
-        scale = g.n / I.size
+        scale = fov_indices(g).size / I.size
+    if g.fov:
+        I = I[fov_mask(g.d, g.N, I)]
     X = grid_coords(g.d, g.N, I)
     return float(scale * (np.asarray(v, dtype=np.float64)[I] @ forward(arch, theta, X, N=g.N)))
 
