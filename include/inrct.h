@@ -94,10 +94,20 @@ typedef struct {
   double angle0, angle_span;
 } inrct_geom;
 
-/* Grid: d in {2, 3}, N pixels per side. */
+/*
+ * Grid: d in {2, 3}, N pixels per side, flat index row-major with x fastest.
+ * fov selects the grid points the method samples (Sec. 3 samples the INR inside
+ * a field-of-view mask and does not give its shape): 0 = every grid point, 1 =
+ * the inscribed disk (2-D) or the cylinder along z (3-D), i.e. the points with
+ * (2 k_x + 1 - N)^2 + (2 k_y + 1 - N)^2 <= N^2 (an exact integer test).  With
+ * fov = 1 inr_eval_grid writes 0 outside the mask, and listed points outside it
+ * contribute nothing to inr_weighted_vjp (as out-of-range indices do); the
+ * projector is unaffected.  A zero-initialised descriptor means fov = 0.
+ */
 typedef struct {
   int d;
   int N;
+  int fov;
 } inrct_grid;
 
 /*

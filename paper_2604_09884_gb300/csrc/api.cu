@@ -198,7 +198,8 @@ int inr_eval_grid(const inrct_mlp* mlp, const float* theta, const inrct_grid* gr
   Net n;
   INRCT_TRY(make_net(mlp, grid, &n));
   INRCT_TRY(check_tc(mlp, n));
-  return eval_dispatch(mlp, n, theta, grid->N, grid_points(grid), image, ws, ws_bytes, stream);
+  INRCT_TRY(eval_dispatch(mlp, n, theta, grid->N, grid_points(grid), image, ws, ws_bytes, stream));
+  return grid->fov ? fov_zero(image, grid_points(grid), grid->N, stream) : INRCT_OK;
 }
 
 size_t inrct_vjp_ws_bytes(const inrct_mlp* mlp, const inrct_grid* grid, int64_t n_idx) {
@@ -298,6 +299,7 @@ static int step_impl(const inrct_geom* geom, const inrct_grid* grid, const inrct
   // Algorithm 1: z = P E{f_theta}, computed without gradient tracking; loss epilogue
   INRCT_TRY(eval_dispatch(mlp, n, theta, grid->N, grid_points(grid), w.x, w.stage, w.stage_bytes,
                           stream, w.wprep));
+  if (grid->fov) INRCT_TRY(fov_zero(w.x, grid_points(grid), grid->N, stream));  // E{f} inside the FOV
   ProjTables tabs;
   INRCT_TRY(build_tables(geom, grid, w.tables, w.tables_bytes, &tabs, stream));
   double* L = loss_out ? loss_out : w.loss;  // the loss at the incoming theta, written in place

@@ -86,4 +86,11 @@ inline int64_t grid_points(const inrct_grid* g) {
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// Grid point i inside the field of view (inscribed disk / cylinder along z):
+// (2 k_x + 1 - N)^2 + (2 k_y + 1 - N)^2 <= N^2, exact in 64-bit integers.
+__host__ __device__ inline bool in_fov(int64_t i, int N) {
+  const int64_t a = 2 * (i % N) + 1 - N, b = 2 * ((i / N) % N) + 1 - N;
+  return a * a + b * b <= (int64_t)N * N;
+}
+
 }  // namespace inrct

@@ -21,6 +21,7 @@ struct Net {
   int hL, hF, hlog2T;
   int hres[kMaxHashLevels];
   int64_t n_table;
+  int fov;  // the grid's field of view (listed points outside it carry no weight)
   int64_t offW[kMaxLayers], offb[kMaxLayers];  // layer l = 0..L (L is the output layer)
   int in_dim[kMaxLayers], out_dim[kMaxLayers];
 };
@@ -79,6 +80,8 @@ int adam_update_devt(float* theta, const double* grad, float* m, float* s, int64
 // *t_dev += 1 on the stream.
 int advance_step_counter(long long* t_dev, cudaStream_t st);
 int f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t st);
+// image[i] = 0 for the grid points outside the field of view.
+int fov_zero(float* image, int64_t n, int N, cudaStream_t st);
 
 // Points processed per VJP chunk: scratch is sized for min(n_idx, this).
 constexpr int64_t kVjpChunk = int64_t(1) << 20;

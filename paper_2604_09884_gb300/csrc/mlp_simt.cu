@@ -36,6 +36,7 @@ struct NetDev {
   int hL, hF, hlog2T;
   unsigned hdense;  // bit l: level l is looked up densely
   float rcp2N;      // 1 / (2N) rounded to FP32
+  int fov;          // listed points outside the field of view carry no weight
   int hres[kMaxHashLevels];
 };
 
@@ -59,6 +60,7 @@ NetDev dev_of(const Net& n, int N) {
   d.hlog2T = n.hlog2T;
   d.hdense = 0;
   d.rcp2N = 1.0f / (2.0f * (float)N);
+  d.fov = n.fov;
   for (int l = 0; l < kMaxHashLevels; ++l) {
     d.hres[l] = l < n.hL ? n.hres[l] : 0;
     if (l < n.hL) {
@@ -388,7 +390,7 @@ __global__ void simt_bwd_kernel(const __grid_constant__ NetDev net, const __grid
     float s = 0.f;
     if (q < npts) {
       const int64_t i = idx ? (int64_t)idx[q] : q;
-      s = (i >= 0 && i < grid_size(net)) ? scale * v[i] : 0.f;
+      s = (i >= 0 && i < grid_size(net) && (!net.fov || in_fov(i, net.N))) ? scale * v[i] : 0.f;
       dout[q] = s;
       if (gtab && s != 0.f) {
         ksh[t][0] = (int)(i % net.N);

@@ -399,6 +399,7 @@ struct TileProg {
   int mode;  // 0 eval, 1 vjp
   int kind, d, F, W, L, N;
   int64_t n_grid, npts;
+  int fov;  // VJP: listed points outside the grid's field of view carry no weight
   float omega0;
   const float* B;       // F x d (FFN)
   const float* theta;   // FP32 parameters (SIREN first layer, output layer)
@@ -714,7 +715,8 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           const bool in_range = gi >= 0 && gi < P.n_grid;
           if (!in_range) gi = 0;
           point_coords(gi, P.N, P.d, x);
-          sv = (MODE == 1 && valid && in_range) ? P.scale * P.v[gi] : 0.f;
+          const bool weighted = valid && in_range && (!P.fov || in_fov(gi, P.N));
+          sv = (MODE == 1 && weighted) ? P.scale * P.v[gi] : 0.f;
         };
         setup(tile0, x0, sv0, valid0);
         setup(tile1, x1, sv1, valid1);
@@ -1208,6 +1210,7 @@ int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image,
   P.theta = theta;
   P.N = N;
   P.n_grid = npts;
+  P.fov = 0;  // evaluation: the caller masks the image
   P.npts = npts;
   P.out = image;
   const int64_t tiles = (npts + kTile - 1) / kTile;
@@ -1376,6 +1379,7 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
   int64_t ng = 1;
   for (int k = 0; k < n.d; ++k) ng *= N;
   P.n_grid = ng;
+  P.fov = n.fov;
   P.v = v;
   P.scale = (float)scale;
   P.E = w.E;

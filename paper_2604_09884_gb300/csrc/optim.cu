@@ -12,6 +12,8 @@ int make_net(const inrct_mlp* mlp, const inrct_grid* grid, Net* n) {
   INRCT_REQUIRE(mlp->d == 2 || mlp->d == 3, "input dimension d=%d must be 2 or 3", mlp->d);
   INRCT_REQUIRE(!grid || grid->d == mlp->d, "mlp d=%d differs from grid d=%d", mlp->d,
                 grid ? grid->d : 0);
+  INRCT_REQUIRE(!grid || grid->fov == 0 || grid->fov == 1, "grid fov=%d must be 0 or 1", grid ? grid->fov : 0);
+  n->fov = grid ? grid->fov : 0;
   INRCT_REQUIRE(mlp->n_hidden >= 1 && mlp->n_hidden + 1 <= kMaxLayers,
                 "n_hidden=%d out of range (1..%d)", mlp->n_hidden, kMaxLayers - 1);
   INRCT_REQUIRE(mlp->width == 64 || mlp->width == 128 || mlp->width == 256,
@@ -208,6 +210,17 @@ __global__ void adam_devt_kernel(float* __restrict__ theta, const double* __rest
 }
 
 __global__ void step_counter_kernel(long long* t) { *t += 1; }
+
+__global__ void fov_zero_kernel(float* __restrict__ image, int64_t n, int N) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !in_fov(i, N)) image[i] = 0.f;
+}
+
+int fov_zero(float* image, int64_t n, int N, cudaStream_t st) {
+  fov_zero_kernel<<<ceil_div(n, 256), 256, 0, st>>>(image, n, N);
+  INRCT_CHECK_LAUNCH("field-of-view mask");
+  return INRCT_OK;
+}
 
 int adam_update(float* theta, const double* grad, float* m, float* s, int64_t p,
                 const inrct_adam* a, cudaStream_t st) {

@@ -712,6 +712,7 @@ __global__ void backproject3d_kernel(GeomDev g, const int4* __restrict__ t0, con
 int check_geom(const inrct_geom* geom, const inrct_grid* grid) {
   INRCT_REQUIRE(geom && grid, "geometry and grid descriptors must not be NULL");
   INRCT_REQUIRE(grid->N > 0 && grid->N <= 4096, "grid side N=%d out of range (1..4096)", grid->N);
+  INRCT_REQUIRE(grid->fov == 0 || grid->fov == 1, "grid fov=%d must be 0 or 1", grid->fov);
   INRCT_REQUIRE(geom->n_views > 0 && geom->n_views <= 4096, "n_views=%d out of range (1..4096)",
                 geom->n_views);
   INRCT_REQUIRE(geom->n_bins_u > 0 && geom->n_bins_u <= 16384, "n_bins_u=%d out of range",

@@ -42,7 +42,7 @@ class Geom(ctypes.Structure):
 
 
 class Grid(ctypes.Structure):
-    _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int)]
+    _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int), ("fov", ctypes.c_int)]
 
 
 class Mlp(ctypes.Structure):
@@ -157,8 +157,8 @@ def geom_desc(g: synth.GeomSpec) -> Geom:
                 g.sdd, g.angle0, g.span)
 
 
-def grid_desc(d: int, N: int) -> Grid:
-    return Grid(d, N)
+def grid_desc(d: int, N: int, fov: int = 0) -> Grid:
+    return Grid(d, N, fov)
 
 
 def view_subset(g: synth.GeomSpec, n_subsets: int, s: int) -> synth.GeomSpec:
@@ -219,7 +219,7 @@ def num_rays(g: synth.GeomSpec) -> int:
 def project(g: synth.GeomSpec, image: torch.Tensor, y: torch.Tensor | None = None, stream=None):
     """z = P x; with y also r = z - y and L = 1/2 ||r||^2.  Returns z, or (z, r, L)."""
     L = lib()
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     dev = image.device
     z = torch.empty(g.m, dtype=torch.float32, device=dev)
     r = torch.empty(g.m, dtype=torch.float32, device=dev) if y is not None else None
@@ -236,7 +236,7 @@ def project_noalloc(g: synth.GeomSpec, image: torch.Tensor, y: torch.Tensor | No
     """project() without a caller workspace: the library's fixed static scratch is used.
     For callers that may not allocate device scratch; the outputs are still the caller's."""
     L = lib()
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     dev = image.device
     z = torch.empty(g.m, dtype=torch.float32, device=dev)
     r = torch.empty(g.m, dtype=torch.float32, device=dev) if y is not None else None
@@ -249,7 +249,7 @@ def project_noalloc(g: synth.GeomSpec, image: torch.Tensor, y: torch.Tensor | No
 def backproject(g: synth.GeomSpec, sino: torch.Tensor, stream=None) -> torch.Tensor:
     """v = P^T r (exact adjoint of project)."""
     L = lib()
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     dev = sino.device
     v = torch.empty(g.n, dtype=torch.float32, device=dev)
     nb = L.inrct_backproject_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
@@ -263,7 +263,7 @@ def tune(g: synth.GeomSpec, device="cuda", stream=None) -> dict:
     """Time the projector launch-shape candidates of this geometry and keep the fastest
     (inrct_tune); returns the plan now in use."""
     L = lib()
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     nb = L.inrct_tune_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
     if nb == 0:
         _check(L.inrct_tune(ctypes.byref(gd), ctypes.byref(grd), None, 0, _stream(stream)))
@@ -275,7 +275,7 @@ def tune(g: synth.GeomSpec, device="cuda", stream=None) -> dict:
 def tune_plan(g: synth.GeomSpec) -> dict:
     """The projector launch plan in use for this geometry (inrct_tune_plan)."""
     L = lib()
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     v = [ctypes.c_int() for _ in range(4)]
     _check(L.inrct_tune_plan(ctypes.byref(gd), ctypes.byref(grd), *[ctypes.byref(x) for x in v]))
     return {"seg": v[0].value, "bp_splits": v[1].value, "zc": v[2].value, "tuned": bool(v[3].value)}
@@ -283,7 +283,7 @@ def tune_plan(g: synth.GeomSpec) -> dict:
 
 def tune_set(g: synth.GeomSpec, seg: int, bp_splits: int, zc: int) -> None:
     """Pin a projector launch plan for this geometry (inrct_tune_set)."""
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     _check(lib().inrct_tune_set(ctypes.byref(gd), ctypes.byref(grd), seg, bp_splits, zc))
 
 
@@ -294,7 +294,7 @@ def tune_reset() -> None:
 def ramp_filter(g: synth.GeomSpec, r: torch.Tensor, stream=None):
     """(F r, 1/2 r^T F r) with F the ramp filter of the FLS loss."""
     L = lib()
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     out = torch.empty_like(r)
     loss = torch.empty(1, dtype=torch.float64, device=r.device)
     nb = L.inrct_ramp_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
@@ -304,10 +304,10 @@ def ramp_filter(g: synth.GeomSpec, r: torch.Tensor, stream=None):
     return out, loss
 
 
-def inr_eval_grid(mlp: MlpHandle, theta: torch.Tensor, N: int, stream=None) -> torch.Tensor:
-    """E{f_theta} on the N^d grid (flat, x fastest)."""
+def inr_eval_grid(mlp: MlpHandle, theta: torch.Tensor, N: int, stream=None, fov: int = 0) -> torch.Tensor:
+    """E{f_theta} on the N^d grid (flat, x fastest); zero outside the field of view if fov."""
     L = lib()
-    grd = grid_desc(mlp.spec.d, N)
+    grd = grid_desc(mlp.spec.d, N, fov)
     img = torch.empty(N ** mlp.spec.d, dtype=torch.float32, device=theta.device)
     nb = L.inrct_eval_ws_bytes(ctypes.byref(mlp.desc), ctypes.byref(grd))
     ws = _ws(nb, theta.device)
@@ -317,10 +317,11 @@ def inr_eval_grid(mlp: MlpHandle, theta: torch.Tensor, N: int, stream=None) -> t
 
 
 def inr_weighted_vjp(mlp: MlpHandle, theta: torch.Tensor, N: int, idx: torch.Tensor,
-                     v: torch.Tensor, scale: float, want_f32: bool = False, stream=None):
-    """scale * sum_k v[idx[k]] grad f(x_idx[k]) as FP64 (and FP32 if asked)."""
+                     v: torch.Tensor, scale: float, want_f32: bool = False, stream=None, fov: int = 0):
+    """scale * sum_k v[idx[k]] grad f(x_idx[k]) as FP64 (and FP32 if asked); with fov, listed
+    points outside the field of view contribute nothing."""
     L = lib()
-    grd = grid_desc(mlp.spec.d, N)
+    grd = grid_desc(mlp.spec.d, N, fov)
     dev = theta.device
     g64 = torch.empty(mlp.p, dtype=torch.float64, device=dev)
     g32 = torch.empty(mlp.p, dtype=torch.float32, device=dev) if want_f32 else None
@@ -333,7 +334,7 @@ def inr_weighted_vjp(mlp: MlpHandle, theta: torch.Tensor, N: int, idx: torch.Ten
 
 
 def step_ws_bytes(g: synth.GeomSpec, mlp: MlpHandle, n_idx: int) -> int:
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     return int(lib().inrct_step_ws_bytes(ctypes.byref(gd), ctypes.byref(grd), ctypes.byref(mlp.desc),
                                          n_idx))
 
@@ -345,7 +346,7 @@ def grad_step(g: synth.GeomSpec, mlp: MlpHandle, theta: torch.Tensor, y: torch.T
               loss_kind: int = LOSS_LS, stream=None):
     """Algorithm 1 + Adam in place on theta/m/s.  ws may be preallocated (step_ws_bytes)."""
     L = lib()
-    gd, grd = geom_desc(g), grid_desc(g.d, g.N)
+    gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     if ws is None:
         ws = _ws(step_ws_bytes(g, mlp, idx.numel()), theta.device)
     _check(L.grad_step(ctypes.byref(gd), ctypes.byref(grd), ctypes.byref(mlp.desc), loss_kind,
@@ -370,7 +371,7 @@ class Batch:
         arr = (Problem * len(problems))()
         for k, q in enumerate(problems):
             g = q["geom"]
-            arr[k] = Problem(geom_desc(g), grid_desc(g.d, g.N), _ptr(q["theta"], torch.float32).value,
+            arr[k] = Problem(geom_desc(g), grid_desc(g.d, g.N, g.fov), _ptr(q["theta"], torch.float32).value,
                              _ptr(q["y"], torch.float32).value, _ptr(q["idx"], torch.int32).value,
                              q["idx"].numel(), float(q["scale"]), _ptr(q["m"], torch.float32).value,
                              _ptr(q["s"], torch.float32).value,

@@ -31,6 +31,7 @@ class GeomSpec:
     sdd: float = 1500.0
     angle0: float = 0.0
     span: float = math.pi
+    fov: int = 0       # grid points sampled: 0 all, 1 the inscribed disk / cylinder
 
     @property
     def d(self):
@@ -46,7 +47,7 @@ class GeomSpec:
 
     def as_dict(self):
         return dict(kind=self.kind, N=self.N, V=self.V, A=self.A, B=self.B, du=self.du,
-                    dv=self.dv, sod=self.sod, sdd=self.sdd, angle0=self.angle0, span=self.span)
+                    dv=self.dv, sod=self.sod, sdd=self.sdd, angle0=self.angle0, span=self.span, fov=self.fov)
 
 
 @dataclass

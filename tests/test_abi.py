@@ -194,3 +194,16 @@ def test_pinned_plans_are_validated_on_the_host(L):
         assert e.value.code == 1
     inrct.tune_reset()
     assert not inrct.tune_plan(g2)["tuned"]
+
+
+def test_field_of_view_flag_is_validated_on_the_host(L):
+    g = synth.GeomSpec("fan2d", 64, 10, 91, sod=100.0, sdd=150.0, span=6.283)
+    gd = inrct.geom_desc(g)
+    m = inrct.Mlp(1, 2, 0, None, 30.0, 2, 64, inrct.FP32)
+    for fov, ok in [(0, True), (1, True), (2, False), (-1, False)]:
+        grd = inrct.grid_desc(2, 64, fov)
+        assert (L.inrct_project_ws_bytes(ctypes.byref(gd), ctypes.byref(grd)) > 0) == ok
+        assert (L.inrct_vjp_ws_bytes(ctypes.byref(m), ctypes.byref(grd), 100) > 0) == ok
+        if not ok:
+            rc = L.inr_eval_grid(ctypes.byref(m), _fake(), ctypes.byref(grd), _fake(), _fake(), 1 << 30, None)
+            assert rc == 1 and b"fov" in L.inrct_last_error()
