@@ -333,6 +333,21 @@ int inrct_batch_destroy(inrct_batch* batch);
 
 /* ------------------------------------------------------------------------ */
 /*
+ * inrct_check_index_set -- validation of an index set I, off the hot path (the
+ * compute calls accept any list: out-of-range indices and points outside the
+ * field of view contribute nothing, repeats count once per listing).  Writes
+ * counts[0] = entries outside [0, n), counts[1] = entries outside the grid's
+ * field of view (fov = 1 only), counts[2] = entries repeating an earlier one
+ * (host array of 3).  idx: n_idx int32 on the device.  ws: at least
+ * inrct_check_index_ws_bytes(grid) bytes of device memory (a bitmap of n bits).
+ * Synchronises `stream`.
+ */
+size_t inrct_check_index_ws_bytes(const inrct_grid* grid);
+int inrct_check_index_set(const inrct_grid* grid, const int32_t* idx, int64_t n_idx, long long* counts,
+                          void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/*
  * Autotuning of the projector launch shapes.  The paper fixes no projector
  * implementation; this is a calling convention of this library only.
  *

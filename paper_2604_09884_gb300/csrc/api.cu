@@ -133,6 +133,20 @@ int backproject(const inrct_geom* geom, const inrct_grid* grid, const float* sin
   return backproject_impl(geom, grid, sino, image, ws, ws_bytes, stream);
 }
 
+size_t inrct_check_index_ws_bytes(const inrct_grid* grid) {
+  if (!grid || grid->N <= 0 || grid->N > 4096 || (grid->d != 2 && grid->d != 3)) return 0;
+  return check_index_ws_bytes(grid_points(grid));
+}
+
+int inrct_check_index_set(const inrct_grid* grid, const int32_t* idx, int64_t n_idx, long long* counts, void* ws,
+                          size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  INRCT_REQUIRE(grid && grid->N > 0 && grid->N <= 4096 && (grid->d == 2 || grid->d == 3), "invalid grid");
+  INRCT_REQUIRE(grid->fov == 0 || grid->fov == 1, "grid fov=%d must be 0 or 1", grid->fov);
+  INRCT_REQUIRE(counts && (idx || n_idx == 0) && n_idx >= 0, "idx and counts must not be NULL");
+  return check_index_set(idx, n_idx, grid_points(grid), grid->N, grid->fov, ws, ws_bytes, counts, stream);
+}
+
 size_t inrct_tune_ws_bytes(const inrct_geom* geom, const inrct_grid* grid) { return tune_ws_bytes(geom, grid); }
 
 int inrct_tune(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t ws_bytes, cudaStream_t stream) {

@@ -82,6 +82,9 @@ int advance_step_counter(long long* t_dev, cudaStream_t st);
 int f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t st);
 // image[i] = 0 for the grid points outside the field of view.
 int fov_zero(float* image, int64_t n, int N, cudaStream_t st);
+size_t check_index_ws_bytes(int64_t n);
+int check_index_set(const int32_t* idx, int64_t n_idx, int64_t n, int N, int fov, void* ws, size_t ws_bytes,
+                    long long* counts_out, cudaStream_t st);
 
 // Points processed per VJP chunk: scratch is sized for min(n_idx, this).
 constexpr int64_t kVjpChunk = int64_t(1) << 20;

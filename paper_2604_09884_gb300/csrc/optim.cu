@@ -216,6 +216,49 @@ __global__ void fov_zero_kernel(float* __restrict__ image, int64_t n, int N) {
   if (i < n && !in_fov(i, N)) image[i] = 0.f;
 }
 
+// Index-set check: counts[0] out of range, counts[1] outside the field of view, counts[2]
+// repeats (an index whose bit in the bitmap was already set by another entry).
+__global__ void check_index_kernel(const int32_t* __restrict__ idx, int64_t n_idx, int64_t n, int N, int fov,
+                                   unsigned int* __restrict__ bits, unsigned long long* __restrict__ counts) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_idx) return;
+  const int64_t i = idx[k];
+  if (i < 0 || i >= n) {
+    atomicAdd(&counts[0], 1ull);
+    return;
+  }
+  if (fov && !in_fov(i, N)) atomicAdd(&counts[1], 1ull);
+  const unsigned int b = 1u << (i & 31);
+  if (atomicOr(&bits[i >> 5], b) & b) atomicAdd(&counts[2], 1ull);
+}
+
+size_t check_index_ws_bytes(int64_t n) { return 256 + align_up(sizeof(unsigned int) * ((n + 31) / 32), 256); }
+
+int check_index_set(const int32_t* idx, int64_t n_idx, int64_t n, int N, int fov, void* ws, size_t ws_bytes,
+                    long long* counts_out, cudaStream_t st) {
+  const size_t need = check_index_ws_bytes(n);
+  if (!ws || ws_bytes < need) {
+    set_error("inrct_check_index_set: workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+    return INRCT_ERR_WORKSPACE;
+  }
+  unsigned long long* counts = static_cast<unsigned long long*>(ws);
+  unsigned int* bits = reinterpret_cast<unsigned int*>(static_cast<char*>(ws) + 256);
+  cudaError_t e = cudaMemsetAsync(ws, 0, need, st);
+  if (e == cudaSuccess && n_idx > 0) {
+    check_index_kernel<<<ceil_div(n_idx, 256), 256, 0, st>>>(idx, n_idx, n, N, fov, bits, counts);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error("inrct_check_index_set: %s", cudaGetErrorString(e));
+    return INRCT_ERR_CUDA;
+  }
+  for (int q = 0; q < 3; ++q) counts_out[q] = (long long)h[q];
+  return INRCT_OK;
+}
+
 int fov_zero(float* image, int64_t n, int N, cudaStream_t st) {
   fov_zero_kernel<<<ceil_div(n, 256), 256, 0, st>>>(image, n, N);
   INRCT_CHECK_LAUNCH("field-of-view mask");

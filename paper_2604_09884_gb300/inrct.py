@@ -112,6 +112,8 @@ def lib():
                                 ctypes.POINTER(Adam), _P, _P, _SZ, ctypes.POINTER(_P)], ctypes.c_int),
         "grad_step_batched": ([_P, _P], ctypes.c_int),
         "inrct_batch_destroy": ([_P], ctypes.c_int),
+        "inrct_check_index_ws_bytes": ([gr], _SZ),
+        "inrct_check_index_set": ([gr, _P, _I64, ctypes.POINTER(ctypes.c_longlong), _P, _SZ, _P], ctypes.c_int),
         "inrct_tune_ws_bytes": ([g, gr], _SZ),
         "inrct_tune": ([g, gr, _P, _SZ, _P], ctypes.c_int),
         "inrct_tune_plan": ([g, gr] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
@@ -270,6 +272,18 @@ def tune(g: synth.GeomSpec, device="cuda", stream=None) -> dict:
     ws = _ws(nb, torch.device(device))
     _check(L.inrct_tune(ctypes.byref(gd), ctypes.byref(grd), _ptr(ws), nb, _stream(stream)))
     return tune_plan(g)
+
+
+def check_index_set(d: int, N: int, idx: torch.Tensor, fov: int = 0, stream=None) -> dict:
+    """Counts of out-of-range, outside-the-FOV and repeated entries of an index set."""
+    L = lib()
+    grd = grid_desc(d, N, fov)
+    nb = L.inrct_check_index_ws_bytes(ctypes.byref(grd))
+    ws = _ws(nb, idx.device)
+    c = (ctypes.c_longlong * 3)()
+    _check(L.inrct_check_index_set(ctypes.byref(grd), _ptr(idx, torch.int32), idx.numel(), c, _ptr(ws), nb,
+                                   _stream(stream)))
+    return {"out_of_range": c[0], "outside_fov": c[1], "repeats": c[2]}
 
 
 def tune_plan(g: synth.GeomSpec) -> dict:

@@ -207,3 +207,13 @@ def test_field_of_view_flag_is_validated_on_the_host(L):
         if not ok:
             rc = L.inr_eval_grid(ctypes.byref(m), _fake(), ctypes.byref(grd), _fake(), _fake(), 1 << 30, None)
             assert rc == 1 and b"fov" in L.inrct_last_error()
+
+
+def test_index_set_check_refuses_on_the_host(L):
+    grd = inrct.grid_desc(2, 64, 1)
+    nb = L.inrct_check_index_ws_bytes(ctypes.byref(grd))
+    assert nb >= 256 + 64 * 64 // 8
+    c = (ctypes.c_longlong * 3)()
+    assert L.inrct_check_index_set(ctypes.byref(grd), _fake(), 10, c, _fake(), nb - 256, None) == 3
+    bad = inrct.grid_desc(2, 64, 3)
+    assert L.inrct_check_index_set(ctypes.byref(bad), _fake(), 10, c, _fake(), nb, None) == 1

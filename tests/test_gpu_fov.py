@@ -99,3 +99,17 @@ def test_grad_step_on_a_masked_problem_matches_the_oracle(prec):
     else:
         assert abs(loss.item() - L0) <= 2e-2 * L0
         assert rel(got, want) <= 1e-2 and float(got @ want / np.linalg.norm(got) / np.linalg.norm(want)) >= 0.999
+
+
+def test_index_set_check_counts():
+    N = 48
+    n = N * N
+    idx = synth.index_set(n, 700, 9).astype(np.int64)
+    listed = np.concatenate([idx, idx[:5], idx[100:102], [-1, n, n + 5, -(1 << 30)]]).astype(np.int32)
+    c0 = inrct.check_index_set(2, N, cuda(listed, torch.int32))
+    assert c0 == {"out_of_range": 4, "outside_fov": 0, "repeats": 7}
+    c1 = inrct.check_index_set(2, N, cuda(listed, torch.int32), fov=1)
+    valid = listed[(listed >= 0) & (listed < n)].astype(np.int64)
+    assert c1 == {"out_of_range": 4, "outside_fov": int((~O.fov_mask(2, N, valid)).sum()), "repeats": 7}
+    assert inrct.check_index_set(3, 20, cuda(np.arange(8000), torch.int32)) == {"out_of_range": 0, "outside_fov": 0,
+                                                                             "repeats": 0}
