@@ -57,6 +57,8 @@ def parse():
                    help="--impl reference: host seconds the timed oracle samples take in total")
     p.add_argument("--subsets", type=int, default=1,
                    help="ordered subsets: step t uses interleaved view subset t mod S (Sec. 3)")
+    p.add_argument("--plan", default=None, metavar="SEG,BP_SPLITS,ZC",
+                   help="pin this projector launch plan instead of running the autotuner")
     return p.parse_args()
 
 
@@ -471,7 +473,14 @@ def main():
     sub_ws = [ws] if S == 1 else [torch.empty(inrct.step_ws_bytes(q, mlp, n_idx), dtype=torch.uint8, device=dev)
                                   for q in sub_g]
     # projector launch shapes: the library's autotuner, once per geometry, before any timing
-    plans = [inrct.tune(q, device=dev) for q in sub_g]
+    # (or a plan pinned on the command line, e.g. to reproduce a measurement's launch shapes)
+    if args.plan:
+        seg, bp, zc = (int(x) for x in args.plan.split(","))
+        for q in sub_g:
+            inrct.tune_set(q, seg, bp, zc)
+        plans = [inrct.tune_plan(q) for q in sub_g]
+    else:
+        plans = [inrct.tune(q, device=dev) for q in sub_g]
 
     def step(t, idx):
         k = t % S
