@@ -35,10 +35,24 @@ __device__ __forceinline__ float grid_coord(int64_t k, int N) {
   return __fdiv_rn((float)(2 * k + 1 - N), (float)N);
 }
 
+// Coordinates of grid point i (x fastest).  Indices below 2^32 take 32-bit divisions (the
+// 64-bit ones are a long instruction sequence, on the path of every tile's set-up).
 __device__ __forceinline__ void point_coords(int64_t i, int N, int d, float* x) {
-  x[0] = grid_coord(i % N, N);
-  x[1] = grid_coord((i / N) % N, N);
-  x[2] = d == 3 ? grid_coord(i / ((int64_t)N * N), N) : 0.f;
+  int64_t ix, iy, iz;
+  if ((uint64_t)i <= 0xffffffffull) {
+    const uint32_t u = (uint32_t)i, n = (uint32_t)N;
+    const uint32_t q = u / n, q2 = q / n;
+    ix = u - q * n;
+    iy = q - q2 * n;
+    iz = q2;
+  } else {
+    ix = i % N;
+    iy = (i / N) % N;
+    iz = i / ((int64_t)N * N);
+  }
+  x[0] = grid_coord(ix, N);
+  x[1] = grid_coord(iy, N);
+  x[2] = d == 3 ? grid_coord(iz, N) : 0.f;
 }
 
 // FP32 SIMT path

@@ -50,10 +50,11 @@ constexpr int kTile = 128;       // points per tile (MMA M)
 constexpr int kNSplit = 1;       // MMA N-groups per weight K-panel: N = W / kNSplit
 constexpr int kKChunk = 64;      // K per weight ring slot (16, 32 or 64: 32-, 64-, 128-byte swizzle);
                                  // 64 measured fastest: each slot costs a fixed hand-off
-// Weight ring: ring_bytes(mode) / (W / kNSplit * 2 kKChunk B) slots.  Evaluation takes the
-// deepest ring that fits; the VJP keeps 64 KB so that more of the SM's L1 is left for its
-// sigma' and scratch traffic.
-__host__ __device__ constexpr int ring_bytes(int mode) { return mode == 0 ? 96 * 1024 : 64 * 1024; }
+// Weight ring: ring_bytes(mode) / (W / kNSplit * 2 kKChunk B) slots.  64 KB in both modes: the
+// weights arrive ahead of the MMAs with two slots (loading each slot only once changes the
+// evaluation's time by 1 %), and the room a deeper ring would take holds the staged parameter
+// tables instead.
+__host__ __device__ constexpr int ring_bytes(int) { return 64 * 1024; }
 constexpr int kRingMax = 8;
 // 64-bit words after the ring: 2 kRingMax + 31 barriers, then tmem base and abort flag (one word)
 constexpr int kTileBars = 2 * kRingMax + 31 + 1;
@@ -406,7 +407,7 @@ struct TileProg {
   const float* bias;    // folded FP32 biases, [L][W]
   const float4* first;  // first-layer table (see PrepTable)
   int n_first;          // its entries (SIREN W, FFN F)
-  int first_staged;     // VJP: the table fits the shared-memory staging area
+  int first_staged;     // the table fits the shared-memory staging area
   const float* wout;    // output-layer weights [W], 16-byte aligned
   int64_t offW0, offb0, offWout, offbout;  // theta offsets (first layer, output layer)
   int n_stages;
@@ -528,9 +529,10 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   uint32_t* tmem_base = reinterpret_cast<uint32_t*>(drain_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_base + 1);
   float* dotp = reinterpret_cast<float*>(bars + kTileBars);  // [NWG][kTile]
-  // VJP (64 KB ring): the small parameter tables are staged in shared memory after the dot
-  // scratch; evaluation (96 KB ring) reads them from global memory through L1.
-  constexpr bool kStage = MODE == 1;
+  // The small parameter tables are staged in shared memory after the dot scratch.  All lanes
+  // of a warp read the same entry: from shared memory that is a broadcast, while through L1
+  // each such load returned a copy per lane (evaluation of 512^2 points of the SIREN 5 x 256:
+  // 179 -> 169 us, together with the paired accumulator loads below).
   float* bias_s = dotp + NWG * kTile;                   // [L][W]
   float* wout_s = bias_s + (size_t)P.L * W;             // [W]
   float4* first_s = reinterpret_cast<float4*>(wout_s + W);  // [n_first] when P.first_staged
@@ -562,12 +564,10 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (kStage) {
-    for (int i = threadIdx.x; i < P.L * W; i += blockDim.x) bias_s[i] = P.bias[i];
-    for (int i = threadIdx.x; i < W; i += blockDim.x) wout_s[i] = P.wout[i];
-    if (P.first_staged)
-      for (int i = threadIdx.x; i < P.n_first; i += blockDim.x) first_s[i] = P.first[i];
-  }
+  for (int i = threadIdx.x; i < P.L * W; i += blockDim.x) bias_s[i] = P.bias[i];
+  for (int i = threadIdx.x; i < W; i += blockDim.x) wout_s[i] = P.wout[i];
+  if (P.first_staged)
+    for (int i = threadIdx.x; i < P.n_first; i += blockDim.x) first_s[i] = P.first[i];
   if (warp == 0) tmem_alloc(tmem_base, 2 * W);
   tc_fence_before();
   __syncthreads();
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
             const int f0 = 32 * c + 8 * g;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const float4 bf = (kStage && P.first_staged) ? first_s[f0 + i] : __ldg(P.first + f0 + i);
+              const float4 bf = P.first_staged ? first_s[f0 + i] : __ldg(P.first + f0 + i);
               float ph = __fadd_rn(__fmul_rn(bf.x, xt[0]), __fmul_rn(bf.y, xt[1]));
               if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, xt[2]));
               four_feat2(ph, &v[8 + i], &v[i]);  // v[0..7] cos, v[8..15] sin
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
             float cs[CW];
 #pragma unroll
             for (int i = 0; i < CW; ++i) {
-              const float4 w1 = (kStage && P.first_staged) ? first_s[col0 + i] : __ldg(P.first + col0 + i);
+              const float4 w1 = P.first_staged ? first_s[col0 + i] : __ldg(P.first + col0 + i);
               const float z = fmaf(w1.x, xt[0], fmaf(w1.y, xt[1], fmaf(w1.z, xt[2], w1.w)));
               if (MODE == 1)
                 __sincosf(z, &v[i], &cs[i]);
@@ -820,87 +820,101 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           af ^= 1u << t;
           tc_fence_after();
           float dot = 0.f;
-          for (int c = 0; c < W / 64; ++c) {
-            const int col0 = 64 * c + CW * g;
-            tmem_ld<CW>(tmem + lane_off + t * W + col0, v);
-            if (bwd) {
-              // v = (W'_l^T delta_l) for layer l; delta_{l-1} = v * sigma'(u_{l-1})
-              float sg[CW];
+          // evaluation: the accumulator columns of two chunks are loaded behind one wait (W / 64
+          // is 2 or 4); the VJP, which holds more live values, loads one chunk at a time
+          constexpr int kPair = MODE == 0 ? 2 : 1;
+          static_assert(kPair == 1 || CW == 16, "paired accumulator loads take 16 columns per chunk");
+          for (int c2 = 0; c2 < W / 64; c2 += kPair) {
+            float vv[kPair * CW];
+            if constexpr (kPair == 2)
+              tmem_ld16x2(tmem + lane_off + t * W + 64 * c2 + CW * g,
+                          tmem + lane_off + t * W + 64 * (c2 + 1) + CW * g, vv);
+            else
+              tmem_ld<CW>(tmem + lane_off + t * W + 64 * c2 + CW * g, vv);
 #pragma unroll
-              for (int k = 0; k < CW / 8; ++k) {
-                const uint32_t u[4] = {sgn[k].x, sgn[k].y, sgn[k].z, sgn[k].w};
+            for (int cc = 0; cc < kPair; ++cc) {
+              const int c = c2 + cc;
+              const int col0 = 64 * c + CW * g;
+              float* v = vv + cc * CW;
+              if (bwd) {
+                // v = (W'_l^T delta_l) for layer l; delta_{l-1} = v * sigma'(u_{l-1})
+                float sg[CW];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  sg[8 * k + 2 * e] = __uint_as_float(u[e] << 16);
-                  sg[8 * k + 2 * e + 1] = __uint_as_float(u[e] & 0xffff0000u);
-                }
-              }
-              if (c + 1 < W / 64) {
+                for (int k = 0; k < CW / 8; ++k) {
+                  const uint32_t u[4] = {sgn[k].x, sgn[k].y, sgn[k].z, sgn[k].w};
 #pragma unroll
-                for (int k = 0; k < CW / 8; ++k)
-                  sgn[k] = store_t ? reinterpret_cast<const uint4*>(P.Sg + sg_off(l - 1, tile_t, c + 1))[k]
-                                   : make_uint4(0, 0, 0, 0);
-              }
-              if (KIND == INRCT_FFN_RELU) {
-#pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] = sg[i] > 0.f ? v[i] : 0.f;
-              } else {
-#pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] *= sg[i];
-              }
-            } else {
-              const float4* bl = reinterpret_cast<const float4*>((kStage ? bias_s : P.bias) + (size_t)l * W + col0);
-              float cs[CW];
-#pragma unroll
-              for (int i4 = 0; i4 < CW / 4; ++i4) {
-                const float4 bb = kStage ? bl[i4] : __ldg(bl + i4);
-                const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                  const int i = 4 * i4 + k;
-                  const float z = v[i] + bq[k];
-                  if (KIND == INRCT_FFN_RELU) {
-                    v[i] = fmaxf(z, 0.f);
-                    if (MODE == 1) cs[i] = z > 0.f ? 1.f : 0.f;
-                  } else if (MODE == 1) {
-                    __sincosf(z, &v[i], &cs[i]);
-                  } else {
-                    v[i] = __sinf(z);
+                  for (int e = 0; e < 4; ++e) {
+                    sg[8 * k + 2 * e] = __uint_as_float(u[e] << 16);
+                    sg[8 * k + 2 * e + 1] = __uint_as_float(u[e] & 0xffff0000u);
                   }
                 }
-              }
-              if (MODE == 1 && store_t) {
-                if (kind == kFwdHidden)  // a_l itself goes out from the panels
-                  store_row_bf16<CW>(P.Sg + sg_off(l, tile_t, c), cs);
-                else                     // a_{L-1} is not a panel (the panels take delta_{L-1})
-                  store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
-              }
-              if (kind == kFwdLast) {
-                const float4* wo = reinterpret_cast<const float4*>((kStage ? wout_s : P.wout) + col0);
-                if (MODE == 0) {
+                if (c + 1 < W / 64) {
 #pragma unroll
-                  for (int i4 = 0; i4 < CW / 4; ++i4) {
-                    const float4 ww = kStage ? wo[i4] : __ldg(wo + i4);
-                    dot = fmaf(v[4 * i4], ww.x, dot);
-                    dot = fmaf(v[4 * i4 + 1], ww.y, dot);
-                    dot = fmaf(v[4 * i4 + 2], ww.z, dot);
-                    dot = fmaf(v[4 * i4 + 3], ww.w, dot);
-                  }
+                  for (int k = 0; k < CW / 8; ++k)
+                    sgn[k] = store_t ? reinterpret_cast<const uint4*>(P.Sg + sg_off(l - 1, tile_t, c + 1))[k]
+                                     : make_uint4(0, 0, 0, 0);
+                }
+                if (KIND == INRCT_FFN_RELU) {
+#pragma unroll
+                  for (int i = 0; i < CW; ++i) v[i] = sg[i] > 0.f ? v[i] : 0.f;
                 } else {
-                  // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
 #pragma unroll
-                  for (int i4 = 0; i4 < CW / 4; ++i4) {
-                    const float4 ww = kStage ? wo[i4] : __ldg(wo + i4);
-                    v[4 * i4] = sv_t * ww.x * cs[4 * i4];
-                    v[4 * i4 + 1] = sv_t * ww.y * cs[4 * i4 + 1];
-                    v[4 * i4 + 2] = sv_t * ww.z * cs[4 * i4 + 2];
-                    v[4 * i4 + 3] = sv_t * ww.w * cs[4 * i4 + 3];
+                  for (int i = 0; i < CW; ++i) v[i] *= sg[i];
+                }
+              } else {
+                const float4* bl = reinterpret_cast<const float4*>(bias_s + (size_t)l * W + col0);
+                float cs[CW];
+#pragma unroll
+                for (int i4 = 0; i4 < CW / 4; ++i4) {
+                  const float4 bb = bl[i4];
+                  const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) {
+                    const int i = 4 * i4 + k;
+                    const float z = v[i] + bq[k];
+                    if (KIND == INRCT_FFN_RELU) {
+                      v[i] = fmaxf(z, 0.f);
+                      if (MODE == 1) cs[i] = z > 0.f ? 1.f : 0.f;
+                    } else if (MODE == 1) {
+                      __sincosf(z, &v[i], &cs[i]);
+                    } else {
+                      v[i] = __sinf(z);
+                    }
                   }
-                  if (store_t && c == 0 && g == 0) P.Y16o[prow_t] = __float2bfloat16_rn(sv_t);
+                }
+                if (MODE == 1 && store_t) {
+                  if (kind == kFwdHidden)  // a_l itself goes out from the panels
+                    store_row_bf16<CW>(P.Sg + sg_off(l, tile_t, c), cs);
+                  else                     // a_{L-1} is not a panel (the panels take delta_{L-1})
+                    store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
+                }
+                if (kind == kFwdLast) {
+                  const float4* wo = reinterpret_cast<const float4*>(wout_s + col0);
+                  if (MODE == 0) {
+#pragma unroll
+                    for (int i4 = 0; i4 < CW / 4; ++i4) {
+                      const float4 ww = wo[i4];
+                      dot = fmaf(v[4 * i4], ww.x, dot);
+                      dot = fmaf(v[4 * i4 + 1], ww.y, dot);
+                      dot = fmaf(v[4 * i4 + 2], ww.z, dot);
+                      dot = fmaf(v[4 * i4 + 3], ww.w, dot);
+                    }
+                  } else {
+                    // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
+#pragma unroll
+                    for (int i4 = 0; i4 < CW / 4; ++i4) {
+                      const float4 ww = wo[i4];
+                      v[4 * i4] = sv_t * ww.x * cs[4 * i4];
+                      v[4 * i4 + 1] = sv_t * ww.y * cs[4 * i4 + 1];
+                      v[4 * i4 + 2] = sv_t * ww.z * cs[4 * i4 + 2];
+                      v[4 * i4 + 3] = sv_t * ww.w * cs[4 * i4 + 3];
+                    }
+                    if (store_t && c == 0 && g == 0) P.Y16o[prow_t] = __float2bfloat16_rn(sv_t);
+                  }
                 }
               }
+              if (pub) st_panel_row<CW>(apan + (4 * t + c) * kPanelBytes, r, (CW / 8) * g, v);
             }
-            if (pub) st_panel_row<CW>(apan + (4 * t + c) * kPanelBytes, r, (CW / 8) * g, v);
           }
           if (pub) fence_async_smem();
           tc_fence_before();
@@ -968,15 +982,14 @@ size_t tile_smem_base(int mode) {
   return 8 * (size_t)kPanelBytes + (size_t)ring_bytes(mode) + 8 * (size_t)kTileBars +
          sizeof(float) * (size_t)kTileNWG * kTile;
 }
-// VJP: biases and output weights staged, and the first-layer table too when it fits
+// Biases and output weights staged, and the first-layer table too when it fits
 bool first_fits(const Net& n) {
   const size_t n_first = n.kind == INRCT_SIREN ? n.W : n.F;
   return tile_smem_base(1) + sizeof(float) * ((size_t)n.L * n.W + n.W) + 16 * n_first <= 232448;
 }
 size_t tile_smem(const Net& n, int mode = 0) {
-  if (mode == 0) return tile_smem_base(0);
   const size_t n_first = n.kind == INRCT_SIREN ? n.W : n.F;
-  return tile_smem_base(1) + sizeof(float) * ((size_t)n.L * n.W + n.W) + (first_fits(n) ? 16 * n_first : 0);
+  return tile_smem_base(mode) + sizeof(float) * ((size_t)n.L * n.W + n.W) + (first_fits(n) ? 16 * n_first : 0);
 }
 
 
