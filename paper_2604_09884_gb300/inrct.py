@@ -133,12 +133,18 @@ def _check(rc):
         raise InrctError(rc, lib().inrct_last_error().decode())
 
 
-def _ptr(t, dtype=None):
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    """Device address of t.  The library takes plain pointers, so a wrong element type, a buffer
+    shorter than the call needs, or a strided view would be read or written out of bounds: each
+    is refused here (element type and size first, so that these checks need no GPU)."""
     if t is None:
         return None
-    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
-    if dtype is not None:
-        assert t.dtype == dtype, f"expected {dtype}, got {t.dtype}"
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: {t.numel()} elements, the call needs {numel}")
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"{name}: expected a contiguous CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -228,8 +234,8 @@ def project(g: synth.GeomSpec, image: torch.Tensor, y: torch.Tensor | None = Non
     loss = torch.empty(1, dtype=torch.float64, device=dev) if y is not None else None
     nb = L.inrct_project_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
     ws = _ws(nb, dev)
-    _check(L.project(ctypes.byref(gd), ctypes.byref(grd), _ptr(image, torch.float32), _ptr(z),
-                     _ptr(y, torch.float32), _ptr(r), _ptr(loss), _ptr(ws), nb, _stream(stream)))
+    _check(L.project(ctypes.byref(gd), ctypes.byref(grd), _ptr(image, torch.float32, g.n, "image"), _ptr(z),
+                     _ptr(y, torch.float32, g.m, "y"), _ptr(r), _ptr(loss), _ptr(ws), nb, _stream(stream)))
     return z if y is None else (z, r, loss)
 
 
@@ -243,8 +249,8 @@ def project_noalloc(g: synth.GeomSpec, image: torch.Tensor, y: torch.Tensor | No
     z = torch.empty(g.m, dtype=torch.float32, device=dev)
     r = torch.empty(g.m, dtype=torch.float32, device=dev) if y is not None else None
     loss = torch.empty(1, dtype=torch.float64, device=dev) if y is not None else None
-    _check(L.project_noalloc(ctypes.byref(gd), ctypes.byref(grd), _ptr(image, torch.float32), _ptr(z),
-                             _ptr(y, torch.float32), _ptr(r), _ptr(loss), _stream(stream)))
+    _check(L.project_noalloc(ctypes.byref(gd), ctypes.byref(grd), _ptr(image, torch.float32, g.n, "image"),
+                             _ptr(z), _ptr(y, torch.float32, g.m, "y"), _ptr(r), _ptr(loss), _stream(stream)))
     return z if y is None else (z, r, loss)
 
 
@@ -256,7 +262,7 @@ def backproject(g: synth.GeomSpec, sino: torch.Tensor, stream=None) -> torch.Ten
     v = torch.empty(g.n, dtype=torch.float32, device=dev)
     nb = L.inrct_backproject_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
     ws = _ws(nb, dev)
-    _check(L.backproject(ctypes.byref(gd), ctypes.byref(grd), _ptr(sino, torch.float32), _ptr(v),
+    _check(L.backproject(ctypes.byref(gd), ctypes.byref(grd), _ptr(sino, torch.float32, g.m, "sino"), _ptr(v),
                          _ptr(ws), nb, _stream(stream)))
     return v
 
@@ -281,7 +287,7 @@ def check_index_set(d: int, N: int, idx: torch.Tensor, fov: int = 0, stream=None
     nb = L.inrct_check_index_ws_bytes(ctypes.byref(grd))
     ws = _ws(nb, idx.device)
     c = (ctypes.c_longlong * 3)()
-    _check(L.inrct_check_index_set(ctypes.byref(grd), _ptr(idx, torch.int32), idx.numel(), c, _ptr(ws), nb,
+    _check(L.inrct_check_index_set(ctypes.byref(grd), _ptr(idx, torch.int32, name="idx"), idx.numel(), c, _ptr(ws), nb,
                                    _stream(stream)))
     return {"out_of_range": c[0], "outside_fov": c[1], "repeats": c[2]}
 
@@ -313,7 +319,7 @@ def ramp_filter(g: synth.GeomSpec, r: torch.Tensor, stream=None):
     loss = torch.empty(1, dtype=torch.float64, device=r.device)
     nb = L.inrct_ramp_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
     ws = _ws(nb, r.device)
-    _check(L.ramp_filter(ctypes.byref(gd), ctypes.byref(grd), _ptr(r, torch.float32), _ptr(out),
+    _check(L.ramp_filter(ctypes.byref(gd), ctypes.byref(grd), _ptr(r, torch.float32, g.m, "r"), _ptr(out),
                          _ptr(loss), _ptr(ws), nb, _stream(stream)))
     return out, loss
 
@@ -325,7 +331,7 @@ def inr_eval_grid(mlp: MlpHandle, theta: torch.Tensor, N: int, stream=None, fov:
     img = torch.empty(N ** mlp.spec.d, dtype=torch.float32, device=theta.device)
     nb = L.inrct_eval_ws_bytes(ctypes.byref(mlp.desc), ctypes.byref(grd))
     ws = _ws(nb, theta.device)
-    _check(L.inr_eval_grid(ctypes.byref(mlp.desc), _ptr(theta, torch.float32), ctypes.byref(grd),
+    _check(L.inr_eval_grid(ctypes.byref(mlp.desc), _ptr(theta, torch.float32, mlp.p, "theta"), ctypes.byref(grd),
                            _ptr(img), _ptr(ws), nb, _stream(stream)))
     return img
 
@@ -341,8 +347,9 @@ def inr_weighted_vjp(mlp: MlpHandle, theta: torch.Tensor, N: int, idx: torch.Ten
     g32 = torch.empty(mlp.p, dtype=torch.float32, device=dev) if want_f32 else None
     nb = L.inrct_vjp_ws_bytes(ctypes.byref(mlp.desc), ctypes.byref(grd), idx.numel())
     ws = _ws(nb, dev)
-    _check(L.inr_weighted_vjp(ctypes.byref(mlp.desc), _ptr(theta, torch.float32), ctypes.byref(grd),
-                              _ptr(idx, torch.int32), idx.numel(), _ptr(v, torch.float32),
+    _check(L.inr_weighted_vjp(ctypes.byref(mlp.desc), _ptr(theta, torch.float32, mlp.p, "theta"),
+                              ctypes.byref(grd), _ptr(idx, torch.int32, name="idx"), idx.numel(),
+                              _ptr(v, torch.float32, N ** mlp.spec.d, "v"),
                               float(scale), _ptr(g64), _ptr(g32), _ptr(ws), nb, _stream(stream)))
     return (g64, g32) if want_f32 else g64
 
@@ -363,11 +370,14 @@ def grad_step(g: synth.GeomSpec, mlp: MlpHandle, theta: torch.Tensor, y: torch.T
     gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     if ws is None:
         ws = _ws(step_ws_bytes(g, mlp, idx.numel()), theta.device)
+    p = mlp.p
     _check(L.grad_step(ctypes.byref(gd), ctypes.byref(grd), ctypes.byref(mlp.desc), loss_kind,
-                       _ptr(theta, torch.float32), _ptr(y, torch.float32), _ptr(idx, torch.int32),
-                       idx.numel(), float(scale), ctypes.byref(adam) if adam is not None else None,
-                       _ptr(m), _ptr(s), _ptr(loss_out), _ptr(grad_out), _ptr(ws), ws.numel(),
-                       _stream(stream)))
+                       _ptr(theta, torch.float32, p, "theta"), _ptr(y, torch.float32, g.m, "y"),
+                       _ptr(idx, torch.int32, name="idx"), idx.numel(), float(scale),
+                       ctypes.byref(adam) if adam is not None else None,
+                       _ptr(m, torch.float32, p, "m"), _ptr(s, torch.float32, p, "s"),
+                       _ptr(loss_out, torch.float64, 1, "loss_out"), _ptr(grad_out, torch.float64, p, "grad_out"),
+                       _ptr(ws, torch.uint8, name="ws"), ws.numel(), _stream(stream)))
 
 
 class Batch:
@@ -385,11 +395,16 @@ class Batch:
         arr = (Problem * len(problems))()
         for k, q in enumerate(problems):
             g = q["geom"]
-            arr[k] = Problem(geom_desc(g), grid_desc(g.d, g.N, g.fov), _ptr(q["theta"], torch.float32).value,
-                             _ptr(q["y"], torch.float32).value, _ptr(q["idx"], torch.int32).value,
-                             q["idx"].numel(), float(q["scale"]), _ptr(q["m"], torch.float32).value,
-                             _ptr(q["s"], torch.float32).value,
-                             _ptr(q["loss"], torch.float64).value if q.get("loss") is not None else None)
+            p = mlp.p
+            arr[k] = Problem(geom_desc(g), grid_desc(g.d, g.N, g.fov),
+                             _ptr(q["theta"], torch.float32, p, f"problem {k} theta").value,
+                             _ptr(q["y"], torch.float32, g.m, f"problem {k} y").value,
+                             _ptr(q["idx"], torch.int32, name=f"problem {k} idx").value,
+                             q["idx"].numel(), float(q["scale"]),
+                             _ptr(q["m"], torch.float32, p, f"problem {k} m").value,
+                             _ptr(q["s"], torch.float32, p, f"problem {k} s").value,
+                             _ptr(q["loss"], torch.float64, 1, f"problem {k} loss").value
+                             if q.get("loss") is not None else None)
         self._arr = arr
         nb = L.inrct_batch_ws_bytes(ctypes.byref(mlp.desc), arr, len(problems))
         if nb == 0:
@@ -421,7 +436,7 @@ def sincospi(x: torch.Tensor, stream=None):
     """Diagnostic: (sin(pi x), cos(pi x)) as the FFN feature code computes them (x in [-1, 1])."""
     sn = torch.empty_like(x)
     cs = torch.empty_like(x)
-    _check(lib().inrct_sincospi(_ptr(x, torch.float32), _ptr(sn), _ptr(cs), x.numel(), _stream(stream)))
+    _check(lib().inrct_sincospi(_ptr(x, torch.float32, name="x"), _ptr(sn), _ptr(cs), x.numel(), _stream(stream)))
     return sn, cs
 
 
@@ -433,7 +448,8 @@ def gemm_tn(X: torch.Tensor, Y: torch.Tensor | None, Y16: torch.Tensor | None, s
     C = torch.empty(M, N + 32, dtype=torch.float32, device=X.device)
     nb = L.inrct_gemm_tn_ws_bytes(K, M, N)
     ws = _ws(nb, X.device)
-    _check(L.inrct_gemm_tn(_ptr(X, torch.bfloat16), _ptr(Y, torch.bfloat16), _ptr(Y16, torch.bfloat16),
+    _check(L.inrct_gemm_tn(_ptr(X, torch.bfloat16, name="X"), _ptr(Y, torch.bfloat16, K * N, "Y"),
+                           _ptr(Y16, torch.bfloat16, 16 * K, "Y16"),
                            K, M, N, _ptr(C), _ptr(ws), nb, _stream(stream)))
     return C
 

@@ -217,3 +217,22 @@ def test_index_set_check_refuses_on_the_host(L):
     assert L.inrct_check_index_set(ctypes.byref(grd), _fake(), 10, c, _fake(), nb - 256, None) == 3
     bad = inrct.grid_desc(2, 64, 3)
     assert L.inrct_check_index_set(ctypes.byref(bad), _fake(), 10, c, _fake(), nb, None) == 1
+
+
+def test_binding_refuses_wrong_buffers_before_any_launch(L):
+    """The library takes plain pointers; the binding refuses a wrong element type, a buffer
+    shorter than the call needs and a non-CUDA or strided tensor (no GPU is touched)."""
+    with pytest.raises(TypeError, match="theta"):
+        inrct._ptr(torch.zeros(8, dtype=torch.float64), torch.float32, 8, "theta")
+    with pytest.raises(ValueError, match="7 elements"):
+        inrct._ptr(torch.zeros(7), torch.float32, 8, "m")
+    with pytest.raises(ValueError, match="contiguous CUDA"):
+        inrct._ptr(torch.zeros(8), torch.float32, 8, "s")
+    assert inrct._ptr(None, torch.float32, 8, "grad_out") is None
+    g = synth.GeomSpec("par2d", 16, 6, 23)
+    with pytest.raises(TypeError, match="image"):
+        inrct.project(g, torch.zeros(g.n, dtype=torch.float64))
+    with pytest.raises(ValueError, match="image"):
+        inrct.project(g, torch.zeros(g.n - 1))
+    with pytest.raises(ValueError, match="sino"):
+        inrct.backproject(g, torch.zeros(g.m - 1))
