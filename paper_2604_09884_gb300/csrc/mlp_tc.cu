@@ -3,20 +3,20 @@
 //
 // Fused MLP tile engine (mlp_tile_kernel)
 // ---------------------------------------
-// A persistent CTA walks tiles of 128 points.  Per tile it runs a program of
-// GEMM stages, each D[128 x W] = A[128 x K] * B[W x K]^T with A the stage
-// input (BF16, in shared memory, K-major 64-column panels) and B a weight
-// matrix streamed by TMA through a 4-slot ring; D accumulates in FP32 in
-// tensor memory (two W-column buffers, so stage s+1 accumulates while the
-// epilogue still reads stage s).  Warp roles:
-//   warps 0-7  epilogue: build the first input (Fourier features or the
-//              SIREN first layer, FP32 on the CUDA cores), then after every
-//              stage read D from TMEM, add the bias, apply the activation
-//              (FP32), re-stage the result as the next stage's BF16 A panels.
-//              Panel c of the next stage is released as soon as it is written,
-//              so the next stage's MMAs overlap the rest of the epilogue.
-//   warp 8     TMA producer of the weight ring.
-//   warp 9     MMA issuer (one elected thread).
+// A persistent CTA (one per SM) walks tiles of 128 points, two at a time (slots 0
+// and 1).  Per tile it runs a program of GEMM stages, each
+// D[128 x W] = A[128 x K] * B[W x K]^T with A the stage input (BF16, in shared
+// memory, K-major 64-column panels) and B a weight matrix streamed by TMA through
+// a 64 KB ring of 64-column chunks; D accumulates in FP32 in tensor memory, one
+// W-column accumulator per slot, so the tensor core works on one slot while the
+// epilogue drains the other.  Warp roles (18 warps):
+//   warps 0-15  epilogue: build the first input (Fourier features or the SIREN
+//               first layer, FP32 on the CUDA cores), then after every stage read
+//               D from TMEM, add the bias, apply the activation (FP32) and write
+//               the next stage's BF16 A panels; the small parameter tables are
+//               staged in shared memory.
+//   warp 16     TMA producer of the weight ring.
+//   warp 17     MMA issuer (one thread).
 // SIREN layers keep omega0 folded into their BF16 weights and FP32 biases
 // (u = omega0 (W h + b) = W' h + b'), so the epilogue applies sin(u).
 //
