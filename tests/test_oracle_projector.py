@@ -316,3 +316,21 @@ def test_view_subsets_partition_the_rays(kind):
         total += O.backproject(sub, O.project(sub, x) - ys)
     ref = O.backproject(full, O.project(full, x) - y)
     assert np.allclose(total, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("kind", ["par2d", "cone3d"])
+def test_fls_loss_gradient_matches_central_differences(kind):
+    """The gradient fls_loss returns, F (z - y), against central differences of the loss value
+    itself (Sec. 3's filtered least squares; F from the band-limited ramp)."""
+    g = O.Geometry("par2d", 16, 3, 23) if kind == "par2d" else O.Geometry("cone3d", 8, 2, 9, 5, sod=40.0,
+                                                                           sdd=60.0)
+    rng = np.random.default_rng(11)
+    z, y = rng.normal(size=g.m), rng.normal(size=g.m)
+    _, grad = O.fls_loss(g, z, y)
+    h = 1e-6
+    for j in rng.choice(g.m, 12, replace=False):
+        zp, zm = z.copy(), z.copy()
+        zp[j] += h
+        zm[j] -= h
+        fd = (O.fls_loss(g, zp, y)[0] - O.fls_loss(g, zm, y)[0]) / (2 * h)
+        assert abs(fd - grad[j]) <= 1e-6 * max(1.0, abs(grad[j])), (j, fd, grad[j])
