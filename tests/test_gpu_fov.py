@@ -113,3 +113,34 @@ def test_index_set_check_counts():
     assert c1 == {"out_of_range": 4, "outside_fov": int((~O.fov_mask(2, N, valid)).sum()), "repeats": 7}
     assert inrct.check_index_set(3, 20, cuda(np.arange(8000), torch.int32)) == {"out_of_range": 0, "outside_fov": 0,
                                                                              "repeats": 0}
+
+
+CASES3 = [(synth.ArchSpec("siren", 3, 128, 3, omega0=30.0), inrct.BF16),
+          (synth.ArchSpec("ffn", 3, 128, 2, n_feat=32, sigma=3.0), inrct.BF16),
+          (synth.ArchSpec("siren", 3, 64, 2, omega0=30.0), inrct.FP32),
+          (synth.ArchSpec("hash", 3, 64, 2, hash_levels=4, hash_feats=2, hash_log2_T=12, hash_base=4,
+                          hash_growth=1.6), inrct.FP32)]
+
+
+@pytest.mark.parametrize("case", CASES3, ids=lambda c: f"{c[0].kind}3d_{'bf16' if c[1] else 'fp32'}")
+def test_three_d_field_of_view_is_a_cylinder(case):
+    """3-D grids: E{f} is zero outside the cylinder (the disk test on x, y of every z slice) and
+    the oracle's inside it, and listed points outside it carry no weight in the VJP."""
+    spec, prec = case
+    N = 24
+    n = N ** 3
+    oa, B32, theta = pair(spec, 5)
+    h = inrct.mlp_desc(spec, prec, B32)
+    img = inrct.inr_eval_grid(h, cuda(theta), N, fov=1).cpu().numpy()
+    m = O.fov_mask(3, N)
+    assert np.all(img[~m] == 0.0) and 0 < m.sum() < n
+    sel = np.flatnonzero(m)[::7]
+    want = O.forward(oa, theta.astype(np.float64), O.grid_coords(3, N, sel), N=N)
+    assert rel(img[sel], want) <= (2e-2 if prec == inrct.BF16 else 1e-5)
+    v = cuda(np.random.default_rng(6).normal(size=n))
+    idx = synth.index_set(n, 3000, 7)
+    inside = idx[O.fov_mask(3, N, idx)]
+    assert 0 < inside.size < idx.size
+    a = inrct.inr_weighted_vjp(h, cuda(theta), N, cuda(idx, torch.int32), v, 1.5, fov=1).cpu().numpy()
+    b = inrct.inr_weighted_vjp(h, cuda(theta), N, cuda(inside, torch.int32), v, 1.5, fov=1).cpu().numpy()
+    assert rel(a, b) <= 1e-6
