@@ -140,3 +140,38 @@ def test_grad_step_fls_fp32_matches_oracle():
     assert abs(loss.item() - Lf) <= 1e-4 * abs(Lf)
     assert rel(grad.cpu().numpy(), want) <= 1e-4
     np.testing.assert_array_equal(th.cpu().numpy(), theta)      # no Adam: theta untouched
+
+
+def test_adam_state_over_three_steps_matches_the_oracle():
+    """Adam inside grad_step over t = 1, 2, 3: after every step theta, m and s equal the oracle's
+    bias-corrected FP64 Adam applied to the kernel's own gradient of that step (the moments
+    accumulate and the bias correction changes with t; the first step alone cannot show either)."""
+    w = synth.workloads()["par2d_128_ffn64"]
+    g, spec = w.geom, w.arch
+    oa, B32 = arch_pair(spec, 7)
+    og = O.Geometry(g.kind, g.N, g.V, g.A, g.B, g.du, g.dv, g.sod, g.sdd, g.angle0, g.span)
+    theta = synth.init_theta(spec, 8).astype(np.float32)
+    y = synth.noisy(O.project(og, synth.phantom(2, g.N, 10, 9)), 0.01, 10).astype(np.float32)
+    idx = synth.index_set(g.n, g.n // 4, 12)
+    h = inrct.mlp_desc(spec, inrct.FP32, B32)
+    th = cuda(theta)
+    m = torch.zeros_like(th)
+    s = torch.zeros_like(th)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.zeros(spec.p, dtype=torch.float64, device="cuda")
+    st = O.AdamState(np.zeros(spec.p), np.zeros(spec.p))
+    for t in (1, 2, 3):
+        before = th.double().cpu().numpy()
+        inrct.grad_step(g, h, th, cuda(y), cuda(idx, torch.int32), g.n / idx.size, inrct.adam(lr=1e-3, t=t),
+                        m, s, loss, grad)
+        torch.cuda.synchronize()
+        want = O.adam_step(before, grad.cpu().numpy(), st, lr=1e-3)
+        # FP32 state against FP64: norm-wise (single entries lose relative accuracy where the
+        # moment's two terms cancel); the kernel applies beta2 = 0.999 as an FP32 value, which
+        # puts 1 - beta2 1.3e-5 (relative) off.  A wrong bias correction is off by a factor.
+        assert rel(m.double().cpu().numpy(), st.m) <= 1e-6
+        assert rel(s.double().cpu().numpy(), st.s) <= 5e-5
+        step = th.double().cpu().numpy() - before
+        assert rel(step, want - before) <= 5e-5
+        # and entry by entry, up to half an ulp of the FP32 theta (|theta| < 0.5 here)
+        np.testing.assert_allclose(step, want - before, rtol=1e-3, atol=3e-8)
