@@ -149,7 +149,10 @@ typedef struct {
   double hash_growth; /* per-level growth factor, 1 <= hash_growth <= 4, N_l <= 2^20 */
 } inrct_mlp;
 
-/* Adam hyper-parameters; t is the 1-based index of the step being taken. */
+/* Adam hyper-parameters (Sec. 4 trains with Adam; Kingma-Ba with bias correction); t is
+ * the 1-based index of the step being taken.  Both bias corrections are folded into the step
+ * size and epsilon in FP64; theta, m and s are then updated in FP32 with beta1 and beta2 taken
+ * as FP32 values. */
 typedef struct {
   double lr, beta1, beta2, eps;
   int64_t t;
