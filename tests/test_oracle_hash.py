@@ -131,3 +131,26 @@ def test_table_gradient_equals_central_differences():
         tp[j] += h
         tm[j] -= h
         assert abs((f(tp) - f(tm)) / (2 * h) - g[j]) <= 1e-8 * max(1.0, abs(g[j]))
+
+
+def test_three_d_table_gradient_equals_central_differences():
+    """The 3-D reverse mode (eight trilinear corners per level, dense and hashed levels) against
+    central differences of the forward pass in table entries and in MLP weights."""
+    arch = _arch(3, hash_levels=3, hash_log2_T=7, hash_base=2, hash_growth=2.5)  # N_l 2 dense; 5, 12 hashed
+    N = 6
+    theta = _theta(arch, 9) * 0.3
+    I = np.arange(N ** 3)
+    X = O.grid_coords(3, N, I)
+    w = np.random.default_rng(10).normal(size=I.size)
+    g = O.vjp(arch, theta, X, w, N=N)
+    f = lambda t: float(w @ O.forward(arch, t, X, N=N))
+    rng = np.random.default_rng(11)
+    touched = np.flatnonzero(g[:arch.table_params])
+    picks = np.concatenate([rng.choice(touched, 16, replace=False),
+                            arch.table_params + rng.choice(arch.p - arch.table_params, 8, replace=False)])
+    for j in picks:
+        h = 1e-4
+        tp, tm = theta.copy(), theta.copy()
+        tp[j] += h
+        tm[j] -= h
+        assert abs((f(tp) - f(tm)) / (2 * h) - g[j]) <= 1e-8 * max(1.0, abs(g[j])), j
