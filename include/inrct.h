@@ -197,13 +197,17 @@ int project(const inrct_geom* geom, const inrct_grid* grid, const float* image, 
  *   A geometry whose scratch (inrct_project_ws_bytes) exceeds the array is
  *   rejected with INRCT_ERR_WORKSPACE before anything is launched (2-D
  *   geometries up to about 1400^2 pixels fit; most 3-D ones do not).
- *   The first call on a device looks up the array's device address on that
- *   device (the device that is current at the call); make that first call
- *   before any stream capture.  All calls on a device share the one array:
- *   calls whose work overlaps on the GPU (different streams, or host threads
+ *   Every call made outside stream capture looks up the array's device address
+ *   on the device that is current at the call; a call made during stream
+ *   capture uses the address found by an earlier call on that device, so make
+ *   the first call on a device before any stream capture (otherwise
+ *   INRCT_ERR_INVALID_ARG).  All calls on a device share the one array: calls
+ *   whose work overlaps on the GPU (different streams, or host threads
  *   without ordering) race on it and must be serialised by the caller.  The
- *   array keeps the last call's contents; each call writes every scratch byte
- *   it later reads, so no clearing is needed.
+ *   array keeps the last call's contents.  A call reuses the ray tables an
+ *   earlier call left there only if they were completely built for the same
+ *   geometry (a fingerprint written after the build, checked on the device);
+ *   everything else it reads it writes first, so no clearing is needed.
  */
 #define INRCT_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int project_noalloc(const inrct_geom* geom, const inrct_grid* grid, const float* image, float* sino,

@@ -80,7 +80,7 @@ def _L():
 
 
 # ----------------------------------------------------------------------------
-# Geometry (Sec. 3: P in R^{m x n}; conventions are readings, listed in DESIGN)
+# Geometry (Sec. 3: P in R^{m x n}; the paper fixes no scan conventions, these are readings)
 # ----------------------------------------------------------------------------
 @dataclass
 class Geometry:

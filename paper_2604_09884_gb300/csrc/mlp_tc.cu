@@ -1217,7 +1217,7 @@ int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image,
     INRCT_TRY(prep_weights(n, theta, w, st));
   }
   cudaMemsetAsync(err, 0, sizeof(int), st);
-  static Maps maps;
+  Maps maps;  // per call: the kernel takes a copy at launch
   TileProg P;
   INRCT_TRY(build_prog(n, w, 0, &P, &maps));
   P.theta = theta;
@@ -1384,7 +1384,7 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
   } else {
     INRCT_TRY(prep_weights(n, theta, w.w, st));
   }
-  static Maps tmaps, gmaps;
+  Maps tmaps, gmaps;  // per call: each launch takes a copy
   TileProg P;
   INRCT_TRY(build_prog(n, w.w, 1, &P, &tmaps));
   P.theta = theta;
@@ -1520,7 +1520,7 @@ int gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int
     set_error("gemm_tn: workspace of %zu bytes too small (need %zu)", ws_bytes, gemm_tn_ws_bytes(K, M, N));
     return INRCT_ERR_WORKSPACE;
   }
-  static Maps maps;
+  Maps maps;
   INRCT_TRY(make_map(&maps.m[0], X, M, K, 64, 64));
   if (N > 0) INRCT_TRY(make_map(&maps.m[1], Y, N, K, 64, 64));
   if (Y16) INRCT_TRY(make_map(&maps.m[2], Y16, K, 16, 64, 16));

@@ -1235,17 +1235,26 @@ static __device__ __align__(256) unsigned char g_project_scratch[INRCT_NOALLOC_S
 static std::mutex g_project_scratch_mu;
 static void* g_project_scratch_addr[256] = {};  // device address of the array, per device ordinal
 
-// Device address of the array on the current device, looked up once per device
-// (host code cannot use the array's name as a device pointer).
-static int project_scratch_address(void** out) {
+// Device address of the array on the current device.  Host code cannot use the array's
+// name as a device pointer, so the address is looked up with cudaGetSymbolAddress: on every
+// call outside stream capture (the lookup is cheap, and a device reset or a re-created primary
+// context then never leaves a stale address behind), and from the per-device cache while the
+// stream is being captured (where the lookup is not allowed to run).
+static int project_scratch_address(cudaStream_t st, void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 256) {
     set_error("project_noalloc: no usable current device (%s)", cudaGetErrorString(e));
     return INRCT_ERR_CUDA;
   }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
   std::lock_guard<std::mutex> lk(g_project_scratch_mu);
-  if (!g_project_scratch_addr[dev]) {
+  if (!capturing || !g_project_scratch_addr[dev]) {
+    if (capturing) {
+      set_error("project_noalloc: the first call on a device must not be made during stream capture");
+      return INRCT_ERR_INVALID_ARG;
+    }
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_project_scratch);
     if (e != cudaSuccess || !p) {
@@ -1269,9 +1278,13 @@ int project_noalloc_impl(const inrct_geom* geom, const inrct_grid* grid, const f
     return INRCT_ERR_WORKSPACE;
   }
   void* ws = nullptr;
-  INRCT_TRY(project_scratch_address(&ws));
-  // every byte of scratch the projection reads is written earlier in the same call
-  // (tables, transposed image, loss partials), so nothing needs clearing
+  INRCT_TRY(project_scratch_address(st, &ws));
+  // What the projection reads from the array: the ray tables, the transposed image and the
+  // loss partials.  The last two are written earlier in the same call.  Ray tables left by an
+  // earlier call are reused only when both seals around the table region carry this
+  // geometry's fingerprint (written by the last block of a completed build); any other
+  // geometry, or tables overwritten in between, fail that check and are rebuilt first.  So
+  // nothing needs clearing.
   return project_impl(geom, grid, image, sino, y, resid, loss_out, ws,
                       (size_t)INRCT_NOALLOC_SCRATCH_BYTES, st);
 }

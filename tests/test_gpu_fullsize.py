@@ -45,7 +45,7 @@ def kink_free(oa, theta, X, N):
     _, _, zs, _ = O.forward(oa, np.asarray(theta, np.float64), X, keep=True, N=N)
     ok = np.ones(len(X), bool)
     for z in zs[:-1]:
-        ok &= (np.abs(z) >= 1e-4 * np.sqrt((z ** 2).mean())).all(axis=1)
+        ok &= (np.abs(z) >= 1e-6 * np.sqrt((z ** 2).mean())).all(axis=1)
     return ok
 
 

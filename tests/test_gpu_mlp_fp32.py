@@ -31,7 +31,7 @@ def arch_pair(spec: synth.ArchSpec, seed=0):
     return oa, B32
 
 
-def kink_free(oa, theta, X, tau=1e-4):
+def kink_free(oa, theta, X, tau=1e-6):
     """Points whose ReLU pre-activations all stay at least tau * rms away from 0.
 
     Where |z| is within rounding of the kink, FP32 and FP64 can take different

@@ -60,6 +60,26 @@ def test_project_noalloc_matches_project_on_two_calls(g):
         assert abs(loss.item() - l_ref.item()) <= TOL * abs(l_ref.item())
 
 
+def test_project_noalloc_after_a_different_geometry():
+    """The second call uses another geometry than the first: ray tables left in the shared array
+    by the first call must not be taken for the second one's (a missing rebuild would change z)."""
+    dev = torch.device("cuda")
+    geoms = [synth.GeomSpec("fan2d", 512, 90, 729, sod=1000.0, sdd=1500.0, span=2 * math.pi),
+             synth.GeomSpec("par2d", 128, 60, 183),
+             synth.GeomSpec("fan2d", 512, 90, 729, sod=1000.0, sdd=1500.0, span=2 * math.pi)]
+    for call, g in enumerate(geoms):
+        x = torch.tensor(synth.phantom(2, g.N, 5, seed=60 + call).reshape(-1), dtype=torch.float32,
+                         device=dev)
+        y = torch.tensor(synth.uniform(g.m, seed=70 + call, lo=0.0, hi=2.0), dtype=torch.float32,
+                         device=dev)
+        z_ref, r_ref, l_ref = inrct.project(g, x, y)
+        z, r, loss = _call_noalloc(g, x, y)
+        torch.cuda.synchronize()
+        assert rel(z, z_ref) <= TOL, call
+        assert rel(r, r_ref) <= TOL, call
+        assert abs(loss.item() - l_ref.item()) <= TOL * abs(l_ref.item()), call
+
+
 def test_project_noalloc_rejects_geometry_beyond_its_buffer():
     g = synth.GeomSpec("cone3d", 256, 40, 384, 384, sod=1000.0, sdd=1500.0, span=2 * math.pi)
     L = inrct.lib()
