@@ -268,6 +268,20 @@ int inr_weighted_vjp(const inrct_mlp* mlp, const float* theta, const inrct_grid*
                      cudaStream_t stream);
 
 /*
+ * inr_virtual_loss -- the virtual loss of Eq. 3 together with its gradient (Eq. 2):
+ *   value_out[0] = scale * sum_{k < n_idx} v[idx[k]] f(x_{idx[k]})   (FP64 device scalar,
+ *   overwritten), and grad_f64 / grad_f32 exactly as inr_weighted_vjp.
+ *   The value comes from the forward pass that the VJP already runs at the listed points
+ *   (v is held constant, as in Eq. 3), so it costs one small reduction more than
+ *   inr_weighted_vjp.  Arguments, workspace (inrct_vjp_ws_bytes), index semantics and
+ *   errors as inr_weighted_vjp; value_out must not be NULL.
+ */
+int inr_virtual_loss(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid,
+                     const int32_t* idx, int64_t n_idx, const float* v, double scale,
+                     double* value_out, double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes,
+                     cudaStream_t stream);
+
+/*
  * grad_step -- Algorithm 1 followed by one Adam update (Sec. 4 trains with Adam):
  *   x = E{f_theta}; z = P x; r = dL/dz; v = P^T r; g = scale * sum_{i in I} v_i grad f(x_i);
  *   theta <- Adam(theta, g).
@@ -386,6 +400,35 @@ int inrct_tune_plan(const inrct_geom* geom, const inrct_grid* grid, int* seg, in
                     int* zc, int* tuned);
 int inrct_tune_set(const inrct_geom* geom, const inrct_grid* grid, int seg, int bp_splits, int zc);
 int inrct_tune_reset(void);
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Device-side failure reporting (not part of the method).  Every wait of the
+ * tensor-core kernels (the BF16 path of inr_eval_grid, inr_weighted_vjp,
+ * inr_virtual_loss, grad_step, grad_step_batched, and inrct_gemm_tn) on an mbarrier is
+ * bounded: when a wait runs past the limit, the kernel records a code in a status word
+ * of the device, stops its other roles, waits (bounded) for its own copies and MMAs in
+ * flight, releases its tensor memory and returns, so the context stays usable; the
+ * call itself has already returned INRCT_OK (launches are asynchronous).
+ *
+ * inrct_device_status synchronises `stream`, then reads and clears the status word of
+ * the current device: INRCT_OK if no wait gave up since the last check, else
+ * INRCT_ERR_TIMEOUT (inrct_last_error names the kernel role and the code: 1xx
+ * weight-gradient GEMM, 2xx weight producer, 3xx MMA issuer, 4xx epilogue), and the
+ * outputs of the tensor-core calls since the last check must be discarded.
+ * INRCT_ERR_CUDA for code 901 (a kernel found its shared memory misaligned and did
+ * nothing) or a failing CUDA call.
+ *
+ * inrct_set_wait_limit sets the limit of every bounded wait of later launches, in
+ * nanoseconds (process-wide; 0 restores the default of one second).
+ *
+ * inrct_debug_stall_weight_loads is a test hook: while on (process-wide), the
+ * tensor-core tile kernel issues no weight loads, so its MMA issuer's first wait runs
+ * out.  With nothing in flight this is the safe way to exercise the timeout path.
+ */
+int inrct_device_status(cudaStream_t stream);
+int inrct_set_wait_limit(unsigned long long ns);
+int inrct_debug_stall_weight_loads(int on);
 
 /* ------------------------------------------------------------------------ */
 /* Instrumentation (host-side, not part of the method) */

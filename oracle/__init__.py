@@ -227,19 +227,6 @@ def fov_indices(g) -> np.ndarray:
     return idx[fov_mask(g.d, g.N, idx)] if g.fov else idx
 
 
-def grid_coords_fp32(d: int, N: int, idx=None) -> np.ndarray:
-    """The pixel centres as an FP32 kernel forms them, for decisions only: the
-    FP32 value nearest (2k + 1 - N) / N (FP64 division, then FP32)."""
-    if idx is None:
-        idx = np.arange(N ** d, dtype=np.int64)
-    idx = np.asarray(idx, dtype=np.int64)
-    c = lambda k: ((2 * k + 1 - N) / N).astype(np.float32)
-    cols = [c(idx % N), c((idx // N) % N)]
-    if d == 3:
-        cols.append(c(idx // (N * N)))
-    return np.stack(cols, axis=1)
-
-
 # ----------------------------------------------------------------------------
 # INR f_theta (Sec. 4: Fourier-feature ReLU networks and SIREN)
 # ----------------------------------------------------------------------------
@@ -384,49 +371,12 @@ def encode(arch: Arch, X: np.ndarray, theta=None, N: int | None = None) -> np.nd
     return X
 
 
-def bf16_round(a) -> np.ndarray:
-    """Round to the nearest bfloat16 (ties to even), as float64 values."""
-    f = np.asarray(a, dtype=np.float64).astype(np.float32)
-    b = f.view(np.uint32).astype(np.uint64)
-    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
-    return b.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
-def _fp32_features(arch: Arch, X32: np.ndarray) -> np.ndarray:
-    """The Fourier features as an FP32 kernel forms them, for mask decisions only:
-    FP32 coordinates (``grid_coords_fp32``), phase B.x with each product and sum
-    rounded to FP32 (x, then y, then z), reduced to t = ph - rint(ph), then
-    cos / sin(2 pi t) rounded to FP32."""
-    x = np.asarray(X32, dtype=np.float32)
-    B = np.asarray(arch.B, dtype=np.float64).astype(np.float32)
-    ph = (x[:, 0:1] * B[None, :, 0]).astype(np.float32) + (x[:, 1:2] * B[None, :, 1]).astype(np.float32)
-    ph = ph.astype(np.float32)
-    if arch.d == 3:
-        ph = (ph + (x[:, 2:3] * B[None, :, 2]).astype(np.float32)).astype(np.float32)
-    t = (ph - np.rint(ph)).astype(np.float32)
-    a = np.pi * (2.0 * t.astype(np.float64))
-    return np.concatenate([np.cos(a).astype(np.float32), np.sin(a).astype(np.float32)], axis=1)
-
-
-def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | None = None,
-            X32: np.ndarray | None = None, N: int | None = None):
+def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, N: int | None = None):
     """f_theta(x_i) for every row of X.  With keep=True also returns the
-    per-layer inputs h_{l-1}, pre-activations z_l and ReLU masks used by ``vjp``.
-
-    ReLU masks are decisions that floating point takes.  decide=None takes them
-    on the FP64 pre-activations.  decide='bf16' takes them as a BF16 tensor-core
-    kernel does: on pre-activations formed from BF16-rounded weights and
-    BF16-rounded layer inputs (accumulated wide, bias added unrounded), starting
-    from the FP32 features of ``_fp32_features``, the rounded chain being
-    carried alongside; every value stays FP64 and the ReLU output is mask * z.
-    X32 gives the FP32 coordinates of the decision chain (default: X rounded).
-    """
+    per-layer inputs h_{l-1}, pre-activations z_l and ReLU masks used by ``vjp``
+    (a mask is z > 0, decided on the FP64 pre-activation)."""
     layers = unpack(arch, theta)
     h = encode(arch, X, theta, N)
-    zds = None
-    if decide == "bf16" and arch.kind == "ffn":
-        X32 = np.asarray(X).astype(np.float32) if X32 is None else X32
-        zds = bf16_decision_preacts(arch, theta, X32)
     hs, zs, masks = [h], [], []
     for li, (W, b) in enumerate(layers):
         z = h @ W.T + b
@@ -434,7 +384,7 @@ def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | 
         if li == len(layers) - 1:
             h = z
         elif arch.kind in ("ffn", "hash"):
-            m = zds[li] > 0.0 if zds is not None else z > 0.0
+            m = z > 0.0
             masks.append(m)
             h = np.where(m, z, 0.0)
         else:
@@ -444,43 +394,14 @@ def forward(arch: Arch, theta, X: np.ndarray, keep: bool = False, decide: str | 
     return (f, hs, zs, masks) if keep else f
 
 
-def bf16_decision_preacts(arch: Arch, theta, X32: np.ndarray) -> list:
-    """The pre-activations on which a BF16 tensor-core kernel decides the ReLU masks of an
-    FFN (``forward``'s decide='bf16'): layer inputs and weights rounded to BF16, products
-    accumulated wide, bias added unrounded, starting from the FP32 features of
-    ``_fp32_features``; returns one [points, width] array per hidden layer."""
-    layers = unpack(arch, theta)
-    hd = bf16_round(_fp32_features(arch, np.asarray(X32, dtype=np.float32)))
-    out = []
-    for W, b in layers[:-1]:
-        zd = hd @ bf16_round(W).T + b
-        out.append(zd)
-        hd = bf16_round(np.where(zd > 0.0, zd, 0.0))
-    return out
-
-
-def bf16_decision_margins(arch: Arch, theta, X32: np.ndarray) -> np.ndarray:
-    """Per point, the smallest |pre-activation| of the BF16 decision chain over all hidden
-    units, in units of its layer's RMS over the given points.  Where it is tiny, sums of the
-    same BF16 operands accumulated in another order (FP32 tensor cores against FP64 here)
-    can round a value differently and flip a mask: both decisions are then valid."""
-    m = None
-    for zd in bf16_decision_preacts(arch, theta, X32):
-        r = (np.abs(zd) / np.sqrt((zd ** 2).mean())).min(axis=1)
-        m = r if m is None else np.minimum(m, r)
-    return m
-
-
-def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray, decide: str | None = None,
-        X32: np.ndarray | None = None, N: int | None = None) -> np.ndarray:
+def vjp(arch: Arch, theta, X: np.ndarray, w: np.ndarray, N: int | None = None) -> np.ndarray:
     """sum_i w_i grad_theta f_theta(x_i), by reverse mode written out layer by layer.
 
     This is the Jacobian-transpose product [d E{f}/d theta]^T w of Sec. 3.
-    ReLU'(0) is taken as 0; ``decide`` picks how ReLU masks are decided (see
-    ``forward``).
+    ReLU'(0) is taken as 0.
     """
     layers = unpack(arch, theta)
-    _, hs, zs, masks = forward(arch, theta, X, keep=True, decide=decide, X32=X32, N=N)
+    _, hs, zs, masks = forward(arch, theta, X, keep=True, N=N)
     w = np.asarray(w, dtype=np.float64)
     grads = [None] * len(layers)
     # df/dz_out = 1, weighted per point by w_i
@@ -549,11 +470,10 @@ def full_gradient(arch: Arch, theta, g: Geometry, y):
     return L, grad, v
 
 
-def estimator(arch: Arch, theta, g: Geometry, v, I, scale=None, decide=None) -> np.ndarray:
+def estimator(arch: Arch, theta, g: Geometry, v, I, scale=None) -> np.ndarray:
     """Eq. (2): (n/|I|) sum_{i in I} v_i grad f(x_i), for the given index set I.
 
-    ``scale`` defaults to n/|I|; v is the backprojected residual (P^T r);
-    ``decide`` picks how ReLU masks are decided (see ``forward``).
+    ``scale`` defaults to n/|I|; v is the backprojected residual (P^T r).
     """
     I = np.asarray(I, dtype=np.int64)
     n = fov_indices(g).size          # the number of sampled points (all, or those in the FOV)
@@ -562,8 +482,7 @@ def estimator(arch: Arch, theta, g: Geometry, v, I, scale=None, decide=None) -> 
     if g.fov:                        # listed points outside the FOV contribute nothing
         I = I[fov_mask(g.d, g.N, I)]
     X = grid_coords(g.d, g.N, I)
-    return vjp(arch, theta, X, scale * np.asarray(v, dtype=np.float64)[I], decide=decide,
-               X32=grid_coords_fp32(g.d, g.N, I), N=g.N)
+    return vjp(arch, theta, X, scale * np.asarray(v, dtype=np.float64)[I], N=g.N)
 
 
 def virtual_loss(arch: Arch, theta, g: Geometry, v, I, scale=None) -> float:

@@ -84,10 +84,10 @@ static int eval_dispatch(const inrct_mlp* mlp, const Net& n, const float* theta,
 
 static int vjp_dispatch(const inrct_mlp* mlp, const Net& n, const float* theta, int N,
                         const int32_t* idx, int64_t n_idx, const float* v, double scale,
-                        double* g64, float* g32, void* ws, size_t ws_bytes, cudaStream_t st,
+                        double* g64, float* g32, double* value, void* ws, size_t ws_bytes, cudaStream_t st,
                         const void* prepared = nullptr) {
-  return use_tc(mlp) ? tc_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, ws, ws_bytes, st, prepared)
-                     : simt_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, ws, ws_bytes, st);
+  return use_tc(mlp) ? tc_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, value, ws, ws_bytes, st, prepared)
+                     : simt_vjp(n, theta, N, idx, n_idx, v, scale, g64, g32, value, ws, ws_bytes, st);
 }
 
 }  // namespace inrct
@@ -222,11 +222,9 @@ size_t inrct_vjp_ws_bytes(const inrct_mlp* mlp, const inrct_grid* grid, int64_t 
   return vjp_ws(mlp, n, n_idx);
 }
 
-int inr_weighted_vjp(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid,
-                     const int32_t* idx, int64_t n_idx, const float* v, double scale,
-                     double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes,
-                     cudaStream_t stream) {
-  clear_error();
+static int vjp_entry(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid, const int32_t* idx,
+                     int64_t n_idx, const float* v, double scale, double* value_out, double* grad_f64,
+                     float* grad_f32, void* ws, size_t ws_bytes, cudaStream_t stream) {
   INRCT_REQUIRE(grid && grid->N > 0 && grid->N <= 4096, "invalid grid");
   INRCT_REQUIRE(n_idx > 0, "n_idx must be positive (got %lld)", (long long)n_idx);
   INRCT_REQUIRE(n_idx <= (int64_t)1 << 31, "n_idx too large");
@@ -234,8 +232,52 @@ int inr_weighted_vjp(const inrct_mlp* mlp, const float* theta, const inrct_grid*
   Net n;
   INRCT_TRY(make_net(mlp, grid, &n));
   INRCT_TRY(check_tc(mlp, n));
-  return vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, v, scale, grad_f64, grad_f32, ws,
+  return vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, v, scale, grad_f64, grad_f32, value_out, ws,
                       ws_bytes, stream);
+}
+
+int inr_weighted_vjp(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid,
+                     const int32_t* idx, int64_t n_idx, const float* v, double scale,
+                     double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes,
+                     cudaStream_t stream) {
+  clear_error();
+  return vjp_entry(mlp, theta, grid, idx, n_idx, v, scale, nullptr, grad_f64, grad_f32, ws, ws_bytes, stream);
+}
+
+int inr_virtual_loss(const inrct_mlp* mlp, const float* theta, const inrct_grid* grid, const int32_t* idx,
+                     int64_t n_idx, const float* v, double scale, double* value_out, double* grad_f64,
+                     float* grad_f32, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  clear_error();
+  INRCT_REQUIRE(value_out, "value_out must not be NULL");
+  return vjp_entry(mlp, theta, grid, idx, n_idx, v, scale, value_out, grad_f64, grad_f32, ws, ws_bytes, stream);
+}
+
+int inrct_device_status(cudaStream_t stream) {
+  clear_error();
+  int code = 0;
+  INRCT_TRY(tc_device_status(stream, &code));
+  if (code == 0) return INRCT_OK;
+  const char* role = code < 200 ? "weight-gradient GEMM" : code < 300 ? "weight producer"
+                     : code < 400 ? "MMA issuer" : code < 900 ? "epilogue" : "set-up";
+  if (code == 901) {
+    set_error("a tensor-core kernel found its shared memory misaligned and did nothing (code 901)");
+    return INRCT_ERR_CUDA;
+  }
+  set_error("a bounded wait of a tensor-core kernel gave up (%s, code %d): the outputs of the calls "
+            "since the last status check are not valid", role, code);
+  return INRCT_ERR_TIMEOUT;
+}
+
+int inrct_set_wait_limit(unsigned long long ns) {
+  clear_error();
+  tc_set_wait_limit(ns);
+  return INRCT_OK;
+}
+
+int inrct_debug_stall_weight_loads(int on) {
+  clear_error();
+  tc_set_stall_loads(on);
+  return INRCT_OK;
 }
 
 // grad_step workspace: x[n], z[m], r[m], v[n], grad[p] (FP64), loss (FP64), then
@@ -329,7 +371,7 @@ static int step_impl(const inrct_geom* geom, const inrct_grid* grid, const inrct
   prof_mark(kMarkBackDone, stream);
   // steps 3-5: the index set is the caller's; gradient of the virtual loss (Eq. 3)
   double* g = grad_out ? grad_out : w.g;
-  INRCT_TRY(vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, w.v, scale, g, nullptr, w.stage,
+  INRCT_TRY(vjp_dispatch(mlp, n, theta, grid->N, idx, n_idx, w.v, scale, g, nullptr, nullptr, w.stage,
                          w.stage_bytes, stream, w.wprep));
   prof_mark(kMarkVjpDone, stream);
   if (adam && t_dev) {
@@ -439,6 +481,13 @@ int inrct_batch_create(const inrct_mlp* mlp, int loss, const inrct_problem* prob
     b->events.push_back(ev);
   }
   cudaStream_t s0 = b->streams[0];
+  if (use_tc(mlp)) {  // the bounded-wait status word's address, looked up before the capture
+    const int rc = tc_status_resolve(s0);
+    if (rc != INRCT_OK) {
+      batch_free(b);
+      return rc;
+    }
+  }
   // projector launch shapes: tune every geometry without a tuned plan, each in its own
   // problem's part of the workspace (nothing lives there before the first launch)
   {

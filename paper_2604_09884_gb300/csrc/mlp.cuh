@@ -61,8 +61,8 @@ int simt_eval(const Net& net, const float* theta, int N, int64_t n, float* image
               size_t ws_bytes, cudaStream_t st);
 size_t simt_vjp_ws_bytes(const Net& net, int64_t n_idx);
 int simt_vjp(const Net& net, const float* theta, int N, const int32_t* idx, int64_t n_idx,
-             const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
-             size_t ws_bytes, cudaStream_t st);
+             const float* v, double scale, double* grad_f64, float* grad_f32, double* value_out,
+             void* ws, size_t ws_bytes, cudaStream_t st);
 
 // BF16 tcgen05 path
 bool tc_supported(const Net& net, char* why, size_t why_len);
@@ -74,9 +74,19 @@ size_t tc_eval_ws_bytes(const Net& net);
 int tc_eval(const Net& net, const float* theta, int N, int64_t n, float* image, void* ws,
             size_t ws_bytes, cudaStream_t st, const void* prepared = nullptr);
 size_t tc_vjp_ws_bytes(const Net& net, int64_t n_idx);
+// value_out (nullable): the virtual loss scale * sum v_i f(x_i) of Eq. 3, FP64 device scalar.
 int tc_vjp(const Net& net, const float* theta, int N, const int32_t* idx, int64_t n_idx,
-           const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
-           size_t ws_bytes, cudaStream_t st, const void* prepared = nullptr);
+           const float* v, double scale, double* grad_f64, float* grad_f32, double* value_out,
+           void* ws, size_t ws_bytes, cudaStream_t st, const void* prepared = nullptr);
+// Reads and clears the bounded-wait status word of the current device after synchronising
+// st; *code = 0 when no wait gave up since the last read.
+int tc_device_status(cudaStream_t st, int* code);
+// Looks up the status word's address on the current device (before a stream capture).
+int tc_status_resolve(cudaStream_t st);
+// Limit of every bounded wait of later launches (0: the default, 1 s).
+void tc_set_wait_limit(unsigned long long ns);
+// Test hook: while on, the tile kernel's producer issues no weight loads.
+void tc_set_stall_loads(int on);
 
 // split-K TN GEMM of the weight gradients, exposed for diagnostics
 size_t gemm_tn_ws_bytes(int64_t K, int M, int N);

@@ -656,8 +656,26 @@ struct VjpWs {
   float* Z;
   float* D;
   float* dout;
+  float* f;  // f(x) at the chunk's points (the virtual loss)
   float* part;
 };
+
+// *value (+)= sum_q w[q] f[q] in FP64: the virtual loss of Eq. 3 over one chunk, w the
+// point weights scale * v_i of the backward kernel (zero for points without weight).  One
+// block, fixed-order tree, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) weighted_sum_kernel(const float* __restrict__ w, const float* __restrict__ f,
+                                                         int64_t n, int accumulate, double* __restrict__ value) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) s += (double)w[q] * (double)f[q];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *value = accumulate ? *value + sh[0] : sh[0];
+}
 
 // Point splits of one layer's dW: enough (tile, split) blocks for about four per SM of
 // a 152-SM part, at least two slabs of points per split, at most kMaxDwSplits partials
@@ -687,6 +705,7 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, VjpWs* out,
   w.Z = c.take<float>(chunk * n.L * n.W);
   w.D = c.take<float>(chunk * n.L * n.W);
   w.dout = c.take<float>(chunk);
+  w.f = c.take<float>(chunk);
   // partials of the largest layer at its split count (split counts grow with the chunk)
   int64_t pe = 0;
   for (int l = 0; l <= n.L; ++l)
@@ -768,8 +787,8 @@ size_t simt_vjp_ws_bytes(const Net& n, int64_t n_idx) {
 }
 
 int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t n_idx,
-             const float* v, double scale, double* grad_f64, float* grad_f32, void* ws,
-             size_t ws_bytes, cudaStream_t st) {
+             const float* v, double scale, double* grad_f64, float* grad_f32, double* value_out,
+             void* ws, size_t ws_bytes, cudaStream_t st) {
   INRCT_TRY(check_theta_alignment(n, theta, "inr_weighted_vjp"));
   const int64_t chunk = n_idx < kVjpChunk ? n_idx : kVjpChunk;
   VjpWs w;
@@ -788,7 +807,8 @@ int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_
     const int32_t* id = idx + c0;
     const unsigned nb = ceil_div(np, TP);
     if (c0 == 0) prof_mark(kMarkVjpKernel, st);
-    simt_fwd_kernel<<<nb, n.W, fwd_smem(n), st>>>(nd, lo, theta, w.Wt, np, id, nullptr, w.E, w.Z);
+    simt_fwd_kernel<<<nb, n.W, fwd_smem(n), st>>>(nd, lo, theta, w.Wt, np, id, value_out ? w.f : nullptr, w.E,
+                                                  w.Z);
     INRCT_CHECK_LAUNCH("simt vjp forward");
     if (c0 == 0 && n.n_table > 0) {
       const cudaError_t e = cudaMemsetAsync(grad_f64, 0, sizeof(double) * n.n_table, st);
@@ -800,6 +820,10 @@ int simt_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_
     simt_bwd_kernel<<<nb, n.W, sizeof(float) * TP * n.W, st>>>(
         nd, lo, theta, np, id, v, (float)scale, w.Z, w.D, w.dout, n.n_table > 0 ? grad_f64 : nullptr);
     INRCT_CHECK_LAUNCH("simt vjp backward");
+    if (value_out) {
+      weighted_sum_kernel<<<1, 256, 0, st>>>(w.dout, w.f, np, c0 > 0, value_out);
+      INRCT_CHECK_LAUNCH("virtual loss sum");
+    }
     if (c0 == 0) prof_mark(kMarkVjpKernelDone, st);
     for (int l = 0; l <= n.L; ++l) {
       const int O = n.out_dim[l], K = n.in_dim[l];

@@ -35,6 +35,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "mlp.cuh"
@@ -75,6 +76,45 @@ __host__ __device__ inline int ffn_panel_col(int k, int F) {
   return k < F ? 64 * (k >> 5) + (k & 31) : 64 * ((k - F) >> 5) + 32 + ((k - F) & 31);
 }
 
+
+// ---------------------------------------------------------------------------
+// Status of the bounded waits.  Every mbarrier wait of the tensor-core kernels gives up after
+// a limit; the first wait that does records its code here (one word per device, read and
+// cleared by inrct_device_status): 1xx weight-gradient GEMM, 2xx weight producer, 3xx MMA
+// issuer, 4xx epilogue; 901 shared memory not 1024-byte aligned.
+// ---------------------------------------------------------------------------
+__device__ int g_wait_status;
+
+std::atomic<unsigned long long> g_wait_ns{kWaitTimeoutNs};
+std::atomic<int> g_stall_loads{0};
+std::mutex g_status_mu;
+void* g_status_addr[256] = {};
+
+// Device address of the status word on the current device: looked up with
+// cudaGetSymbolAddress on every call outside stream capture (cheap, and never stale after a
+// device reset), taken from the per-device cache during capture.
+int status_word(cudaStream_t st, int** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    set_error("no usable current device (%s)", cudaGetErrorString(e));
+    return INRCT_ERR_CUDA;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capturing = st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+  std::lock_guard<std::mutex> lk(g_status_mu);
+  if (!capturing || !g_status_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_wait_status);
+    if (e != cudaSuccess || !p) {
+      set_error("status word: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return INRCT_ERR_CUDA;
+    }
+    g_status_addr[dev] = p;
+  }
+  *out = static_cast<int*>(g_status_addr[dev]);
+  return INRCT_OK;
+}
 
 // ---------------------------------------------------------------------------
 // host: tensor maps
@@ -131,6 +171,7 @@ struct PrepTable {
   int64_t offW[kMaxLayers], offb[kMaxLayers];
   __nv_bfloat16* Wb[kMaxLayers];
   __nv_bfloat16* WbT[kMaxLayers];
+  __nv_bfloat16* Wlo[kMaxLayers];  // split forward stages: bf16(W' - Wb), else NULL
   float* bias[kMaxLayers];
   int permF;  // FFN: F, and entry 0 (layer 0) is stored with interleaved input columns; else 0
   // the row blockIdx.y == n fills the small tables the tile kernel reads through L1:
@@ -167,10 +208,12 @@ __global__ void prep_all_kernel(const float* __restrict__ theta, const __grid_co
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int o = (int)(t / in), k = (int)(t % in);
-    const __nv_bfloat16 w = __float2bfloat16_rn(scale * theta[T.offW[l] + t]);
+    const float wf = scale * theta[T.offW[l] + t];
+    const __nv_bfloat16 w = __float2bfloat16_rn(wf);
     const int kw = (l == 0 && T.permF > 0) ? ffn_panel_col(k, T.permF) : k;
     T.Wb[l][(int64_t)o * in + kw] = w;
     if (T.WbT[l]) T.WbT[l][(int64_t)kw * out + o] = w;
+    if (T.Wlo[l]) T.Wlo[l][(int64_t)o * in + kw] = __float2bfloat16_rn(wf - __bfloat162float(w));
     if (t < out) T.bias[l][t] = scale * theta[T.offb[l] + t];
   }
 }
@@ -209,6 +252,11 @@ struct GemmPlan {
   const double* bpart;
   int n_bpart;
   int64_t off_bout;
+  // the virtual loss (Eq. 3): FP64 partial sums of scale * v_i * f(x_i) from the VJP tile
+  // kernel (n_bpart of them), summed by the same block into *value_out (NULL: not wanted)
+  const double* vpart;
+  double* value_out;
+  uint64_t wait_ns;  // limit of every bounded wait of the GEMM kernel
 };
 
 constexpr int kGemmStages = 4;
@@ -254,13 +302,15 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = tmem_base;
   const uint32_t xbytes = 2 * 8192, ybytes = (uint32_t)J.N * 128, y16bytes = J.has_y16 ? 2048 : 0;
 
+  const uint64_t lim = plan.wait_ns;
   if (warp == 0) {
     if (lane == 0) {
       uint32_t ep = 1;
+      int armed = 0;  // loads issued
       for (int c = 0; c < nch; ++c) {
         const int s = c % kGemmStages;
         if (c > 0 && s == 0) ep ^= 1;
-        if (!mbar_wait(&empty[s], ep, &abort_flag, err, 101)) break;
+        if (!mbar_wait(&empty[s], ep, &abort_flag, err, 101, lim)) break;
         uint8_t* st = smem + s * kGemmStageBytes;
         mbar_arrive_expect_tx(&full[s], xbytes + ybytes + y16bytes);
         const int k0 = (int)(k_begin + 64 * c);
@@ -269,7 +319,12 @@ __global__ void __launch_bounds__(192, 1)
         for (int b = 0; b < J.N / 64; ++b)
           tma_load_2d(st + 16384 + b * 8192, &maps.m[J.my], &full[s], J.n0 + 64 * b, k0);
         if (J.has_y16) tma_load_2d(st + 16384 + 32768, &maps.m[J.my16], &full[s], k0, 0);
+        ++armed;
       }
+      // no load may still be writing shared memory when the CTA exits (the abort path leaves
+      // loads the MMA thread never waited for): wait for the last stages' loads to land
+      for (int c = armed > kGemmStages ? armed - kGemmStages : 0; c < armed; ++c)
+        mbar_wait_drain(&full[c % kGemmStages], (uint32_t)((c / kGemmStages) & 1), lim);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -280,7 +335,7 @@ __global__ void __launch_bounds__(192, 1)
       for (int c = 0; c < nch; ++c) {
         const int s = c % kGemmStages;
         if (c > 0 && s == 0) fp ^= 1;
-        if (!mbar_wait(&full[s], fp, &abort_flag, err, 102)) break;
+        if (!mbar_wait(&full[s], fp, &abort_flag, err, 102, lim)) break;
         tc_fence_after();
         const uint32_t st = smem_u32(smem + s * kGemmStageBytes);
 #pragma unroll
@@ -295,8 +350,14 @@ __global__ void __launch_bounds__(192, 1)
         issued = true;
         mma_commit(&empty[s]);
       }
-      if (issued) mma_commit(&accf);
-      else mbar_arrive(&accf);
+      if (issued) {
+        mma_commit(&accf);
+        // every issued MMA completes before the tensor memory is released (on the abort path
+        // the epilogue does not wait for them)
+        mbar_wait_drain(&accf, 0, lim);
+      } else {
+        mbar_arrive(&accf);
+      }
     }
   } else {
     // epilogue warps 2..5: lanes 32*(warp%4) .. of TMEM = rows of C
@@ -304,7 +365,7 @@ __global__ void __launch_bounds__(192, 1)
     const int row = mt * 128 + q * 32 + lane;
     const int ldc = J.N + 32;
     float* out = part + J.part_off + ((int64_t)sp * J.M + row) * ldc;
-    const bool ok = warp_wait(&accf, 0, &abort_flag, err, 103);
+    const bool ok = warp_wait(&accf, 0, &abort_flag, err, 103, lim);
     tc_fence_after();
     float v[32];
     auto emit = [&](int col, int tcol) {
@@ -347,18 +408,26 @@ __global__ void __launch_bounds__(192, 1)
 __global__ void gemm_reduce_kernel(const __grid_constant__ GemmPlan plan, const float* __restrict__ part,
                                    int accumulate, double* __restrict__ grad) {
   const int jb = blockIdx.y;
-  if (jb == plan.n_jobs) {  // output bias: fixed-order tree over the partials
+  if (jb == plan.n_jobs) {  // output bias and virtual loss: fixed-order trees over the partials
     if (blockIdx.x != 0) return;
     __shared__ double sh[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < plan.n_bpart; i += blockDim.x) s += plan.bpart[i];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    for (int which = 0; which < 2; ++which) {
+      const double* src = which ? plan.vpart : plan.bpart;
+      if (which && !plan.value_out) break;
+      double s = 0.0;
+      for (int i = threadIdx.x; i < plan.n_bpart; i += blockDim.x) s += src[i];
+      sh[threadIdx.x] = s;
+      __syncthreads();
+      for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        double* dst = which ? plan.value_out : grad + plan.off_bout;
+        *dst = accumulate ? *dst + sh[0] : sh[0];
+      }
       __syncthreads();
     }
-    if (threadIdx.x == 0) grad[plan.off_bout] = accumulate ? grad[plan.off_bout] + sh[0] : sh[0];
     return;
   }
   const GemmJob& J = plan.job[jb];
@@ -412,6 +481,7 @@ struct TileProg {
   int64_t offW0, offb0, offWout, offbout;  // theta offsets (first layer, output layer)
   int n_stages;
   int st_kind[kMaxStages], st_layer[kMaxStages], st_panels[kMaxStages], st_map[kMaxStages];
+  int st_map_lo[kMaxStages];  // split forward stages: map of the low parts W_lo of the weights
   int in_panels;        // panels of the first stage's input
   // eval
   float* out;
@@ -436,8 +506,10 @@ struct TileProg {
   __nv_bfloat16* Y16c;  // [16][npts_pad]
   __nv_bfloat16* Y16o;  // [16][npts_pad]
   double* bias_part;    // [gridDim.x][4] FP64 sums of scale * v_i (output-layer bias gradient)
+  double* vloss_part;   // [gridDim.x][4] FP64 sums of scale * v_i * f(x_i) (the virtual loss, Eq. 3)
   int64_t npts_pad;
-  int stall;            // diagnostic: the producer issues nothing (tests bounded waits)
+  int stall;            // test hook: the producer issues no weight loads (a bounded wait runs out)
+  uint64_t wait_ns;     // limit of every bounded wait
 };
 
 template <int CW>
@@ -493,24 +565,38 @@ __device__ __forceinline__ void four_feat2(float ph, float* s, float* c) {
 // those are streamed through the four panel buffers with per-panel barriers
 // (a_full: written, a_empty: read by the MMA).
 //
+// SPLIT (the VJP of ReLU networks).  The forward stages decide the ReLU masks that the
+// backward stages apply, and a mask decided on BF16-rounded operands differs from the
+// exact one wherever a pre-activation lies within BF16 rounding of zero (about 1 % of the
+// units of the 3-D Fourier-feature networks, several per point).  So the forward stages
+// form their pre-activations to about FP32 accuracy: every operand x is split into
+// x_hi = bf16(x) and x_lo = bf16(x - x_hi), and the stage accumulates
+// a_hi W_hi^T + a_lo W_hi^T + a_hi W_lo^T in FP32 (the dropped a_lo W_lo^T and the
+// rounding of the low parts are about 2^-16 of each product).  The low parts of a stage's
+// input take the panel space of the second slot, so one tile is in flight per CTA
+// (NSLOT = 1); the ring carries the W_hi and W_lo chunks of each K panel in turn.  The
+// backward stages and the scratch the weight-gradient GEMM reads stay single BF16.
+//
 // NWG epilogue warpgroups; each thread of warpgroup g owns CW = 64/NWG columns of
 // every 64-column chunk of its TMEM lane (row).
-template <int MODE, int KIND, int NWG>
+template <int MODE, int KIND, int NWG, bool SPLIT>
 __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     mlp_tile_kernel(const __grid_constant__ Maps maps, const __grid_constant__ TileProg P,
                     int* __restrict__ err) {
+  constexpr int NSLOT = SPLIT ? 1 : 2;
+  static_assert(!SPLIT || MODE == 1, "split operands serve the VJP's mask decisions");
   // Dynamic shared memory only (no static): [8 input panels][weight ring][barriers][dot scratch].
   // The panels and the ring need 1024-byte alignment (128-byte swizzle atoms); the dynamic
   // window starts there when the kernel has no static shared memory, which is checked.
   extern __shared__ __align__(1024) uint8_t dsm[];
   if ((smem_u32(dsm) & 1023u) != 0) {
-    if (threadIdx.x == 0) atomicExch(err, 901);
+    if (threadIdx.x == 0) atomicCAS(err, 0, 901);
     return;
   }
   uint8_t* smem = dsm;
   const int W = P.W;
   const int NW = W / kNSplit;                    // MMA N and weight rows per ring slot
-  uint8_t* apan = smem;                          // 2 slots x 4 x 16 KB input panels
+  uint8_t* apan = smem;                          // 2 slots x 4 x 16 KB input panels (SPLIT: hi, lo)
   uint8_t* ring = smem + 8 * kPanelBytes;        // n_ring x (NW x 2 kKChunk B) weight chunks
   const uint32_t chunk_bytes = (uint32_t)NW * (2 * kKChunk);
   const int n_ring = ring_bytes(MODE) / (int)chunk_bytes;
@@ -537,10 +623,12 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   float* wout_s = bias_s + (size_t)P.L * W;             // [W]
   float4* first_s = reinterpret_cast<float4*>(wout_s + W);  // [n_first] when P.first_staged
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t lim = P.wait_ns;
   const int64_t n_tiles = (P.npts + kTile - 1) / kTile;
-  // this CTA's tiles are blockIdx.x + j * gridDim.x; they are taken in pairs (slot 0, slot 1)
+  // this CTA's tiles are blockIdx.x + j * gridDim.x; they are taken in groups of NSLOT
+  // (slot 0, slot 1)
   const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int64_t n_pairs = (my_tiles + 1) / 2;
+  const int64_t n_groups = (my_tiles + NSLOT - 1) / NSLOT;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < n_ring; ++s) {
@@ -568,7 +656,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   for (int i = threadIdx.x; i < W; i += blockDim.x) wout_s[i] = P.wout[i];
   if (P.first_staged)
     for (int i = threadIdx.x; i < P.n_first; i += blockDim.x) first_s[i] = P.first[i];
-  if (warp == 0) tmem_alloc(tmem_base, 2 * W);
+  if (warp == 0) tmem_alloc(tmem_base, NSLOT * W);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -577,21 +665,29 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   if (warp == 4 * NWG) {
     // ---------------- TMA producer ----------------
     if (lane == 0 && !P.stall) {
-      for (int s = 0; s < P.n_stages; ++s) prefetch_map(&maps.m[P.st_map[s]]);
+      for (int s = 0; s < P.n_stages; ++s) {
+        prefetch_map(&maps.m[P.st_map[s]]);
+        if (SPLIT && P.st_kind[s] != kBwd) prefetch_map(&maps.m[P.st_map_lo[s]]);
+      }
       uint32_t slot = 0, ep = 1;
-      for (int64_t pr = 0; pr < n_pairs; ++pr) {
+      int64_t armed = 0;  // weight loads issued
+      for (int64_t pr = 0; pr < n_groups; ++pr) {
         for (int s = 0; s < P.n_stages; ++s) {
-          for (int t = 0; t < 2; ++t) {
+          const int n_src = (SPLIT && P.st_kind[s] != kBwd) ? 2 : 1;  // W_hi (then W_lo) per chunk
+          for (int t = 0; t < NSLOT; ++t) {
             for (int c = 0; c < P.st_panels[s]; ++c) {
               for (int kk = 0; kk < 64 / kKChunk; ++kk) {
                 for (int h = 0; h < kNSplit; ++h) {
-                  if (!mbar_wait(&w_empty[slot], ep, abort_flag, err, 201)) goto producer_done;
-                  mbar_arrive_expect_tx(&w_full[slot], chunk_bytes);
-                  tma_load_2d(ring + slot * chunk_bytes, &maps.m[P.st_map[s]], &w_full[slot],
-                              64 * c + kKChunk * kk, h * NW);
-                  if (++slot == n_ring) {
-                    slot = 0;
-                    ep ^= 1;
+                  for (int src = 0; src < n_src; ++src) {
+                    if (!mbar_wait(&w_empty[slot], ep, abort_flag, err, 201, lim)) goto producer_done;
+                    mbar_arrive_expect_tx(&w_full[slot], chunk_bytes);
+                    tma_load_2d(ring + slot * chunk_bytes, &maps.m[src ? P.st_map_lo[s] : P.st_map[s]],
+                                &w_full[slot], 64 * c + kKChunk * kk, h * NW);
+                    ++armed;
+                    if (++slot == n_ring) {
+                      slot = 0;
+                      ep ^= 1;
+                    }
                   }
                 }
               }
@@ -599,8 +695,14 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           }
         }
       }
+    producer_done:
+      // No load may still be writing shared memory when the CTA exits.  On the abort path
+      // the MMA issuer stops waiting for the chunks, so wait here (bounded, whatever the abort
+      // flag says) for the last n_ring loads, the only ones not yet consumed; load j went to
+      // ring slot j mod n_ring with phase parity (j / n_ring) mod 2.
+      for (int64_t j = armed > n_ring ? armed - n_ring : 0; j < armed; ++j)
+        mbar_wait_drain(&w_full[j % n_ring], (uint32_t)((j / n_ring) & 1), lim);
     }
-  producer_done:;
   } else if (warp == 4 * NWG + 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
@@ -619,11 +721,12 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                        (int)(layer * P.npts_pad + tile * kTile));
         bulk_commit_group();
       };
-      for (int64_t pr = 0; pr < n_pairs; ++pr) {
-        const int64_t tile0 = blockIdx.x + (2 * pr) * (int64_t)gridDim.x;
+      for (int64_t pr = 0; pr < n_groups; ++pr) {
+        const int64_t tile0 = blockIdx.x + (NSLOT * pr) * (int64_t)gridDim.x;
         for (int s = 0; s < P.n_stages; ++s) {
-          for (int t = 0; t < 2; ++t) {
-            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, abort_flag, err, 301)) goto mma_done;
+          const bool fsplit = SPLIT && P.st_kind[s] != kBwd;
+          for (int t = 0; t < NSLOT; ++t) {
+            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, abort_flag, err, 301, lim)) goto mma_done;
             irp ^= 1u << t;
             tc_fence_after();
             if (MODE == 1 && P.st_in_arr[s] >= 0 && tile0 + t * gridDim.x < n_tiles)
@@ -634,29 +737,50 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               const int as = c & 3;
               if (c >= 4) {  // a streamed input panel (first stage only)
                 const int bit = 4 * t + as;
-                if (!mbar_wait(&a_full[4 * t + as], (ap >> bit) & 1u, abort_flag, err, 302)) goto mma_done;
+                if (!mbar_wait(&a_full[4 * t + as], (ap >> bit) & 1u, abort_flag, err, 302, lim)) goto mma_done;
                 ap ^= 1u << bit;
                 tc_fence_after();
               }
               const uint32_t abase = smem_u32(apan + (4 * t + as) * kPanelBytes);
+              const uint32_t lbase = smem_u32(apan + (4 + as) * kPanelBytes);  // low parts (SPLIT)
               for (int kk = 0; kk < 64 / kKChunk; ++kk) {
                 for (int h = 0; h < kNSplit; ++h) {
-                  if (!mbar_wait(&w_full[slot], wf, abort_flag, err, 303)) goto mma_done;
-                  tc_fence_after();
-                  const uint32_t bbase = smem_u32(ring + slot * chunk_bytes);
                   const uint32_t dcol = tmem + t * W + h * NW;
+                  // W_hi chunk: A_hi (and, split, A_lo) against it
+                  if (!mbar_wait(&w_full[slot], wf, abort_flag, err, 303, lim)) goto mma_done;
+                  tc_fence_after();
+                  {
+                    const uint32_t bbase = smem_u32(ring + slot * chunk_bytes);
 #pragma unroll
-                  for (int j = 0; j < kKChunk / 16; ++j) {
-                    const int ks = kk * (kKChunk / 16) + j;  // K=16 step within the 64-wide panel
-                    mma_bf16(dcol, desc_sw128(abase + 32 * ks, 16, 1024),
-                             desc_sw(bbase + 32 * j, 16, 16 * kKChunk, 2 * kKChunk), idesc,
-                             (c > 0 || ks > 0) ? 1u : 0u);
+                    for (int j = 0; j < kKChunk / 16; ++j) {
+                      const int ks = kk * (kKChunk / 16) + j;  // K=16 step within the 64-wide panel
+                      const uint64_t bd = desc_sw(bbase + 32 * j, 16, 16 * kKChunk, 2 * kKChunk);
+                      mma_bf16(dcol, desc_sw128(abase + 32 * ks, 16, 1024), bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                      if (fsplit) mma_bf16(dcol, desc_sw128(lbase + 32 * ks, 16, 1024), bd, idesc, 1u);
+                    }
                   }
                   issued = true;
                   mma_commit(&w_empty[slot]);
                   if (++slot == n_ring) {
                     slot = 0;
                     wf ^= 1;
+                  }
+                  if (fsplit) {
+                    // W_lo chunk: A_hi against it
+                    if (!mbar_wait(&w_full[slot], wf, abort_flag, err, 303, lim)) goto mma_done;
+                    tc_fence_after();
+                    const uint32_t bbase = smem_u32(ring + slot * chunk_bytes);
+#pragma unroll
+                    for (int j = 0; j < kKChunk / 16; ++j) {
+                      const int ks = kk * (kKChunk / 16) + j;
+                      mma_bf16(dcol, desc_sw128(abase + 32 * ks, 16, 1024),
+                               desc_sw(bbase + 32 * j, 16, 16 * kKChunk, 2 * kKChunk), idesc, 1u);
+                    }
+                    mma_commit(&w_empty[slot]);
+                    if (++slot == n_ring) {
+                      slot = 0;
+                      wf ^= 1;
+                    }
                   }
                 }
               }
@@ -667,10 +791,10 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           }
         }
         if (MODE == 1) {
-          // the deltas of the last stage: stored, then the feature pass of the next pair may
+          // the deltas of the last stage: stored, then the feature pass of the next group may
           // overwrite the panels
-          for (int t = 0; t < 2; ++t) {
-            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, abort_flag, err, 304)) goto mma_done;
+          for (int t = 0; t < NSLOT; ++t) {
+            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, abort_flag, err, 304, lim)) goto mma_done;
             irp ^= 1u << t;
             if (tile0 + t * gridDim.x < n_tiles) store_panels(t, P.map_dlt, P.tail_layer, tile0 + t * gridDim.x);
             bulk_wait_read_all();
@@ -684,7 +808,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
         // drain: every issued MMA completes before TMEM is released (matters on the
         // abort path; otherwise the epilogue has already waited for all of them)
         mma_commit(drain_bar);
-        mbar_wait_drain(drain_bar, 0);
+        mbar_wait_drain(drain_bar, 0, lim);
       }
     }
   } else {
@@ -701,12 +825,13 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     const int n0 = P.in_panels < 4 ? P.in_panels : 4;  // first-stage panels published together
     float v[CW];
     double bsum = 0.0;  // VJP: this row's share of sum scale * v_i (warps of column group 0)
-    for (int64_t pr = 0; pr < n_pairs; ++pr) {
+    double fsum = 0.0;  // VJP: this row's share of sum scale * v_i * f(x_i) (the virtual loss)
+    for (int64_t pr = 0; pr < n_groups; ++pr) {
       // per-slot point data, kept in scalars (slot t selects with a conditional)
-      const int64_t tile0 = blockIdx.x + (2 * pr) * (int64_t)gridDim.x;
-      const int64_t tile1 = tile0 + gridDim.x;  // may be past the end: a dummy tile
-      float x0[3], x1[3], sv0, sv1;
-      bool valid0, valid1;
+      const int64_t tile0 = blockIdx.x + (NSLOT * pr) * (int64_t)gridDim.x;
+      const int64_t tile1 = tile0 + gridDim.x;  // two slots only; may be past the end: a dummy tile
+      float x0[3], x1[3] = {0.f, 0.f, 0.f}, sv0, sv1 = 0.f;
+      bool valid0, valid1 = false;
       {
         auto setup = [&](int64_t tile, float* x, float& sv, bool& valid) {
           const int64_t pt = tile * kTile + r;
@@ -719,18 +844,18 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           sv = (MODE == 1 && weighted) ? P.scale * P.v[gi] : 0.f;
         };
         setup(tile0, x0, sv0, valid0);
-        setup(tile1, x1, sv1, valid1);
+        if (NSLOT == 2) setup(tile1, x1, sv1, valid1);
       }
       if (MODE == 1 && g == 0) bsum += (double)sv0 + (double)sv1;
-      // ---- first stage input of both slots ----
-      for (int t = 0; t < 2; ++t) {
+      // ---- first stage input ----
+      for (int t = 0; t < NSLOT; ++t) {
         const int64_t prow_t = (t ? tile1 : tile0) * kTile + r;  // scratch row (padded to the tile)
         const bool store_t = (t ? tile1 : tile0) < n_tiles;      // dummy tiles write nowhere
         const int64_t tile_t = t ? tile1 : tile0;
         const float xt[3] = {t ? x1[0] : x0[0], t ? x1[1] : x0[1], t ? x1[2] : x0[2]};
         if (MODE == 1 && pr > 0) {
-          // the previous pair's last deltas are still being stored from these panels
-          if (!warp_wait(&st_done[t], (sdp >> t) & 1u, abort_flag, err, 405)) goto epi_done;
+          // the previous group's last deltas are still being stored from these panels
+          if (!warp_wait(&st_done[t], (sdp >> t) & 1u, abort_flag, err, 405, lim)) goto epi_done;
           sdp ^= 1u << t;
         }
         for (int c = 0; c < P.in_panels; ++c) {
@@ -773,14 +898,19 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           const int as = c & 3;
           if (c >= 4) {  // streamed panel: the MMA must have read panel c - 4 from this buffer
             const int bit = 4 * t + as;
-            if (!warp_wait(&a_empty[4 * t + as], (ae >> bit) & 1u, abort_flag, err, 401)) goto epi_done;
+            if (!warp_wait(&a_empty[4 * t + as], (ae >> bit) & 1u, abort_flag, err, 401, lim)) goto epi_done;
             ae ^= 1u << bit;
           }
           if (KIND == INRCT_FFN_RELU) {
             st_panel_row<8>(apan + (4 * t + as) * kPanelBytes, r, g, v);
             st_panel_row<8>(apan + (4 * t + as) * kPanelBytes, r, 4 + g, v + 8);
+            if (SPLIT) {
+              st_panel_row_lo<8>(apan + (4 + as) * kPanelBytes, r, g, v);
+              st_panel_row_lo<8>(apan + (4 + as) * kPanelBytes, r, 4 + g, v + 8);
+            }
           } else {
             st_panel_row<CW>(apan + (4 * t + as) * kPanelBytes, r, (CW / 8) * g, v);
+            if (SPLIT) st_panel_row_lo<CW>(apan + (4 + as) * kPanelBytes, r, (CW / 8) * g, v);
           }
           if (c == n0 - 1) {
             // panels 0 .. n0-1 written and (program order) this slot's accumulator drained
@@ -799,7 +929,8 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
       for (int s = 0; s < P.n_stages; ++s) {
         const int kind = P.st_kind[s], l = P.st_layer[s];
         const bool write_panel = s + 1 < P.n_stages;  // the next stage's input
-        for (int t = 0; t < 2; ++t) {
+        const bool write_lo = SPLIT && kind == kFwdHidden;  // the next stage is a split forward stage
+        for (int t = 0; t < NSLOT; ++t) {
           const int64_t prow_t = (t ? tile1 : tile0) * kTile + r;
           const bool store_t = (t ? tile1 : tile0) < n_tiles;
           const bool valid_t = t ? valid1 : valid0;
@@ -816,7 +947,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               sgn[k] = store_t ? reinterpret_cast<const uint4*>(P.Sg + sg_off(l - 1, tile_t, 0))[k]
                                : make_uint4(0, 0, 0, 0);
           }
-          if (!warp_wait(&acc_full[t], (af >> t) & 1u, abort_flag, err, 402)) goto epi_done;
+          if (!warp_wait(&acc_full[t], (af >> t) & 1u, abort_flag, err, 402, lim)) goto epi_done;
           af ^= 1u << t;
           tc_fence_after();
           float dot = 0.f;
@@ -889,17 +1020,17 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                     store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
                 }
                 if (kind == kFwdLast) {
+                  // f(x) = w_out . a_{L-1} + b_out: this thread's share of the dot product
                   const float4* wo = reinterpret_cast<const float4*>(wout_s + col0);
-                  if (MODE == 0) {
 #pragma unroll
-                    for (int i4 = 0; i4 < CW / 4; ++i4) {
-                      const float4 ww = wo[i4];
-                      dot = fmaf(v[4 * i4], ww.x, dot);
-                      dot = fmaf(v[4 * i4 + 1], ww.y, dot);
-                      dot = fmaf(v[4 * i4 + 2], ww.z, dot);
-                      dot = fmaf(v[4 * i4 + 3], ww.w, dot);
-                    }
-                  } else {
+                  for (int i4 = 0; i4 < CW / 4; ++i4) {
+                    const float4 ww = wo[i4];
+                    dot = fmaf(v[4 * i4], ww.x, dot);
+                    dot = fmaf(v[4 * i4 + 1], ww.y, dot);
+                    dot = fmaf(v[4 * i4 + 2], ww.z, dot);
+                    dot = fmaf(v[4 * i4 + 3], ww.w, dot);
+                  }
+                  if (MODE == 1) {
                     // delta_{L-1} = scale v_i * w_out * sigma'(u_{L-1})
 #pragma unroll
                     for (int i4 = 0; i4 < CW / 4; ++i4) {
@@ -913,30 +1044,37 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                   }
                 }
               }
-              if (pub) st_panel_row<CW>(apan + (4 * t + c) * kPanelBytes, r, (CW / 8) * g, v);
+              if (pub) {
+                st_panel_row<CW>(apan + (4 * t + c) * kPanelBytes, r, (CW / 8) * g, v);
+                if (write_lo) st_panel_row_lo<CW>(apan + (4 + c) * kPanelBytes, r, (CW / 8) * g, v);
+              }
             }
           }
           if (pub) fence_async_smem();
           tc_fence_before();
           __syncwarp();
           if (pub && lane == 0) mbar_arrive(&in_ready[t]);
-          if (MODE == 0 && kind == kFwdLast) {
-            // out = b_out + sum of the NWG column-group partial dot products of row r; one
+          if (kind == kFwdLast) {
+            // f = b_out + sum of the NWG column-group partial dot products of row r; one
             // scratch buffer per row quarter, released by its summing warp (dot_free)
             if (dot_uses > 0) {
-              if (!warp_wait(&dot_free[q], (dot_uses - 1) & 1u, abort_flag, err, 406)) goto epi_done;
+              if (!warp_wait(&dot_free[q], (dot_uses - 1) & 1u, abort_flag, err, 406, lim)) goto epi_done;
             }
             dotp[g * kTile + r] = dot;
             __syncwarp();
             if (lane == 0) mbar_arrive(&dot_bar[q]);
             if (g == 0) {
-              if (!warp_wait(&dot_bar[q], dot_uses & 1u, abort_flag, err, 404)) goto epi_done;
+              if (!warp_wait(&dot_bar[q], dot_uses & 1u, abort_flag, err, 404, lim)) goto epi_done;
               float f = bout;
 #pragma unroll
               for (int q2 = 0; q2 < NWG; ++q2) f += dotp[q2 * kTile + r];
               __syncwarp();
               if (lane == 0) mbar_arrive(&dot_free[q]);
-              if (valid_t) P.out[prow_t] = f;
+              if (MODE == 0) {
+                if (valid_t) P.out[prow_t] = f;
+              } else {
+                fsum += (double)sv_t * (double)f;  // sv_t is 0 for points without weight
+              }
             }
             ++dot_uses;
           }
@@ -945,8 +1083,14 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     }
     if (MODE == 1 && g == 0) {
 #pragma unroll
-      for (int o = 16; o; o >>= 1) bsum += __shfl_down_sync(0xffffffffu, bsum, o);
-      if (lane == 0) P.bias_part[(int64_t)blockIdx.x * 4 + q] = bsum;
+      for (int o = 16; o; o >>= 1) {
+        bsum += __shfl_down_sync(0xffffffffu, bsum, o);
+        fsum += __shfl_down_sync(0xffffffffu, fsum, o);
+      }
+      if (lane == 0) {
+        P.bias_part[(int64_t)blockIdx.x * 4 + q] = bsum;
+        P.vloss_part[(int64_t)blockIdx.x * 4 + q] = fsum;
+      }
     }
   epi_done:;
   }
@@ -954,7 +1098,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 2 * W);
+    tmem_dealloc(tmem, NSLOT * W);
   }
 }
 
@@ -993,33 +1137,36 @@ size_t tile_smem(const Net& n, int mode = 0) {
 }
 
 
-template <int MODE, int KIND>
+template <int MODE, int KIND, bool SPLIT>
 int launch_tile_t(const Net& n, const Maps& maps, const TileProg& P, int grid, int* err, cudaStream_t st) {
   const size_t sm = tile_smem(n, MODE);
-  cudaError_t e = cudaFuncSetAttribute(mlp_tile_kernel<MODE, KIND, kTileNWG>,
+  cudaError_t e = cudaFuncSetAttribute(mlp_tile_kernel<MODE, KIND, kTileNWG, SPLIT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
     set_error("tile kernel shared memory (%zu bytes): %s", sm, cudaGetErrorString(e));
     return INRCT_ERR_CUDA;
   }
-  mlp_tile_kernel<MODE, KIND, kTileNWG><<<grid, 32 * (4 * kTileNWG + 2), sm, st>>>(maps, P, err);
+  mlp_tile_kernel<MODE, KIND, kTileNWG, SPLIT><<<grid, 32 * (4 * kTileNWG + 2), sm, st>>>(maps, P, err);
   INRCT_CHECK_LAUNCH("mlp tile kernel");
   return INRCT_OK;
 }
 
+// Instances: evaluation (two slots) for both kinds; VJP with two slots for SIREN and with
+// split forward operands (one slot) for ReLU networks.
 int launch_tile(int mode, const Net& n, const Maps& maps, const TileProg& P, int grid, int* err,
                 cudaStream_t st) {
   if (mode == 0)
-    return n.kind == INRCT_SIREN ? launch_tile_t<0, INRCT_SIREN>(n, maps, P, grid, err, st)
-                                 : launch_tile_t<0, INRCT_FFN_RELU>(n, maps, P, grid, err, st);
-  return n.kind == INRCT_SIREN ? launch_tile_t<1, INRCT_SIREN>(n, maps, P, grid, err, st)
-                               : launch_tile_t<1, INRCT_FFN_RELU>(n, maps, P, grid, err, st);
+    return n.kind == INRCT_SIREN ? launch_tile_t<0, INRCT_SIREN, false>(n, maps, P, grid, err, st)
+                                 : launch_tile_t<0, INRCT_FFN_RELU, false>(n, maps, P, grid, err, st);
+  return n.kind == INRCT_SIREN ? launch_tile_t<1, INRCT_SIREN, false>(n, maps, P, grid, err, st)
+                               : launch_tile_t<1, INRCT_FFN_RELU, true>(n, maps, P, grid, err, st);
 }
 constexpr size_t kGemmSmem = (size_t)kGemmStages * kGemmStageBytes + 2048 + 1024;
 
 struct TcWeights {
   __nv_bfloat16* Wb[kMaxLayers];
   __nv_bfloat16* WbT[kMaxLayers];
+  __nv_bfloat16* Wlo[kMaxLayers];  // low parts of Wb for the split forward stages (ReLU networks)
   float* bias;
   float4* first;  // SIREN: W entries; FFN: F entries
   float* wout;    // W
@@ -1028,15 +1175,19 @@ struct TcWeights {
 // Layers handled by the MMA stages: FFN 0..L-1, SIREN 1..L-1 (the SIREN first layer is FP32).
 int first_mma_layer(const Net& n) { return n.kind == INRCT_SIREN ? 1 : 0; }
 
+// The VJP of a ReLU network runs its forward stages on split operands (see mlp_tile_kernel).
+bool split_vjp(const Net& n, int mode) { return mode == 1 && n.kind == INRCT_FFN_RELU; }
+
 // BF16 weights (and their transposes) plus FP32 biases, laid out in order.
 void weights_layout(const Net& n, Carver& c, TcWeights* w) {
   w->bias = c.take<float>((size_t)n.L * n.W);
   w->first = c.take<float4>((size_t)(n.kind == INRCT_SIREN ? n.W : n.F));
   w->wout = c.take<float>((size_t)n.W);
-  for (int l = 0; l < kMaxLayers; ++l) w->Wb[l] = w->WbT[l] = nullptr;
+  for (int l = 0; l < kMaxLayers; ++l) w->Wb[l] = w->WbT[l] = w->Wlo[l] = nullptr;
   for (int l = first_mma_layer(n); l < n.L; ++l) {
     w->Wb[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
     w->WbT[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
+    if (n.kind == INRCT_FFN_RELU) w->Wlo[l] = c.take<__nv_bfloat16>((size_t)n.in_dim[l] * n.out_dim[l]);
   }
 }
 
@@ -1060,6 +1211,7 @@ int prep_weights(const Net& n, const float* theta, const TcWeights& w, cudaStrea
     T.offb[i] = n.offb[l];
     T.Wb[i] = w.Wb[l];
     T.WbT[i] = w.WbT[l];
+    T.Wlo[i] = w.Wlo[l];
     T.bias[i] = w.bias + (int64_t)l * n.W;
     most = std::max<int64_t>(most, (int64_t)n.in_dim[l] * n.out_dim[l]);
   }
@@ -1126,6 +1278,13 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
     // a ring slot holds out_dim / kNSplit output rows x 64 K (see mlp_tile_kernel)
     INRCT_TRY(make_map(&maps->m[mi++], w.Wb[l], n.in_dim[l], n.out_dim[l], kKChunk, n.out_dim[l] / kNSplit,
                        2 * kKChunk));
+    P->st_map_lo[s] = -1;
+    if (split_vjp(n, mode)) {
+      INRCT_REQUIRE(w.Wlo[l] != nullptr, "tile kernel: no low parts of layer %d", l);
+      P->st_map_lo[s] = mi;
+      INRCT_TRY(make_map(&maps->m[mi++], w.Wlo[l], n.in_dim[l], n.out_dim[l], kKChunk,
+                         n.out_dim[l] / kNSplit, 2 * kKChunk));
+    }
     INRCT_REQUIRE(n.out_dim[l] == n.W, "tile kernel: MMA layer %d has %d outputs, expected %d", l,
                   n.out_dim[l], n.W);
   }
@@ -1137,6 +1296,7 @@ int build_prog(const Net& n, const TcWeights& w, int mode, TileProg* P, Maps* ma
       P->st_in_layer[s] = l;
       P->st_panels[s] = n.out_dim[l] / 64;
       P->st_map[s] = mi;
+      P->st_map_lo[s] = -1;
       // W'_l^T is [in][out]: rows = in (the MMA N), K = out; chunks of in / kNSplit rows
       INRCT_REQUIRE(n.in_dim[l] == n.W, "tile kernel: backward stage %d has N=%d, expected %d", l,
                     n.in_dim[l], n.W);
@@ -1197,12 +1357,11 @@ int tc_prepare(const Net& n, const float* theta, void* buf, size_t bytes, cudaSt
   return prep_weights(n, theta, w, st);
 }
 
-size_t tc_eval_ws_bytes(const Net& n) { return 256 + weights_bytes(n) + 256; }
+size_t tc_eval_ws_bytes(const Net& n) { return weights_bytes(n) + 256; }
 
 int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image, void* ws, size_t ws_bytes,
             cudaStream_t st, const void* prepared) {
   Carver c(ws, ws_bytes);
-  int* err = c.take<int>(64);
   TcWeights w;
   weights_layout(n, c, &w);
   if (!ws || !c.ok) {
@@ -1216,10 +1375,13 @@ int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image,
   } else {
     INRCT_TRY(prep_weights(n, theta, w, st));
   }
-  cudaMemsetAsync(err, 0, sizeof(int), st);
+  int* err = nullptr;
+  INRCT_TRY(status_word(st, &err));
   Maps maps;  // per call: the kernel takes a copy at launch
   TileProg P;
   INRCT_TRY(build_prog(n, w, 0, &P, &maps));
+  P.wait_ns = g_wait_ns.load();
+  P.stall = g_stall_loads.load();
   P.theta = theta;
   P.N = N;
   P.n_grid = npts;
@@ -1237,11 +1399,11 @@ int tc_eval(const Net& n, const float* theta, int N, int64_t npts, float* image,
 namespace {
 
 struct TcVjpWs {
-  int* err;
   TcWeights w;
   __nv_bfloat16 *E, *Act, *Dlt, *Sg, *Y16c, *Y16o;
   float* part;
   double* bias_part;
+  double* vloss_part;
   int64_t pad;
   size_t part_floats;
 };
@@ -1339,7 +1501,6 @@ GemmPlan plan_gemm(const Net& n, int64_t K, int64_t* part_floats, bool for_sizin
 size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* out, bool* ok) {
   Carver c(ws, cap);
   TcVjpWs w;
-  w.err = c.take<int>(64);
   weights_layout(n, c, &w.w);
   const int64_t pad = (chunk + kTile - 1) / kTile * kTile;
   w.pad = pad;
@@ -1353,7 +1514,8 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* ou
   plan_gemm(n, chunk, &pf, true);
   w.part_floats = (size_t)pf;
   w.part = c.take<float>((size_t)pf);
-  w.bias_part = c.take<double>(4 * 1024);  // 4 per tile-kernel CTA
+  w.bias_part = c.take<double>(4 * 1024);   // 4 per tile-kernel CTA
+  w.vloss_part = c.take<double>(4 * 1024);  // 4 per tile-kernel CTA
   if (out) *out = w;
   if (ok) *ok = c.ok;
   return c.off + 256;
@@ -1367,8 +1529,8 @@ size_t tc_vjp_ws_bytes(const Net& n, int64_t n_idx) {
 }
 
 int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t n_idx, const float* v,
-           double scale, double* grad_f64, float* grad_f32, void* ws, size_t ws_bytes, cudaStream_t st,
-           const void* prepared) {
+           double scale, double* grad_f64, float* grad_f32, double* value_out, void* ws, size_t ws_bytes,
+           cudaStream_t st, const void* prepared) {
   const int64_t chunk = n_idx < kVjpChunk ? n_idx : kVjpChunk;
   TcVjpWs w;
   bool ok;
@@ -1377,7 +1539,8 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     set_error("inr_weighted_vjp (bf16): workspace of %zu bytes too small (need %zu)", ws_bytes, need);
     return INRCT_ERR_WORKSPACE;
   }
-  cudaMemsetAsync(w.err, 0, sizeof(int), st);
+  int* err = nullptr;
+  INRCT_TRY(status_word(st, &err));
   if (prepared) {  // weights converted once by the caller (grad_step)
     Carver pc(const_cast<void*>(prepared), SIZE_MAX);
     weights_layout(n, pc, &w.w);
@@ -1387,6 +1550,8 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
   Maps tmaps, gmaps;  // per call: each launch takes a copy
   TileProg P;
   INRCT_TRY(build_prog(n, w.w, 1, &P, &tmaps));
+  P.wait_ns = g_wait_ns.load();
+  P.stall = g_stall_loads.load();
   P.theta = theta;
   P.N = N;
   int64_t ng = 1;
@@ -1405,7 +1570,9 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
   P.Y16c = w.Y16c;
   P.Y16o = w.Y16o;
   P.bias_part = w.bias_part;
+  P.vloss_part = w.vloss_part;
   P.npts_pad = w.pad;
+  const bool split = split_vjp(n, 1);  // one tile in flight per CTA, else two
   INRCT_TRY(set_smem_attr((const void*)tn_gemm_kernel, kGemmSmem));
   for (int64_t c0 = 0; c0 < n_idx; c0 += chunk) {
     const int64_t np = std::min(chunk, n_idx - c0);
@@ -1413,9 +1580,10 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     P.npts = np;
     const int64_t tiles = (np + kTile - 1) / kTile;
     if (c0 == 0) prof_mark(kMarkVjpKernel, st);
-    const int tile_grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 1) / 2, num_sms()));
+    const int64_t per_cta = split ? tiles : (tiles + 1) / 2;
+    const int tile_grid = (int)std::max<int64_t>(1, std::min<int64_t>(per_cta, num_sms()));
     INRCT_REQUIRE(tile_grid <= 1024, "tile grid %d exceeds the bias partial buffer", tile_grid);
-    INRCT_TRY(launch_tile(1, n, tmaps, P, tile_grid, w.err, st));
+    INRCT_TRY(launch_tile(1, n, tmaps, P, tile_grid, err, st));
     if (c0 == 0) prof_mark(kMarkVjpKernelDone, st);
     // split-K weight-gradient GEMMs over this chunk's points
     int64_t pf;
@@ -1432,12 +1600,15 @@ int tc_vjp(const Net& n, const float* theta, int N, const int32_t* idx, int64_t 
     }
     INRCT_TRY(make_map(&gmaps.m[3 * n.L], w.Act + (int64_t)(n.L - 1) * w.pad * n.W, n.W, np, 64, 64));
     INRCT_TRY(make_map(&gmaps.m[3 * n.L + 2], w.Y16o, w.pad, 16, 64, 16));
-    tn_gemm_kernel<<<G.cta_begin[G.n_jobs], 192, kGemmSmem, st>>>(gmaps, G, w.part, w.err);
+    G.wait_ns = P.wait_ns;
+    tn_gemm_kernel<<<G.cta_begin[G.n_jobs], 192, kGemmSmem, st>>>(gmaps, G, w.part, err);
     INRCT_CHECK_LAUNCH("tn gemm");
     int maxe = 0;
     for (int q = 0; q < G.n_jobs; ++q)
       maxe = std::max(maxe, G.job[q].M * (G.job[q].w_cols + 1));
     G.bpart = w.bias_part;
+    G.vpart = w.vloss_part;
+    G.value_out = value_out;
     G.n_bpart = 4 * tile_grid;
     G.off_bout = n.offb[n.L];
     gemm_reduce_kernel<<<dim3(ceil_div(maxe, 256), G.n_jobs + 1), 256, 0, st>>>(G, w.part, c0 > 0, grad_f64);
@@ -1489,7 +1660,7 @@ GemmPlan diag_plan(int64_t K, int M, int N, bool y16, int64_t* pf) {
 size_t gemm_tn_ws_bytes(int64_t K, int M, int N) {
   int64_t pf;
   diag_plan(K, M, N, true, &pf);
-  return 256 + align_up(sizeof(float) * pf, 256) + 256;
+  return align_up(sizeof(float) * pf, 256) + 256;
 }
 
 __global__ void sincospi_diag_kernel(const float* __restrict__ x, float* __restrict__ s, float* __restrict__ c,
@@ -1514,7 +1685,6 @@ int gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int
   int64_t pf;
   GemmPlan G = diag_plan(K, M, N, Y16 != nullptr, &pf);
   Carver c(ws, ws_bytes);
-  int* err = c.take<int>(64);
   float* part = c.take<float>((size_t)pf);
   if (!ws || !c.ok) {
     set_error("gemm_tn: workspace of %zu bytes too small (need %zu)", ws_bytes, gemm_tn_ws_bytes(K, M, N));
@@ -1524,7 +1694,9 @@ int gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int
   INRCT_TRY(make_map(&maps.m[0], X, M, K, 64, 64));
   if (N > 0) INRCT_TRY(make_map(&maps.m[1], Y, N, K, 64, 64));
   if (Y16) INRCT_TRY(make_map(&maps.m[2], Y16, K, 16, 64, 16));
-  cudaMemsetAsync(err, 0, sizeof(int), st);
+  int* err = nullptr;
+  INRCT_TRY(status_word(st, &err));
+  G.wait_ns = g_wait_ns.load();
   INRCT_TRY(set_smem_attr((const void*)tn_gemm_kernel, kGemmSmem));
   tn_gemm_kernel<<<G.cta_begin[1], 192, kGemmSmem, st>>>(maps, G, part, err);
   INRCT_CHECK_LAUNCH("tn gemm (diagnostic)");
@@ -1533,5 +1705,28 @@ int gemm_tn(const void* X, const void* Y, const void* Y16, int64_t K, int M, int
   INRCT_CHECK_LAUNCH("tn gemm reduce (diagnostic)");
   return INRCT_OK;
 }
+
+int tc_device_status(cudaStream_t st, int* code) {
+  int* word = nullptr;
+  INRCT_TRY(status_word(st, &word));
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, word, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(word, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error("device status: %s", cudaGetErrorString(e));
+    return INRCT_ERR_CUDA;
+  }
+  *code = h;
+  return INRCT_OK;
+}
+
+int tc_status_resolve(cudaStream_t st) {
+  int* word = nullptr;
+  return status_word(st, &word);
+}
+
+void tc_set_wait_limit(unsigned long long ns) { g_wait_ns.store(ns ? ns : kWaitTimeoutNs); }
+void tc_set_stall_loads(int on) { g_stall_loads.store(on ? 1 : 0); }
 
 }  // namespace inrct

@@ -20,7 +20,8 @@
 namespace inrct {
 namespace tc {
 
-constexpr uint64_t kWaitTimeoutNs = 1000000000ull;  // 1 s per wait, then the kernel gives up
+// Default limit of one bounded wait (1 s); the host may pass another (inrct_set_wait_limit).
+constexpr uint64_t kWaitTimeoutNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -62,37 +63,38 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for the phase of the given parity.  Gives up after kWaitTimeoutNs or as
-// soon as another role raised the abort flag; on its own timeout it raises the
-// flag and records `code` in the global error word.  Returns false on give-up.
+// Waits for the phase of the given parity.  Gives up after limit_ns or as soon as
+// another role raised the abort flag; on its own timeout it raises the flag and records
+// `code` in the global error word (the first code recorded is kept).  Returns false on
+// give-up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, int code) {
+                                          int* err, int code, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kWaitTimeoutNs) {
+    if (globaltimer() - t0 > limit_ns) {
       *abort_flag = 1;
-      atomicExch(err, code);
+      atomicCAS(err, 0, code);
       return false;
     }
   }
 }
 
-// Bounded wait that ignores the abort flag (used to drain in-flight MMAs).
-__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+// Bounded wait that ignores the abort flag (used to drain in-flight MMAs and copies).
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity))
-    if (globaltimer() - t0 > kWaitTimeoutNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   return true;
 }
 
 // Warp-uniform wait: lane 0 polls, the result is broadcast to the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, int code) {
+                                          int* err, int code, uint64_t limit_ns) {
   int ok = 1;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err, code) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err, code, limit_ns) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
   return ok != 0;
@@ -296,6 +298,28 @@ __device__ __forceinline__ void st_panel_row(uint8_t* panel, int r, int j0, cons
     w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
     w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
     w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+    *reinterpret_cast<uint4*>(panel + r * 128 + ((j ^ (r & 7)) << 4)) = w;
+  }
+}
+
+// The BF16 rounding of what BF16 rounding leaves of x: x = bf16(x) + bf16_rest(x) exactly,
+// since bf16(x) is within a factor 2 of x (Sterbenz); rounding the rest to BF16 again gives the
+// low part of a two-term BF16 split, about 2^-16 |x| accurate.
+__device__ __forceinline__ float bf16_rest(float x) {
+  return x - __uint_as_float(pack_bf16(x, x) & 0xffff0000u);
+}
+
+// As st_panel_row, for the low parts bf16(x - bf16(x)) of the CW values.
+template <int CW>
+__device__ __forceinline__ void st_panel_row_lo(uint8_t* panel, int r, int j0, const float* v) {
+#pragma unroll
+  for (int q = 0; q < CW / 8; ++q) {
+    const int j = j0 + q;
+    uint4 w;
+    w.x = pack_bf16(bf16_rest(v[8 * q + 0]), bf16_rest(v[8 * q + 1]));
+    w.y = pack_bf16(bf16_rest(v[8 * q + 2]), bf16_rest(v[8 * q + 3]));
+    w.z = pack_bf16(bf16_rest(v[8 * q + 4]), bf16_rest(v[8 * q + 5]));
+    w.w = pack_bf16(bf16_rest(v[8 * q + 6]), bf16_rest(v[8 * q + 7]));
     *reinterpret_cast<uint4*>(panel + r * 128 + ((j ^ (r & 7)) << 4)) = w;
   }
 }

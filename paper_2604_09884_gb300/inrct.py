@@ -97,6 +97,11 @@ def lib():
         "inrct_vjp_ws_bytes": ([m, gr, _I64], _SZ),
         "inr_weighted_vjp": ([m, _P, gr, _P, _I64, _P, ctypes.c_double, _P, _P, _P, _SZ, _P],
                              ctypes.c_int),
+        "inr_virtual_loss": ([m, _P, gr, _P, _I64, _P, ctypes.c_double, _P, _P, _P, _P, _SZ, _P],
+                             ctypes.c_int),
+        "inrct_device_status": ([_P], ctypes.c_int),
+        "inrct_set_wait_limit": ([ctypes.c_ulonglong], ctypes.c_int),
+        "inrct_debug_stall_weight_loads": ([ctypes.c_int], ctypes.c_int),
         "inrct_step_ws_bytes": ([g, gr, m, _I64], _SZ),
         "inrct_launch_count": ([], ctypes.c_longlong),
         "inrct_profile_begin": ([ctypes.c_int], ctypes.c_int),
@@ -354,6 +359,41 @@ def inr_weighted_vjp(mlp: MlpHandle, theta: torch.Tensor, N: int, idx: torch.Ten
     return (g64, g32) if want_f32 else g64
 
 
+def inr_virtual_loss(mlp: MlpHandle, theta: torch.Tensor, N: int, idx: torch.Tensor,
+                     v: torch.Tensor, scale: float, want_f32: bool = False, stream=None, fov: int = 0):
+    """The virtual loss of Eq. 3, scale * sum_k v[idx[k]] f(x_idx[k]) (FP64 [1]), and its gradient
+    (FP64, and FP32 if asked), both from one library call."""
+    L = lib()
+    grd = grid_desc(mlp.spec.d, N, fov)
+    dev = theta.device
+    val = torch.empty(1, dtype=torch.float64, device=dev)
+    g64 = torch.empty(mlp.p, dtype=torch.float64, device=dev)
+    g32 = torch.empty(mlp.p, dtype=torch.float32, device=dev) if want_f32 else None
+    nb = L.inrct_vjp_ws_bytes(ctypes.byref(mlp.desc), ctypes.byref(grd), idx.numel())
+    ws = _ws(nb, dev)
+    _check(L.inr_virtual_loss(ctypes.byref(mlp.desc), _ptr(theta, torch.float32, mlp.p, "theta"),
+                              ctypes.byref(grd), _ptr(idx, torch.int32, name="idx"), idx.numel(),
+                              _ptr(v, torch.float32, N ** mlp.spec.d, "v"), float(scale), _ptr(val), _ptr(g64),
+                              _ptr(g32), _ptr(ws), nb, _stream(stream)))
+    return (val, g64, g32) if want_f32 else (val, g64)
+
+
+def device_status(stream=None) -> None:
+    """Synchronise the stream and raise InrctError (TIMEOUT) if a bounded wait of a tensor-core
+    kernel gave up since the last check (inrct_device_status); clears the status."""
+    _check(lib().inrct_device_status(_stream(stream)))
+
+
+def set_wait_limit(ns: int) -> None:
+    """Limit of every bounded wait of later tensor-core launches, in ns (0: the default, 1 s)."""
+    _check(lib().inrct_set_wait_limit(int(ns)))
+
+
+def debug_stall_weight_loads(on: bool) -> None:
+    """Test hook: while on, the tile kernel issues no weight loads (its first MMA wait runs out)."""
+    _check(lib().inrct_debug_stall_weight_loads(1 if on else 0))
+
+
 def step_ws_bytes(g: synth.GeomSpec, mlp: MlpHandle, n_idx: int) -> int:
     gd, grd = geom_desc(g), grid_desc(g.d, g.N, g.fov)
     return int(lib().inrct_step_ws_bytes(ctypes.byref(gd), ctypes.byref(grd), ctypes.byref(mlp.desc),
@@ -481,22 +521,22 @@ def adam(lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, t=1) -> Adam:
 class InrVirtualLoss(torch.autograd.Function):
     """Virtual loss of Eq. (3): L~(theta) = scale * sum_{i in I} v_i f_theta(x_i), v held constant.
 
-    forward evaluates L~ with the library's VJP machinery absent: the value
-    needs f at the listed points only, taken from the full-grid evaluation
-    image E{f} that Algorithm 1 already produced (gathered here by index);
-    backward returns grad_out * the library's fused weighted VJP (Eq. 2), so
-    autograd through theta never stores per-point activations.
+    forward makes one library call, inr_virtual_loss, which runs the fused VJP at the listed
+    points and returns both the value (from the forward pass the VJP runs there) and the
+    gradient of Eq. (2); backward hands autograd that gradient times the incoming grad_out.
+    No per-point activation is kept between the two.
+
+    Usage: ``InrVirtualLoss.apply(theta, v, idx, scale, mlp, N)``; the result is a 0-d FP64
+    tensor, and ``backward()`` leaves the FP32 gradient in ``theta.grad``.
     """
 
     @staticmethod
-    def forward(ctx, theta, image, v, idx, scale, mlp, N):
-        ctx.save_for_backward(theta, v, idx)
-        ctx.scale, ctx.mlp, ctx.N = float(scale), mlp, int(N)
-        vi = v[idx.long()].double()
-        return (ctx.scale * (vi * image[idx.long()].double()).sum()).reshape(())
+    def forward(ctx, theta, v, idx, scale, mlp, N, fov=0):
+        value, grad = inr_virtual_loss(mlp, theta, int(N), idx, v, float(scale), fov=fov)
+        ctx.save_for_backward(grad)
+        return value.reshape(())
 
     @staticmethod
     def backward(ctx, grad_out):
-        theta, v, idx = ctx.saved_tensors
-        g = inr_weighted_vjp(ctx.mlp, theta, ctx.N, idx, v, ctx.scale)
-        return (grad_out.to(g.dtype) * g).to(theta.dtype), None, None, None, None, None, None
+        (grad,) = ctx.saved_tensors
+        return (grad_out.to(grad.dtype) * grad).to(torch.float32), None, None, None, None, None, None

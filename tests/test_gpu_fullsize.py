@@ -5,9 +5,11 @@ oracle's forward at those coordinates.  The VJP runs over the workload's whole i
 (|I| = n/4, 2^20 or 2^22 points, chunked exactly as in the benchmark) with v zero except at
 2000 listed points: every other term of Eq. 2 is then exactly zero, so the result must equal
 the oracle's VJP over those 2000 points.  Bars: BF16 evaluation 2e-2 relative L2 (as on
-small grids), BF16 gradient 1e-2 with cosine >= 0.999 (ReLU masks decided in BF16 on both
-sides, weight only on points whose BF16 decisions clear zero by 1e-3 of their layer's RMS),
-FP32 gradient 1e-4 (points within rounding of a ReLU kink are not given weight)."""
+small grids), BF16 gradient 1e-2 with cosine >= 0.999, FP32 gradient 1e-4.  The oracle
+decides every ReLU mask on its FP64 pre-activations; points with a pre-activation within
+1e-6 of its layer's RMS of zero (where FP32-accurate arithmetic may decide either way) are
+not given weight.  The ReLU workloads are checked at their initial parameters and at
+parameters the oracle itself trained for 30 Adam steps on a small cone scan."""
 import numpy as np
 import pytest
 import torch
@@ -72,27 +74,49 @@ def test_full_grid_evaluation_at_sampled_points(case):
     assert rel(got, want) <= (2e-2 if prec == inrct.BF16 else 1e-5)
 
 
-@pytest.mark.parametrize("case", CASES, ids=ids)
+_TRAINED = {}
+
+
+def oracle_trained_theta(w, oa, theta0, steps=30, lr=1e-3):
+    """theta0 after `steps` Adam steps of the oracle's Algorithm 1 (|I| = n, LS loss) on a small
+    cone scan (16^3 grid, 12 views of a 24 x 24 panel) of a 6-ellipsoid phantom: parameters as
+    training leaves them (units switched off, a smaller and less coherent gradient), computed by
+    the oracle alone."""
+    key = w.name
+    if key not in _TRAINED:
+        g = O.Geometry("cone3d", 16, 12, 24, 24, sod=64.0, sdd=96.0, span=2 * np.pi)
+        y = O.project(g, synth.phantom(3, 16, 6, 5))
+        I = np.arange(g.n)
+        th = np.asarray(theta0, np.float64)
+        st = O.AdamState(np.zeros_like(th), np.zeros_like(th))
+        for _ in range(steps):
+            th, _, _ = O.grad_step(oa, th, g, y, I, st, lr)
+        _TRAINED[key] = th.astype(np.float32)
+    return _TRAINED[key]
+
+
+VJP_CASES = CASES + [("cone3d_256_ffn256", inrct.BF16, "trained"), ("cone3d_501_ffn512", inrct.BF16, "trained")]
+
+
+def vjp_ids(c):
+    return ids(c) + ("_trained" if len(c) > 2 else "")
+
+
+@pytest.mark.parametrize("case", VJP_CASES, ids=vjp_ids)
 def test_full_index_set_vjp_with_sampled_weights(case):
-    name, prec = case
+    name, prec = case[:2]
     w, oa, B32, theta = setup(name)
+    if len(case) > 2:
+        theta = oracle_trained_theta(w, oa, theta)
     g = w.geom
     n_idx = g.n if (prec == inrct.FP32 and w.arch.kind == "siren") else w.batch  # FP32 path: |I| = n
     idx = synth.index_set(g.n, n_idx, 31)
     relu = w.arch.kind != "siren"
-    n_cand = 4 * N_SAMPLE if (relu and prec == inrct.BF16) else N_SAMPLE
-    pick = np.sort(np.random.default_rng(32).choice(n_idx, n_cand, replace=False))
+    pick = np.sort(np.random.default_rng(32).choice(n_idx, N_SAMPLE, replace=False))
     live = idx[pick].astype(np.int64)
-    X = O.grid_coords(g.d, g.N, live)
-    if relu and prec == inrct.FP32:
-        live = live[kink_free(oa, theta, X, g.N)]
-    elif relu:
-        # BF16 masks: the kernel sums the BF16 operands on tensor cores, the oracle in FP64;
-        # where a pre-activation lies within rounding of zero (or a rounding difference
-        # upstream moves it across) both masks are valid, so those points get no weight
-        mg = O.bf16_decision_margins(oa, theta, O.grid_coords_fp32(g.d, g.N, live))
-        live = live[mg >= 1e-3][:N_SAMPLE]
-        assert live.size >= N_SAMPLE // 2
+    if relu:
+        live = live[kink_free(oa, theta, O.grid_coords(g.d, g.N, live), g.N)]
+        assert live.size >= 0.9 * N_SAMPLE
     X = O.grid_coords(g.d, g.N, live)
     vals = np.random.default_rng(33).normal(size=live.size)
     v = torch.zeros(g.n, dtype=torch.float32, device="cuda")
@@ -102,10 +126,8 @@ def test_full_index_set_vjp_with_sampled_weights(case):
     got = inrct.inr_weighted_vjp(h, torch.tensor(theta, device="cuda"), g.N,
                                  torch.from_numpy(idx).cuda(), v, scale).cpu().numpy()
     wv = scale * vals.astype(np.float32).astype(np.float64)
+    want = O.vjp(oa, theta.astype(np.float64), X, wv, N=g.N)
     if prec == inrct.BF16:
-        want = O.vjp(oa, theta.astype(np.float64), X, wv, decide="bf16", X32=O.grid_coords_fp32(g.d, g.N, live),
-                     N=g.N)
         assert rel(got, want) <= 1e-2 and cos(got, want) >= 0.999, (rel(got, want), cos(got, want))
     else:
-        want = O.vjp(oa, theta.astype(np.float64), X, wv, N=g.N)
         assert rel(got, want) <= 1e-4, rel(got, want)

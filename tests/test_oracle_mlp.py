@@ -233,55 +233,3 @@ def test_adam_first_step_closed_form():
     np.testing.assert_allclose(th, -0.1 * g / (np.abs(g) + 1e-8), rtol=1e-14, atol=0)
 
 
-def test_bf16_round_matches_torch_and_ties_to_even():
-    assert O.bf16_round(1.0) == 1.0
-    assert O.bf16_round(1 + 2.0 ** -8) == 1.0                      # tie -> even mantissa
-    assert O.bf16_round(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6        # tie -> even mantissa
-    x = np.random.default_rng(0).normal(size=10000) * 10.0 ** np.random.default_rng(1).integers(-8, 8, 10000)
-    want = torch.tensor(x.astype(np.float32)).bfloat16().double().numpy()
-    np.testing.assert_array_equal(O.bf16_round(x.astype(np.float32)), want)
-
-
-def test_bf16_decided_masks_give_the_frozen_mask_gradient():
-    # With ReLU masks decided on the BF16-rounded chain, the oracle's gradient is
-    # the gradient of the network whose ReLUs are replaced by multiplication with
-    # those (constant) masks: check against torch autograd of that network.
-    arch = _arch("ffn", d=3, width=16, n_hidden=3, n_feat=8)
-    theta = _theta(arch, 9)
-    X = np.random.default_rng(10).uniform(-1, 1, (40, 3))
-    w = np.random.default_rng(11).normal(size=40)
-    _, _, zs, masks = O.forward(arch, theta, X, keep=True, decide="bf16")
-    # the decisions differ from the FP64 ones only near the kink
-    for z, m in zip(zs[:-1], masks):
-        diff = m != (z > 0)
-        assert (np.abs(z[diff]) < 2e-2 * np.sqrt((z ** 2).mean())).all()
-    th = torch.tensor(theta, requires_grad=True)
-    P = 2 * math.pi * torch.tensor(X) @ torch.tensor(arch.B).T
-    h = torch.cat([torch.cos(P), torch.sin(P)], 1)
-    off = 0
-    for li, (o, i) in enumerate(arch.layer_shapes()):
-        W = th[off:off + o * i].view(o, i)
-        off += o * i
-        b = th[off:off + o]
-        off += o
-        h = torch.nn.functional.linear(h, W, b)
-        if li < len(masks):
-            h = h * torch.tensor(masks[li], dtype=torch.float64)
-    (h[:, 0] @ torch.tensor(w)).backward()
-    np.testing.assert_allclose(O.vjp(arch, theta, X, w, decide="bf16"), th.grad.numpy(),
-                               rtol=1e-11, atol=1e-12)
-    s_arch = _arch("siren", width=8)
-    s_th = _theta(s_arch, 2)
-    np.testing.assert_array_equal(O.vjp(s_arch, s_th, X[:, :2], w, decide="bf16"),
-                                  O.vjp(s_arch, s_th, X[:, :2], w))
-
-
-def test_fp32_grid_coords_are_the_nearest_fp32_centres():
-    from fractions import Fraction
-    for N in (7, 67, 501):
-        X32 = O.grid_coords_fp32(2, N)[:N, 0]
-        for k in range(N):
-            exact = Fraction(2 * k + 1 - N, N)
-            x = float(X32[k])
-            ulp = float(np.spacing(np.float32(abs(x)))) if x != 0 else 2.0 ** -149
-            assert abs(Fraction(x) - exact) <= Fraction(ulp) / 2
