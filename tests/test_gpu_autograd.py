@@ -92,4 +92,36 @@ def test_virtual_loss_backward_scales_with_the_incoming_gradient():
     g1 = theta.grad.clone()
     theta.grad = None
     inrct.InrVirtualLoss.apply(theta, v, idx, 2.0, mlp, N).backward()
-    assert torch.equal(g1, 3.0 * theta.grad)
+    # grad_out * g is formed in FP64 and then rounded to FP32: equal to an FP32 ulp
+    assert torch.allclose(g1, 3.0 * theta.grad, rtol=2e-7, atol=0)
+
+
+def test_virtual_loss_fp32_path_matches_the_oracle():
+    """The FP32 SIMT path of inr_virtual_loss: value (Eq. 3) and gradient (Eq. 2) against the
+    oracle at the FP32 bars (1e-5 value relative to sum |w f|, 1e-4 gradient)."""
+    spec = synth.ArchSpec("ffn", 3, 128, 3, n_feat=64, sigma=4.0)
+    N = 20
+    n = N ** 3
+    dev = torch.device("cuda")
+    B32 = synth.fourier_matrix(spec.n_feat, 3, spec.sigma, 6).astype(np.float32)
+    oa = O.Arch("ffn", 3, spec.width, spec.n_hidden, spec.n_feat, B32.astype(np.float64))
+    theta32 = synth.init_theta(spec, 7).astype(np.float32)
+    idx = synth.index_set(n, 3000, 8)
+    _, _, zs, _ = O.forward(oa, theta32.astype(np.float64), O.grid_coords(3, N, idx), keep=True)
+    ok = np.ones(idx.size, bool)
+    for z in zs[:-1]:
+        ok &= (np.abs(z) >= 1e-6 * np.sqrt((z ** 2).mean())).all(axis=1)
+    idx = idx[ok].astype(np.int32)
+    vv = np.random.default_rng(9).normal(size=n).astype(np.float32)
+    scale = n / idx.size
+    mlp = inrct.mlp_desc(spec, inrct.FP32, B32, device=dev)
+    theta = torch.tensor(theta32, device=dev, requires_grad=True)
+    loss = inrct.InrVirtualLoss.apply(theta, torch.from_numpy(vv).to(dev), torch.from_numpy(idx).to(dev),
+                                      scale, mlp, N)
+    loss.backward()
+    X = O.grid_coords(3, N, idx)
+    wv = scale * vv.astype(np.float64)[idx]
+    f = O.forward(oa, theta32.astype(np.float64), X)
+    assert abs(loss.item() - float(wv @ f)) <= 1e-5 * float(np.abs(wv * f).sum())
+    want = O.vjp(oa, theta32.astype(np.float64), X, wv)
+    assert rel(theta.grad.double().cpu().numpy(), want) <= 1e-4

@@ -38,7 +38,10 @@ def test_a_wait_that_runs_out_is_reported_and_the_next_call_succeeds(kind):
         inrct.inr_eval_grid(mlp, theta, N)                  # returns OK: launches are asynchronous
         with pytest.raises(inrct.InrctError) as e:
             inrct.device_status()
-        assert e.value.code == 5 and "code 303" in str(e.value), str(e.value)
+        # the MMA issuer's wait for the first weight chunk (303) or, when the first stage streams
+        # more than four input panels, the epilogue's wait for a free panel buffer (401) runs
+        # out first: both wait on the loads that never come
+        assert e.value.code == 5 and ("code 303" in str(e.value) or "code 401" in str(e.value)), str(e.value)
         inrct.inr_weighted_vjp(mlp, theta, N, idx, v, 2.0)
         with pytest.raises(inrct.InrctError) as e:
             inrct.device_status()
