@@ -35,6 +35,63 @@ __device__ __forceinline__ float grid_coord(int64_t k, int N) {
   return __fdiv_rn((float)(2 * k + 1 - N), (float)N);
 }
 
+// Integer numerators m_a = 2 k_a + 1 - N of the pixel-centre coordinates x_a = m_a / N of grid
+// point i (x fastest; m_2 = 0 in 2-D).  Exact, |m_a| < N <= 4096.
+__device__ __forceinline__ void point_numerators(int64_t i, int N, int d, int* m) {
+  int64_t ix, iy, iz;
+  if ((uint64_t)i <= 0xffffffffull) {
+    const uint32_t u = (uint32_t)i, n = (uint32_t)N;
+    const uint32_t q = u / n, q2 = q / n;
+    ix = u - q * n;
+    iy = q - q2 * n;
+    iz = q2;
+  } else {
+    ix = i % N;
+    iy = (i / N) % N;
+    iz = i / ((int64_t)N * N);
+  }
+  m[0] = (int)(2 * ix + 1 - N);
+  m[1] = (int)(2 * iy + 1 - N);
+  m[2] = d == 3 ? (int)(2 * iz + 1 - N) : 0;
+}
+
+// Error-free sum: a + b = s + e exactly (Knuth's two-sum, no ordering assumption).
+__device__ __forceinline__ float two_sum(float a, float b, float* e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  *e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// Phase of a Fourier feature, B . x reduced modulo 1 to t in about [-1/2, 1/2], for the grid
+// point with coordinate numerators m (x_a = m_a / N), accurate to about an FP32 ulp of t.
+// With x_a = m_a / N the phase is (sum_a B_a m_a) / N: each product B_a m_a (m_a is an exact
+// FP32 integer) is p + e exactly by an FMA, the products are added with error-free sums into a
+// head s and a tail, the quotient by N is q = s / N with the exact remainder s - q N (an FMA),
+// and t = (q - rint q) + (remainder + tail) / N.  Forming B . x from rounded coordinates in FP32
+// instead leaves an absolute phase error of about |B . x| 2^-24 (2e-6 at |B . x| = 30), which
+// moves features by about 2 pi times that: enough to flip the ReLU masks of units within
+// 1e-5 of their RMS of zero.
+__device__ __forceinline__ float ffn_phase_exact(float b0, float b1, float b2, const int* m, int d, int N) {
+  const float m0 = (float)m[0], m1 = (float)m[1], m2 = (float)m[2];
+  const float p0 = __fmul_rn(b0, m0), e0 = __fmaf_rn(b0, m0, -p0);
+  const float p1 = __fmul_rn(b1, m1), e1 = __fmaf_rn(b1, m1, -p1);
+  float t1;
+  float s = two_sum(p0, p1, &t1);
+  float tail = __fadd_rn(__fadd_rn(e0, e1), t1);
+  if (d == 3) {
+    const float p2 = __fmul_rn(b2, m2), e2 = __fmaf_rn(b2, m2, -p2);
+    float t2;
+    s = two_sum(s, p2, &t2);
+    tail = __fadd_rn(tail, __fadd_rn(e2, t2));
+  }
+  const float fN = (float)N;
+  const float q = __fdiv_rn(s, fN);
+  const float r = __fmaf_rn(-q, fN, s);  // s - q N, exact for a correctly rounded quotient
+  const float t = __fsub_rn(q, rintf(q));
+  return __fadd_rn(t, __fdiv_rn(__fadd_rn(r, tail), fN));
+}
+
 // Coordinates of grid point i (x fastest).  Indices below 2^32 take 32-bit divisions (the
 // 64-bit ones are a long instruction sequence, on the path of every tile's set-up).
 __device__ __forceinline__ void point_coords(int64_t i, int N, int d, float* x) {

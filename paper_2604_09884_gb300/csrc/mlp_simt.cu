@@ -292,10 +292,11 @@ __global__ void __launch_bounds__(256)
     for (int e = t; e < TP * net.F; e += W) {
       const int p = e / net.F, f = e % net.F;
       const float* Bf = net.B + (int64_t)f * net.d;
-      float ph = Bf[0] * xs[p][0] + Bf[1] * xs[p][1];
-      if (net.d == 3) ph += Bf[2] * xs[p][2];
+      const int m[3] = {2 * ks[p][0] + 1 - net.N, 2 * ks[p][1] + 1 - net.N,
+                        net.d == 3 ? 2 * ks[p][2] + 1 - net.N : 0};
+      const float t = ffn_phase_exact(Bf[0], Bf[1], net.d == 3 ? Bf[2] : 0.f, m, net.d, net.N);
       float s, c;
-      sincospif(2.f * ph, &s, &c);
+      sincospif(2.f * t, &s, &c);
       bufA[p * Kmax + f] = c;
       bufA[p * Kmax + net.F + f] = s;
     }

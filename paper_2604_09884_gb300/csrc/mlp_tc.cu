@@ -831,20 +831,22 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
       const int64_t tile0 = blockIdx.x + (NSLOT * pr) * (int64_t)gridDim.x;
       const int64_t tile1 = tile0 + gridDim.x;  // two slots only; may be past the end: a dummy tile
       float x0[3], x1[3] = {0.f, 0.f, 0.f}, sv0, sv1 = 0.f;
+      int m0[3] = {0, 0, 0}, m1[3] = {0, 0, 0};  // coordinate numerators (exact FFN phases, VJP)
       bool valid0, valid1 = false;
       {
-        auto setup = [&](int64_t tile, float* x, float& sv, bool& valid) {
+        auto setup = [&](int64_t tile, float* x, int* m, float& sv, bool& valid) {
           const int64_t pt = tile * kTile + r;
           valid = pt < P.npts;
           int64_t gi = valid ? (P.idx ? (int64_t)P.idx[pt] : pt) : 0;
           const bool in_range = gi >= 0 && gi < P.n_grid;
           if (!in_range) gi = 0;
           point_coords(gi, P.N, P.d, x);
+          if (MODE == 1 && KIND == INRCT_FFN_RELU) point_numerators(gi, P.N, P.d, m);
           const bool weighted = valid && in_range && (!P.fov || in_fov(gi, P.N));
           sv = (MODE == 1 && weighted) ? P.scale * P.v[gi] : 0.f;
         };
-        setup(tile0, x0, sv0, valid0);
-        if (NSLOT == 2) setup(tile1, x1, sv1, valid1);
+        setup(tile0, x0, m0, sv0, valid0);
+        if (NSLOT == 2) setup(tile1, x1, m1, sv1, valid1);
       }
       if (MODE == 1 && g == 0) bsum += (double)sv0 + (double)sv1;
       // ---- first stage input ----
@@ -853,6 +855,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
         const bool store_t = (t ? tile1 : tile0) < n_tiles;      // dummy tiles write nowhere
         const int64_t tile_t = t ? tile1 : tile0;
         const float xt[3] = {t ? x1[0] : x0[0], t ? x1[1] : x0[1], t ? x1[2] : x0[2]};
+        const int mt[3] = {t ? m1[0] : m0[0], t ? m1[1] : m0[1], t ? m1[2] : m0[2]};
         if (MODE == 1 && pr > 0) {
           // the previous group's last deltas are still being stored from these panels
           if (!warp_wait(&st_done[t], (sdp >> t) & 1u, abort_flag, err, 405, lim)) goto epi_done;
@@ -867,9 +870,14 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const float4 bf = P.first_staged ? first_s[f0 + i] : __ldg(P.first + f0 + i);
-              float ph = __fadd_rn(__fmul_rn(bf.x, xt[0]), __fmul_rn(bf.y, xt[1]));
-              if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, xt[2]));
-              four_feat2(ph, &v[8 + i], &v[i]);  // v[0..7] cos, v[8..15] sin
+              if (MODE == 1) {
+                // the VJP decides ReLU masks downstream: the phase to an FP32 ulp of t
+                feat_sincos(ffn_phase_exact(bf.x, bf.y, bf.z, mt, P.d, P.N), &v[8 + i], &v[i]);
+              } else {
+                float ph = __fadd_rn(__fmul_rn(bf.x, xt[0]), __fmul_rn(bf.y, xt[1]));
+                if (P.d == 3) ph = __fadd_rn(ph, __fmul_rn(bf.z, xt[2]));
+                four_feat2(ph, &v[8 + i], &v[i]);  // v[0..7] cos, v[8..15] sin
+              }
             }
             if (MODE == 1 && store_t) {
               store_row_bf16<8>(P.E + prow_t * (2 * P.F) + 64 * c + 8 * g, v);

@@ -95,7 +95,8 @@ def oracle_trained_theta(w, oa, theta0, steps=30, lr=1e-3):
     return _TRAINED[key]
 
 
-VJP_CASES = CASES + [("cone3d_256_ffn256", inrct.BF16, "trained"), ("cone3d_501_ffn512", inrct.BF16, "trained")]
+VJP_CASES = CASES + [("cone3d_256_ffn256", inrct.BF16, "trained"), ("cone3d_501_ffn512", inrct.BF16, "trained"),
+                     ("cone3d_256_ffn256", inrct.FP32), ("cone3d_501_ffn512", inrct.FP32)]
 
 
 def vjp_ids(c):
