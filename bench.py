@@ -4,9 +4,11 @@ One step is Algorithm 1 of the paper followed by an Adam update, through the
 library's grad_step: grid evaluation of the INR (tcgen05 BF16 MLP), Joseph
 projection with the LS loss epilogue, exact adjoint backprojection, the fused
 residual-weighted VJP at |I| sampled points, weight-gradient GEMM, FP64
-reduction, Adam.  Workload (default): 512^2 fan beam, 90 views over 360 deg,
-729 curved bins, SOD/SDD 1000/1500, SIREN 5 x 256 (omega0 = 30), |I| = n/4,
-synthetic 20-ellipse phantom with 1 % noise.
+reduction, Adam.  Workload (default, the largest single-GPU configuration): 501^3 cone
+beam, 60 views over 360 deg, 768 x 768 flat panel, SOD/SDD 1000/1500, Fourier features 512
+(sigma 8) + 5 x 256 ReLU, |I| = 2^22, synthetic 40-ellipsoid phantom with 1 % noise.  The same
+line carries, under "fan2d_512_siren256", the figures of the 512^2 fan beam workload (90 views,
+729 curved bins, SIREN 5 x 256, |I| = n/4).
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
 Under torchrun every rank runs an independent replica (weak scaling, no
@@ -33,6 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "INR-CT grad steps/s, proj+backproj GRays/s; BF16 vs FP32 at <=1e-2 grad err"
 L2_BYTES = 129 * 1024 * 1024
 BATCHED = "batched16_siren128"
+HEADLINE = "cone3d_501_ffn512"       # the default workload: the largest single-GPU configuration
+SECONDARY = "fan2d_512_siren256"     # carried in the default line as an extra key
 VJP_CHUNK = 1 << 20          # points per VJP chunk (the library's scratch unit)
 # FP32 FMA peak of the SIMT path: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -44,7 +48,12 @@ def parse():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="fan2d_512_siren256")
+    p.add_argument("--workload", default=HEADLINE)
+    p.add_argument("--no-secondary", action="store_true",
+                   help=f"default workload only: skip the {SECONDARY} figures carried in the line")
+    p.add_argument("--secondary-steps", type=int, default=1000, help=f"timed steps of {SECONDARY}")
+    p.add_argument("--projector-only", action="store_true",
+                   help="time the projector P and its adjoint alone on the workload's geometry")
     p.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     p.add_argument("--frac", type=float, default=None, help="|I|/n (default: the workload's)")
     p.add_argument("--loss", default="ls", choices=["ls", "fls"])
