@@ -412,11 +412,359 @@ def run_batched(args, probs, rank, world, local, dev):
     batch.close()
 
 
+def projector_roofline(g, m_step, per, hbm_peak, peak_src, name):
+    """Rates of P and P^T from the stage profile against the measured HBM bandwidth, under both
+    byte models: compulsory bytes (P: image in, sinogram, residual out and y in: 4n + 12m;
+    P^T: sinogram in, image out: 4n + 4m) and the per-view streaming model (the image read once
+    per view, 4nV + 4m, and 12m / 4m of sinogram traffic), with the DRAM bytes per launch of the
+    committed ncu record where one matches the current source."""
+    out = {}
+    V = g.V
+    for key, stage, sino_bytes, traffic_key in (("project", "project_loss", 12.0, "project3d_kernel" if g.d == 3
+                                                 else "project2d_kernel"),
+                                                ("backproject", "backproject", 4.0, "backproject3d_kernel" if g.d == 3
+                                                 else "backproject2d_tile_kernel")):
+        ms = per[stage]
+        if ms <= 0:
+            continue
+        comp = 4.0 * g.n + sino_bytes * m_step
+        stream = 4.0 * g.n * V + sino_bytes * m_step
+        out[key] = {"ms": ms, "GRays/s": m_step / ms / 1e6,
+                    "compulsory_bytes": comp, "streaming_bytes": stream,
+                    "achieved_GB/s_compulsory": comp / ms / 1e6, "achieved_GB/s_streaming": stream / ms / 1e6,
+                    "frac_compulsory": comp / ms / 1e6 / hbm_peak, "frac_streaming": stream / ms / 1e6 / hbm_peak,
+                    "peak": hbm_peak, "peak_source": f"{peak_src} (HBM copy)",
+                    "traffic": recorded_traffic(traffic_key, name)}
+    return out
+
+
+def build_problem(w, rank, dev, prec_name):
+    """The workload's synthetic problem, resident on the device: phantom, noisy data, network."""
+    import torch
+
+    from paper_2604_09884_gb300 import inrct, synth
+    g, a = w.geom, w.arch
+    seed = w.seed + 1000 * rank                      # every replica its own problem
+    x_true = torch.tensor(synth.phantom(g.d, g.N, w.n_shapes, seed).reshape(-1), dtype=torch.float32,
+                          device=dev)
+    y_clean = inrct.project(g, x_true)
+    y = torch.tensor(synth.noisy(y_clean.cpu().numpy(), w.noise, seed + 1), device=dev)
+    del y_clean
+    B = synth.fourier_matrix(a.n_feat, a.d, a.sigma, seed + 2) if a.kind == "ffn" else None
+    prec = inrct.BF16 if prec_name == "bf16" else inrct.FP32
+    mlp = inrct.mlp_desc(a, prec, B, device=dev)
+    theta = torch.tensor(synth.init_theta(a, seed + 3), dtype=torch.float32, device=dev)
+    return {"seed": seed, "x_true": x_true, "y": y, "B": B, "mlp": mlp, "theta": theta}
+
+
+def run_projector_only(args, w, rank, world, local, dev):
+    """P and P^T alone on the workload's geometry (tuned plans), CUDA-event timed per call with
+    L2 flushed in between; used by the projector profiles."""
+    import torch
+
+    from paper_2604_09884_gb300 import inrct, synth
+    g = w.geom
+    x = torch.tensor(synth.phantom(g.d, g.N, w.n_shapes, w.seed).reshape(-1), dtype=torch.float32, device=dev)
+    y = inrct.project(g, x)
+    if args.plan:
+        inrct.tune_set(g, *(int(q) for q in args.plan.split(",")))
+        plan = inrct.tune_plan(g)
+    else:
+        plan = inrct.tune(g, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, fn in (("project", lambda: inrct.project(g, x, y)), ("backproject", lambda: inrct.backproject(g, y))):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[name] = {"ms_median": statistics.median(ts), "ms_min": min(ts), "GRays/s": g.m / statistics.median(ts) / 1e6}
+    if rank == 0:
+        print(json.dumps({"mode": "projector-only", "workload": w.name, "rays": g.m, "voxels": g.n,
+                          "plan": plan, "calls": args.steps, "timing": res,
+                          "note": "each call includes its ray-table set-up; L2 flushed between calls"}), flush=True)
+
+
+def run_single(args, w, rank, world, local, dev, steps, warmup, e2e_steps, cpu_budget, headline):
+    """One workload: timed steps, end-to-end steps, and the figures of the line (rank 0 gets the
+    line as a dict; other ranks None).  Large workloads (n > 2^24) compare against one FP32
+    full gradient instead of timed FP32 steps and skip the |I|/n sweep."""
+    import torch
+
+    from paper_2604_09884_gb300 import inrct, synth
+    g, a = w.geom, w.arch
+    big = g.n > (1 << 24)
+    pb = build_problem(w, rank, dev, args.prec)
+    x_true, y, B, mlp, theta = pb["x_true"], pb["y"], pb["B"], pb["mlp"], pb["theta"]
+    seed = pb["seed"]
+    m = torch.zeros_like(theta)
+    s = torch.zeros_like(theta)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    n_idx = w.batch
+    scale = g.n / n_idx
+    ws = torch.empty(inrct.step_ws_bytes(g, mlp, n_idx), dtype=torch.uint8, device=dev)
+    loss_kind = inrct.LOSS_FLS if args.loss == "fls" else inrct.LOSS_LS
+    # index sets: a fresh uniform subset per step (drawn on the host, staged in HBM)
+    n_sets = 4 if big else 16
+    idx_host = [torch.from_numpy(synth.index_set(g.n, n_idx, seed + 10 + k)).pin_memory()
+                for k in range(n_sets)]
+    idx_dev = [t.to(dev) for t in idx_host]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    S = max(1, args.subsets)
+    sub_g = [inrct.view_subset(g, S, k) for k in range(S)] if S > 1 else [g]
+    sub_y = [inrct.view_subset_rows(g, y, S, k) for k in range(S)] if S > 1 else [y]
+    sub_ws = [ws] if S == 1 else [torch.empty(inrct.step_ws_bytes(q, mlp, n_idx), dtype=torch.uint8, device=dev)
+                                  for q in sub_g]
+    # projector launch shapes: the library's autotuner, once per geometry, before any timing
+    # (or a plan pinned on the command line, e.g. to reproduce a measurement's launch shapes)
+    if args.plan:
+        seg, bp, zc = (int(x) for x in args.plan.split(","))
+        for q in sub_g:
+            inrct.tune_set(q, seg, bp, zc)
+        plans = [inrct.tune_plan(q) for q in sub_g]
+    else:
+        plans = [inrct.tune(q, device=dev) for q in sub_g]
+
+    def step(t, idx):
+        k = t % S
+        inrct.grad_step(sub_g[k], mlp, theta, sub_y[k], idx, scale, inrct.adam(lr=w.lr, t=t), m, s, loss,
+                        None, sub_ws[k], loss_kind)
+
+    t = 0
+    for _ in range(warmup):
+        t += 1
+        step(t, idx_dev[t % n_sets])
+    torch.cuda.synchronize()
+    inrct.device_status()
+
+    # ---- timed region (device): inputs resident, L2 flushed between steps (untimed) ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    prof_steps = min(steps, 256)
+    inrct.profile_begin(prof_steps)
+    l0 = inrct.launch_count()
+    with ClockSampler(local) as clk:
+        for k in range(steps):
+            flush.zero_()
+            t += 1
+            starts[k].record(stream)
+            step(t, idx_dev[t % n_sets])
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    launches = inrct.launch_count() - l0
+    stages, nprof = inrct.profile_end()
+    inrct.device_status()                            # no bounded wait gave up in the timed steps
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [st.elapsed_time(en) for st, en in zip(starts, ends)]
+    value, total_s = job_rate(steps, sum(step_ms) / 1000.0, world, dev)
+    ms_per_step = 1000.0 * total_s / steps
+
+    # ---- end to end through the public API, host buffers, copies inside the timed region ----
+    loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(e2e_steps, steps))
+    idx_stage = torch.empty_like(idx_dev[0])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        t += 1
+        idx_stage.copy_(idx_host[t % n_sets], non_blocking=True)
+        step(t, idx_stage)
+        loss_host.copy_(loss, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_value, e2e_s = job_rate(e2e_steps, time.perf_counter() - t0, world, dev)
+    peak_mem = torch.cuda.max_memory_allocated(dev)
+    del idx_stage
+
+    # ---- reconstruction error of the trained INR, and other subsampling fractions ----
+    with torch.no_grad():
+        img = inrct.inr_eval_grid(mlp, theta, g.N)
+        mse = float(((img - x_true) ** 2).mean())
+        del img
+    fractions = {f"{n_idx / g.n:.4g}": {"steps_per_s": value / world, "batch": n_idx}}
+    if not args.no_fractions and not big:
+        for f in (1.0, 0.05):
+            nI = max(1, int(round(f * g.n)))
+            wsf = torch.empty(inrct.step_ws_bytes(g, mlp, nI), dtype=torch.uint8, device=dev)
+            idxf = torch.from_numpy(synth.index_set(g.n, nI, seed + 99)).to(dev)
+            thf, mf, sf = theta.clone(), torch.zeros_like(theta), torch.zeros_like(theta)
+            kf = 20
+            for tf in range(1, 3 + kf):
+                if tf == 3:
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                inrct.grad_step(g, mlp, thf, y, idxf, g.n / nI, inrct.adam(lr=w.lr, t=tf), mf, sf, None, None,
+                                wsf, loss_kind)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fractions[f"{f:.4g}"] = {"steps_per_s": 1000.0 * kf / e0.elapsed_time(e1), "batch": nI,
+                                     "timing": f"{kf} steps back to back, L2 not flushed"}
+            del wsf
+
+    # ---- the plain FP32 path and the BF16 / FP32 gradient agreement ----
+    fp32 = None
+    if args.prec == "bf16" and not args.no_fp32:
+        mlp32 = inrct.mlp_desc(a, inrct.FP32, B, device=dev)
+
+        def agree(ga, gb):
+            return {"rel_l2": float(torch.linalg.norm(ga - gb) / torch.linalg.norm(gb)),
+                    "cosine": float(torch.dot(ga, gb) / (torch.linalg.norm(ga) * torch.linalg.norm(gb)))}
+
+        # one estimator at the current theta: v = P^T r of the FP32 image, the same index set
+        img = inrct.inr_eval_grid(mlp32, theta, g.N)
+        _, r, _ = inrct.project(g, img, y)
+        del img
+        vfull = inrct.backproject(g, r)
+        del r
+        g16 = inrct.inr_weighted_vjp(mlp, theta, g.N, idx_dev[0], vfull, scale)
+        g32 = inrct.inr_weighted_vjp(mlp32, theta, g.N, idx_dev[0], vfull, scale)
+        same_I = dict(agree(g16, g32), batch=n_idx, v="P^T (P f_theta - y) at the current theta")
+        del g32
+        torch.cuda.reset_peak_memory_stats(dev)
+        idx_all = torch.arange(g.n, dtype=torch.int32, device=dev)
+        ws32 = torch.empty(inrct.step_ws_bytes(g, mlp32, g.n), dtype=torch.uint8, device=dev)
+        th32 = theta.clone()
+        loss32 = torch.zeros(1, dtype=torch.float64, device=dev)
+        if big:
+            # the plain FP32 form once: the full gradient (|I| = n) at the current theta, timed
+            gfull = torch.empty(a.p, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inrct.grad_step(g, mlp32, th32, y, idx_all, 1.0, None, None, None, loss32, gfull, ws32, loss_kind)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            k32, ms32 = 1, e0.elapsed_time(e1)
+            full = dict(agree(g16, gfull), note="the BF16 estimator (|I| = batch, the same theta and v) against "
+                                                "the FP32 full gradient (|I| = n): subsampling and precision")
+            del gfull
+        else:
+            m32, s32 = torch.zeros_like(theta), torch.zeros_like(theta)
+            for t32 in range(1, 3):
+                inrct.grad_step(g, mlp32, th32, y, idx_all, 1.0, inrct.adam(lr=w.lr, t=t32), m32, s32, loss32,
+                                None, ws32, loss_kind)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k32 = max(1, args.fp32_steps)
+            e0.record(stream)
+            for t32 in range(3, 3 + k32):
+                inrct.grad_step(g, mlp32, th32, y, idx_all, 1.0, inrct.adam(lr=w.lr, t=t32), m32, s32, loss32,
+                                None, ws32, loss_kind)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms32 = e0.elapsed_time(e1) / k32
+            full = None
+        inrct.device_status()
+        fp32 = {"steps_per_s": 1000.0 / ms32, "ms_per_step": ms32, "batch": g.n, "steps": k32,
+                "step_ws_bytes": int(ws32.numel()),
+                "peak_mem_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                "peak_mem_note": "device peak during the FP32 steps, the BF16 run's buffers still allocated",
+                "grad_bf16_vs_fp32": same_I}
+        if full is not None:
+            fp32["grad_bf16_estimator_vs_fp32_full"] = full
+        del ws32, idx_all, th32, g16, vfull
+
+    # ---- kernel rates from the stage profile (live, inside the timed steps) ----
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    peak_src = "measured" if peaks else "fallback"
+    per = {k: v / max(nprof, 1) for k, v in stages.items()}
+    kernels = {}
+    f_eval = mlp_flops(a, g.n, vjp=False)
+    # the VJP runs in chunks of at most VJP_CHUNK points; the profile marks bracket the
+    # first chunk's tile kernel, everything after it (further chunks, all GEMMs) is the
+    # "rest" stage
+    first = min(n_idx, VJP_CHUNK)
+    f_vjp = mlp_flops(a, first, vjp=True)
+    f_dw = dw_flops(a, n_idx) + mlp_flops(a, n_idx - first, vjp=True)
+    if per["eval_mlp_kernel"] > 0:
+        kernels["eval_mlp_kernel"] = {"ms": per["eval_mlp_kernel"],
+                                      "TFLOP/s": f_eval / per["eval_mlp_kernel"] / 1e9}
+    if per["vjp_mlp_kernel"] > 0:
+        kernels["vjp_mlp_kernel"] = {"ms": per["vjp_mlp_kernel"],
+                                     "TFLOP/s": f_vjp / per["vjp_mlp_kernel"] / 1e9,
+                                     "note": "algorithmic FLOPs; the ReLU networks' forward stages run "
+                                             "three MMAs per product (split operands)" if a.kind == "ffn" else ""}
+    if per["vjp_dw_gemm_reduce"] > 0:
+        key = "vjp_dw_gemm_reduce" if n_idx <= VJP_CHUNK else "vjp_rest (further chunks + dW GEMMs)"
+        kernels[key] = {"ms": per["vjp_dw_gemm_reduce"], "TFLOP/s": f_dw / per["vjp_dw_gemm_reduce"] / 1e9}
+    m_step = g.m // S                                # rays per step (a view subset when S > 1)
+    roof_proj = projector_roofline(g, m_step, per, hbm_peak, peak_src, w.name)
+    pair_ms = per["project_loss"] + per["backproject"]
+    dominant = max(("eval_mlp_kernel", "vjp_mlp_kernel"), key=lambda k: per[k])
+    flops = f_eval if dominant == "eval_mlp_kernel" else f_vjp
+    achieved = flops / per[dominant] / 1e9
+    roofline = {"kernel": "mlp_tile_kernel (" + ("grid evaluation" if dominant == "eval_mlp_kernel"
+                                                 else "VJP") + ")",
+                "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": achieved / bf16_peak, "peak_source": f"{peak_src} (bf16 burst)",
+                "traffic": recorded_traffic("mlp_tile_kernel_" + ("eval" if dominant == "eval_mlp_kernel"
+                                                                  else "vjp"), w.name)}
+    if args.prec != "bf16":
+        # FP32 SIMT path: FMA-bound at best (nominal peak from unit counts and the maximum clock)
+        roofline = {"kernel": "simt_fwd_kernel + simt_bwd_kernel (" +
+                              ("grid evaluation" if dominant == "eval_mlp_kernel" else "VJP") + ")",
+                    "bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_SIMT_TFLOPS,
+                    "peak_source": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                    "traffic": recorded_traffic("simt_" + ("eval" if dominant == "eval_mlp_kernel" else "vjp"),
+                                                w.name)}
+
+    cpu = None
+    if rank == 0 and world == 1 and cpu_budget > 0:
+        rate, k, fr = oracle_rate(w, budget_s=cpu_budget, frac_max=1 / 16)
+        cpu = {"value": rate, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{k} samples of about {fr:.3g} of a step each (forward on that fraction of "
+                         "the grid, P/P^T on that fraction of the views (at least one), VJP on that "
+                         "fraction of |I|), each part extrapolated linearly to the full step"}
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
+            "config": {"workload": w.name, "note": w.note, "batch": n_idx,
+                       "loss": args.loss, "precision": args.prec, "view_subsets": S,
+                       "projector_plan": {k: plans[0][k] for k in ("seg", "bp_splits", "zc")},
+                       "l2": "flushed between timed steps (untimed 258 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "gray_s_proj_backproj": m_step / pair_ms / 1e6 if pair_ms > 0 else None,
+            "stage_ms": per, "kernels": kernels, "roofline": roofline, "roofline_projector": roof_proj,
+            "e2e": {"value": e2e_value, "unit": "steps/s",
+                    "h2d_bytes_per_step": int(idx_host[0].numel() * 4), "d2h_bytes_per_step": 8},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": cpu,
+            "peak_mem_bytes": int(peak_mem), "step_ws_bytes": int(ws.numel()),
+            "fp32_path": fp32, "fractions": fractions,
+            "mse_vs_x_true": mse,
+            "loss_last": float(loss_host.item())}
+
+
 def main():
     args = parse()
     import torch
 
-    from paper_2604_09884_gb300 import inrct, synth
+    from paper_2604_09884_gb300 import synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -447,251 +795,25 @@ def main():
     dev = torch.device("cuda", local)
     if isinstance(w, list):
         run_batched(args, w, rank, world, local, dev)
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
-    g, a = w.geom, w.arch
-    seed = w.seed + 1000 * rank                      # every replica its own problem
-    # ---- synthetic problem, resident on the device ----
-    x_true = torch.tensor(synth.phantom(g.d, g.N, w.n_shapes, seed).reshape(-1), dtype=torch.float32,
-                          device=dev)
-    y_clean = inrct.project(g, x_true)
-    y = torch.tensor(synth.noisy(y_clean.cpu().numpy(), w.noise, seed + 1), device=dev)
-    B = synth.fourier_matrix(a.n_feat, a.d, a.sigma, seed + 2) if a.kind == "ffn" else None
-    prec = inrct.BF16 if args.prec == "bf16" else inrct.FP32
-    mlp = inrct.mlp_desc(a, prec, B, device=dev)
-    theta = torch.tensor(synth.init_theta(a, seed + 3), dtype=torch.float32, device=dev)
-    m = torch.zeros_like(theta)
-    s = torch.zeros_like(theta)
-    loss = torch.zeros(1, dtype=torch.float64, device=dev)
-    n_idx = w.batch
-    scale = g.n / n_idx
-    ws = torch.empty(inrct.step_ws_bytes(g, mlp, n_idx), dtype=torch.uint8, device=dev)
-    loss_kind = inrct.LOSS_FLS if args.loss == "fls" else inrct.LOSS_LS
-    # index sets: a fresh uniform subset per step (drawn on the host, staged in HBM)
-    n_sets = 16
-    idx_host = [torch.from_numpy(synth.index_set(g.n, n_idx, seed + 10 + k)).pin_memory()
-                for k in range(n_sets)]
-    idx_dev = [t.to(dev) for t in idx_host]
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    S = max(1, args.subsets)
-    sub_g = [inrct.view_subset(g, S, k) for k in range(S)] if S > 1 else [g]
-    sub_y = [inrct.view_subset_rows(g, y, S, k) for k in range(S)] if S > 1 else [y]
-    sub_ws = [ws] if S == 1 else [torch.empty(inrct.step_ws_bytes(q, mlp, n_idx), dtype=torch.uint8, device=dev)
-                                  for q in sub_g]
-    # projector launch shapes: the library's autotuner, once per geometry, before any timing
-    # (or a plan pinned on the command line, e.g. to reproduce a measurement's launch shapes)
-    if args.plan:
-        seg, bp, zc = (int(x) for x in args.plan.split(","))
-        for q in sub_g:
-            inrct.tune_set(q, seg, bp, zc)
-        plans = [inrct.tune_plan(q) for q in sub_g]
+    elif args.projector_only:
+        run_projector_only(args, w, rank, world, local, dev)
     else:
-        plans = [inrct.tune(q, device=dev) for q in sub_g]
-
-    def step(t, idx):
-        k = t % S
-        inrct.grad_step(sub_g[k], mlp, theta, sub_y[k], idx, scale, inrct.adam(lr=w.lr, t=t), m, s, loss,
-                        None, sub_ws[k], loss_kind)
-
-    t = 0
-    for _ in range(args.warmup):
-        t += 1
-        step(t, idx_dev[t % n_sets])
-    torch.cuda.synchronize()
-
-    # ---- timed region (device): inputs resident, L2 flushed between steps (untimed) ----
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    prof_steps = min(args.steps, 256)
-    inrct.profile_begin(prof_steps)
-    l0 = inrct.launch_count()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            t += 1
-            starts[k].record(stream)
-            step(t, idx_dev[t % n_sets])
-            ends[k].record(stream)
-        torch.cuda.synchronize()
-    launches = inrct.launch_count() - l0
-    stages, nprof = inrct.profile_end()
-    if world > 1:
-        torch.distributed.barrier()
-    step_ms = [st.elapsed_time(en) for st, en in zip(starts, ends)]
-    value, total_s = job_rate(args.steps, sum(step_ms) / 1000.0, world, dev)
-    ms_per_step = 1000.0 * total_s / args.steps
-
-    # ---- end to end through the public API, host buffers, copies inside the timed region ----
-    loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.e2e_steps, args.steps))
-    idx_stage = torch.empty_like(idx_dev[0])
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for k in range(e2e_steps):
-        t += 1
-        idx_stage.copy_(idx_host[t % n_sets], non_blocking=True)
-        step(t, idx_stage)
-        loss_host.copy_(loss, non_blocking=True)
-    torch.cuda.synchronize()
-    e2e_value, e2e_s = job_rate(e2e_steps, time.perf_counter() - t0, world, dev)
-    peak_mem = torch.cuda.max_memory_allocated(dev)
-
-    # ---- reconstruction error of the trained INR, and other subsampling fractions ----
-    with torch.no_grad():
-        mse = float(((inrct.inr_eval_grid(mlp, theta, g.N) - x_true) ** 2).mean())
-    fractions = {f"{n_idx / g.n:.4g}": {"steps_per_s": value / world, "batch": n_idx}}
-    if not args.no_fractions:
-        for f in (1.0, 0.05):
-            nI = max(1, int(round(f * g.n)))
-            wsf = torch.empty(inrct.step_ws_bytes(g, mlp, nI), dtype=torch.uint8, device=dev)
-            idxf = torch.from_numpy(synth.index_set(g.n, nI, seed + 99)).to(dev)
-            thf, mf, sf = theta.clone(), torch.zeros_like(theta), torch.zeros_like(theta)
-            kf = 20
-            for tf in range(1, 3 + kf):
-                if tf == 3:
-                    torch.cuda.synchronize()
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                inrct.grad_step(g, mlp, thf, y, idxf, g.n / nI, inrct.adam(lr=w.lr, t=tf), mf, sf, None, None,
-                                wsf, loss_kind)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            fractions[f"{f:.4g}"] = {"steps_per_s": 1000.0 * kf / e0.elapsed_time(e1), "batch": nI,
-                                     "timing": f"{kf} steps back to back, L2 not flushed"}
-            del wsf
-
-    # ---- the plain FP32 path (|I| = n) and the BF16 / FP32 gradient agreement ----
-    fp32 = None
-    if args.prec == "bf16" and not args.no_fp32:
-        torch.cuda.reset_peak_memory_stats(dev)
-        mlp32 = inrct.mlp_desc(a, inrct.FP32, B, device=dev)
-        idx_all = torch.arange(g.n, dtype=torch.int32, device=dev)
-        ws32 = torch.empty(inrct.step_ws_bytes(g, mlp32, g.n), dtype=torch.uint8, device=dev)
-        th32, m32, s32 = theta.clone(), torch.zeros_like(theta), torch.zeros_like(theta)
-        loss32 = torch.zeros(1, dtype=torch.float64, device=dev)
-        for t32 in range(1, 3):
-            inrct.grad_step(g, mlp32, th32, y, idx_all, 1.0, inrct.adam(lr=w.lr, t=t32), m32, s32, loss32,
-                            None, ws32, loss_kind)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k32 = max(1, args.fp32_steps)
-        e0.record(stream)
-        for t32 in range(3, 3 + k32):
-            inrct.grad_step(g, mlp32, th32, y, idx_all, 1.0, inrct.adam(lr=w.lr, t=t32), m32, s32, loss32,
-                            None, ws32, loss_kind)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1) / k32
-        ws32_bytes = ws32.numel()
-        peak32 = torch.cuda.max_memory_allocated(dev)
-        del ws32
-        # one estimator at the current theta: v = P^T r of its own image, the same index set
-        img = inrct.inr_eval_grid(mlp32, theta, g.N)
-        _, r, _ = inrct.project(g, img, y)
-        vfull = inrct.backproject(g, r)
-        g16 = inrct.inr_weighted_vjp(mlp, theta, g.N, idx_dev[0], vfull, scale)
-        g32 = inrct.inr_weighted_vjp(mlp32, theta, g.N, idx_dev[0], vfull, scale)
-        rel = float(torch.linalg.norm(g16 - g32) / torch.linalg.norm(g32))
-        cos = float(torch.dot(g16, g32) / (torch.linalg.norm(g16) * torch.linalg.norm(g32)))
-        fp32 = {"steps_per_s": 1000.0 / ms32, "ms_per_step": ms32, "batch": g.n, "steps": k32,
-                "step_ws_bytes": int(ws32_bytes),
-                "peak_mem_bytes": int(peak32),
-                "peak_mem_note": "device peak during the FP32 steps, the BF16 run's buffers still allocated",
-                "grad_bf16_vs_fp32": {"rel_l2": rel, "cosine": cos, "batch": n_idx,
-                                      "v": "P^T (P f_theta - y) at the current theta"}}
-
-    # ---- kernel rates from the stage profile (live, inside the timed steps) ----
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    bf16_peak = peaks.get("bf16_tflops", 1900.0)
-    peak_src = "measured" if peaks else "fallback"
-    per = {k: v / max(nprof, 1) for k, v in stages.items()}
-    kernels = {}
-    f_eval = mlp_flops(a, g.n, vjp=False)
-    # the VJP runs in chunks of at most VJP_CHUNK points; the profile marks bracket the
-    # first chunk's tile kernel, everything after it (further chunks, all GEMMs) is the
-    # "rest" stage
-    first = min(n_idx, VJP_CHUNK)
-    f_vjp = mlp_flops(a, first, vjp=True)
-    f_dw = dw_flops(a, n_idx) + mlp_flops(a, n_idx - first, vjp=True)
-    if per["eval_mlp_kernel"] > 0:
-        kernels["eval_mlp_kernel"] = {"ms": per["eval_mlp_kernel"],
-                                      "TFLOP/s": f_eval / per["eval_mlp_kernel"] / 1e9}
-    if per["vjp_mlp_kernel"] > 0:
-        kernels["vjp_mlp_kernel"] = {"ms": per["vjp_mlp_kernel"],
-                                     "TFLOP/s": f_vjp / per["vjp_mlp_kernel"] / 1e9}
-    if per["vjp_dw_gemm_reduce"] > 0:
-        key = "vjp_dw_gemm_reduce" if n_idx <= VJP_CHUNK else "vjp_rest (further chunks + dW GEMMs)"
-        kernels[key] = {"ms": per["vjp_dw_gemm_reduce"], "TFLOP/s": f_dw / per["vjp_dw_gemm_reduce"] / 1e9}
-    # projector: compulsory bytes = image once + sinogram out (+ y in, residual out)
-    m_step = g.m // S                                # rays per step (a view subset when S > 1)
-    proj_bytes = 4.0 * (g.n + 3 * m_step)
-    back_bytes = 4.0 * (g.n + m_step)
-    kernels["project_loss"] = {"ms": per["project_loss"],
-                               "GB/s": proj_bytes / per["project_loss"] / 1e6,
-                               "GRays/s": m_step / per["project_loss"] / 1e6}
-    kernels["backproject"] = {"ms": per["backproject"],
-                              "GB/s": back_bytes / per["backproject"] / 1e6,
-                              "GRays/s": m_step / per["backproject"] / 1e6}
-    pair_ms = per["project_loss"] + per["backproject"]
-    dominant = max(("eval_mlp_kernel", "vjp_mlp_kernel"), key=lambda k: per[k])
-    flops = f_eval if dominant == "eval_mlp_kernel" else f_vjp
-    achieved = flops / per[dominant] / 1e9
-    roofline = {"kernel": "mlp_tile_kernel (" + ("grid evaluation" if dominant == "eval_mlp_kernel"
-                                                 else "VJP") + ")",
-                "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": achieved / bf16_peak, "peak_source": f"{peak_src} (bf16 burst)",
-                "traffic": recorded_traffic("mlp_tile_kernel_" + ("eval" if dominant == "eval_mlp_kernel"
-                                                                  else "vjp"), w.name)}
-    if args.prec != "bf16":
-        # FP32 SIMT path: FMA-bound at best (nominal peak from unit counts and the maximum clock)
-        roofline = {"kernel": "simt_fwd_kernel + simt_bwd_kernel (" +
-                              ("grid evaluation" if dominant == "eval_mlp_kernel" else "VJP") + ")",
-                    "bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_SIMT_TFLOPS,
-                    "peak_source": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2 x 2.07 GHz)",
-                    "traffic": recorded_traffic("simt_" + ("eval" if dominant == "eval_mlp_kernel" else "vjp"),
-                                                w.name)}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, k, fr = oracle_rate(w, budget_s=15.0, frac_max=1 / 16)
-        cpu = {"value": rate, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{k} samples of about {fr:.3g} of a step each (forward on that fraction of "
-                         "the grid, P/P^T on that fraction of the views (at least one), VJP on that "
-                         "fraction of |I|), each part extrapolated linearly to the full step"}
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
-                "config": {"workload": w.name, "note": w.note, "batch": n_idx,
-                           "loss": args.loss, "precision": args.prec, "view_subsets": S,
-                           "projector_plan": {k: plans[0][k] for k in ("seg", "bp_splits", "zc")},
-                           "l2": "flushed between timed steps (untimed 258 MB write)",
-                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "gray_s_proj_backproj": m_step / pair_ms / 1e6 if pair_ms > 0 else None,
-                "stage_ms": per, "kernels": kernels, "roofline": roofline,
-                "e2e": {"value": e2e_value, "unit": "steps/s",
-                        "h2d_bytes_per_step": int(idx_host[0].numel() * 4), "d2h_bytes_per_step": 8},
-                "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": cpu,
-                "peak_mem_bytes": int(peak_mem), "step_ws_bytes": int(ws.numel()),
-                "fp32_path": fp32, "fractions": fractions,
-                "mse_vs_x_true": mse,
-                "loss_last": float(loss_host.item())}
-        print(json.dumps(line), flush=True)
+        cpu_s = 0.0 if args.no_cpu_baseline else 15.0
+        line = run_single(args, w, rank, world, local, dev, args.steps, args.warmup, args.e2e_steps, cpu_s,
+                          headline=True)
+        if w.name == HEADLINE and args.frac is None and not args.no_secondary and args.subsets == 1:
+            # the 512^2 fan workload's figures, carried in the same line
+            torch.cuda.empty_cache()
+            sec = run_single(args, wl[SECONDARY], rank, world, local, dev, max(1, args.secondary_steps),
+                             max(args.warmup, 20), 200, 0.0 if args.no_cpu_baseline else 10.0, headline=False)
+            if rank == 0:
+                line[SECONDARY] = {k: sec[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "config",
+                                                       "roofline", "roofline_projector", "kernels", "stage_ms",
+                                                       "e2e", "gpu_launches", "clocks", "cpu_baseline",
+                                                       "peak_mem_bytes", "step_ws_bytes", "fp32_path",
+                                                       "fractions", "mse_vs_x_true")}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -640,44 +640,51 @@ __global__ void backproject3d_kernel(GeomDev g, const int4* __restrict__ t0, con
       const float* scol = sino_s + (size_t)k * B * A + a;
       if (fabsf(hg) > 1e-3f) {
         // One sweep over the rows that can reach this z-chunk, in increasing z: a row's
-        // crossing u splits into floor(u) = i0 and f, and it gives 1 - f to voxel i0 and f
-        // to i0 + 1 (the forward's taps), so while the voxel loop below is unrolled every
-        // row lands in registers known at compile time.  With |pitch| > 1e-3 voxel per row
-        // the crossings step by more than 2^22 in 32.32 fixed point, far above the
-        // truncation jitter of dj (Pk >> 16) (|dj| < 2^12): they are strictly monotone.
-        // The rows are those of the per-voxel windows below, united over the chunk.
+        // crossing u (in voxels, relative to the chunk's first voxel z0) gives 1 - f to voxel
+        // floor(u) and f to floor(u) + 1 (the forward's taps), so while the voxel loop below is
+        // unrolled every row lands in registers known at compile time.  The first row's
+        // crossing is formed exactly in the forward's 32.32 fixed point; the following ones
+        // step by the row pitch 2 |hg| in FP32 (one FMA from the first, no accumulation),
+        // which keeps them within a few 1e-6 voxel of the forward's (|u| < ZC + 2): the weights
+        // match the forward's to FP32 rounding.  With |pitch| > 1e-3 voxel per row the
+        // crossings are strictly increasing.  The rows are those of the per-voxel windows
+        // below, united over the chunk.
         const float bzA = 0.5f * fmaf((float)z0 - Cz, inv_hg, Bm1);
         const float bzB = 0.5f * fmaf((float)(z0 + ZC - 1) - Cz, inv_hg, Bm1);
         const int bl = max(0, (int)ceilf(fminf(bzA, bzB) - hb));
         const int bh = min(B - 1, (int)floorf(fmaxf(bzA, bzB) + hb));
         if (bl > bh) continue;
         const int dir = hg > 0.f ? 1 : -1;
-        int b = dir > 0 ? bl : bh;
-        const int bend = dir > 0 ? bh + 1 : bl - 1;
-        const int mr = 2 * b - (B - 1);
-        int64_t Zb = CzF + (int64_t)mr * Hh, Pk = (int64_t)mr * Kk;
-        const int64_t dZ = 2 * dir * Hh, dP = 2 * dir * Kk;
-        int i0;
-        float f;
-        split_fx(Zb + dj * (Pk >> 16), i0, f);
-        auto next = [&]() {
-          b += dir;
-          Zb += dZ;
-          Pk += dP;
-          if (b != bend) split_fx(Zb + dj * (Pk >> 16), i0, f);
-        };
-        while (b != bend && i0 < z0 - 1) next();
-        while (b != bend && i0 == z0 - 1) {
-          acc[0] = fmaf(wq * f, __ldg(scol + (size_t)b * A), acc[0]);
-          next();
+        const int bfirst = dir > 0 ? bl : bh;
+        const float nrow = (float)(bh - bl + 1);
+        const int mr = 2 * bfirst - (B - 1);
+        const int64_t Zf = CzF + (int64_t)mr * Hh + dj * (((int64_t)mr * Kk) >> 16) - ((int64_t)z0 << 32);
+        const float u0 = (float)Zf * 2.3283064365386963e-10f;  // * 2^-32
+        const float du = 2.f * fabsf(hg);
+        const float* sp = scol + (ptrdiff_t)bfirst * A;
+        const ptrdiff_t step = (ptrdiff_t)dir * A;
+        float rr = 0.f, u = u0;
+        while (rr < nrow && u < -1.f) {
+          rr += 1.f;
+          sp += step;
+          u = fmaf(rr, du, u0);
+        }
+        while (rr < nrow && u < 0.f) {  // floor(u) = -1: f = u + 1 to voxel 0
+          acc[0] = fmaf(wq * (u + 1.f), __ldg(sp), acc[0]);
+          rr += 1.f;
+          sp += step;
+          u = fmaf(rr, du, u0);
         }
 #pragma unroll
         for (int zq = 0; zq < ZC; ++zq) {
-          while (b != bend && i0 == z0 + zq) {
-            const float sv_b = __ldg(scol + (size_t)b * A);
-            acc[zq] = fmaf(wq * __fsub_rn(1.f, f), sv_b, acc[zq]);
-            if (zq + 1 < ZC) acc[zq + 1] = fmaf(wq * f, sv_b, acc[zq + 1]);
-            next();
+          while (rr < nrow && u < (float)(zq + 1)) {  // floor(u) = zq
+            const float ws = wq * __ldg(sp);
+            const float f = u - (float)zq;
+            acc[zq] = fmaf(-f, ws, acc[zq] + ws);
+            if (zq + 1 < ZC) acc[zq + 1] = fmaf(f, ws, acc[zq + 1]);
+            rr += 1.f;
+            sp += step;
+            u = fmaf(rr, du, u0);
           }
         }
         continue;
