@@ -454,9 +454,10 @@ int inrct_profile_end(double* stage_ms, int n_stages, int* steps_out);
 /*
  * inrct_sincospi -- s[i] = sin(pi x[i]), c[i] = cos(pi x[i]) for x[i] in [-1, 1], computed
  * exactly as the Fourier features gamma(x) = [cos 2 pi B x; sin 2 pi B x] of the FFN
- * networks (Sec. 4) are inside the tensor-core kernels (the phase B x is first reduced
- * to t in [-1/2, 1/2] exactly, then sincospif(2t), about an FP32 ulp); exposed for
- * diagnostics.  x, s, c:
+ * networks (Sec. 4) are inside the tensor-core VJP (the phase B x is first reduced
+ * to t in [-1/2, 1/2], then sincospif(2t), about an FP32 ulp); exposed for diagnostics.
+ * (The grid evaluation, whose features only enter BF16 operands, takes the hardware
+ * sine and cosine of 2 pi t instead.)  x, s, c:
  * n FP32 device values.  INVALID_ARG for NULL buffers or n <= 0.
  */
 int inrct_sincospi(const float* x, float* s, float* c, int64_t n, cudaStream_t stream);
