@@ -52,8 +52,11 @@ def parse():
     p.add_argument("--no-secondary", action="store_true",
                    help=f"default workload only: skip the {SECONDARY} figures carried in the line")
     p.add_argument("--secondary-steps", type=int, default=1000, help=f"timed steps of {SECONDARY}")
-    p.add_argument("--projector-only", action="store_true",
-                   help="time the projector P and its adjoint alone on the workload's geometry")
+    p.add_argument("--only", choices=["projector", "eval", "vjp"], default=None,
+                   help="time one stage alone on the workload (P and P^T; the grid evaluation; the VJP "
+                        "at |I| points), e.g. for a profiler")
+    p.add_argument("--grid-n", type=int, default=None,
+                   help="with --only eval/vjp: a grid of this side instead of the workload's (same network)")
     p.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     p.add_argument("--frac", type=float, default=None, help="|I|/n (default: the workload's)")
     p.add_argument("--loss", default="ls", choices=["ls", "fls"])
@@ -457,24 +460,50 @@ def build_problem(w, rank, dev, prec_name):
     return {"seed": seed, "x_true": x_true, "y": y, "B": B, "mlp": mlp, "theta": theta}
 
 
-def run_projector_only(args, w, rank, world, local, dev):
-    """P and P^T alone on the workload's geometry (tuned plans), CUDA-event timed per call with
-    L2 flushed in between; used by the projector profiles."""
+def run_stage_only(args, w, rank, world, local, dev):
+    """One stage alone, CUDA-event timed per call with L2 flushed in between (used by the
+    profiles): P and P^T on the workload's geometry (tuned plans, or --plan), or the grid
+    evaluation / the VJP at |I| = the workload's batch (scaled to --grid-n) with the workload's
+    network in its precision."""
     import torch
 
     from paper_2604_09884_gb300 import inrct, synth
     g = w.geom
-    x = torch.tensor(synth.phantom(g.d, g.N, w.n_shapes, w.seed).reshape(-1), dtype=torch.float32, device=dev)
-    y = inrct.project(g, x)
-    if args.plan:
-        inrct.tune_set(g, *(int(q) for q in args.plan.split(",")))
-        plan = inrct.tune_plan(g)
-    else:
-        plan = inrct.tune(g, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    info = {}
+    if args.only == "projector":
+        x = torch.tensor(synth.phantom(g.d, g.N, w.n_shapes, w.seed).reshape(-1), dtype=torch.float32, device=dev)
+        if args.plan:
+            inrct.tune_set(g, *(int(q) for q in args.plan.split(",")))
+            info["plan"] = inrct.tune_plan(g)
+        else:
+            info["plan"] = inrct.tune(g, device=dev)
+        y = inrct.project(g, x)
+        fns = (("project", lambda: inrct.project(g, x, y)), ("backproject", lambda: inrct.backproject(g, y)))
+        units = g.m
+        info.update(rays=g.m, voxels=g.n)
+    else:
+        a = w.arch
+        N = args.grid_n or g.N
+        n = N ** g.d
+        B = synth.fourier_matrix(a.n_feat, a.d, a.sigma, w.seed + 2) if a.kind == "ffn" else None
+        mlp = inrct.mlp_desc(a, inrct.BF16 if args.prec == "bf16" else inrct.FP32, B, device=dev)
+        theta = torch.tensor(synth.init_theta(a, w.seed + 3), dtype=torch.float32, device=dev)
+        if args.only == "eval":
+            fns = (("eval", lambda: inrct.inr_eval_grid(mlp, theta, N)),)
+            units = n
+            info.update(points=n, flops=mlp_flops(a, n, vjp=False))
+        else:
+            nI = max(1, min(n, int(round(w.batch * n / g.n))))
+            idx = torch.from_numpy(synth.index_set(n, nI, w.seed + 10)).to(dev)
+            v = torch.tensor(synth.uniform(n, w.seed + 11), dtype=torch.float32, device=dev)
+            fns = (("vjp", lambda: inrct.inr_weighted_vjp(mlp, theta, N, idx, v, n / nI)),)
+            units = nI
+            info.update(points=nI, flops=mlp_flops(a, nI, vjp=True) + dw_flops(a, nI))
+        info.update(grid_n=N, precision=args.prec)
     res = {}
-    for name, fn in (("project", lambda: inrct.project(g, x, y)), ("backproject", lambda: inrct.backproject(g, y))):
+    for name, fn in fns:
         for _ in range(max(1, args.warmup)):
             fn()
         ts = []
@@ -486,11 +515,15 @@ def run_projector_only(args, w, rank, world, local, dev):
             e1.record(stream)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
-        res[name] = {"ms_median": statistics.median(ts), "ms_min": min(ts), "GRays/s": g.m / statistics.median(ts) / 1e6}
+        med = statistics.median(ts)
+        res[name] = {"ms_median": med, "ms_min": min(ts), "units_per_s": units / med * 1e3}
+        if "flops" in info:
+            res[name]["TFLOP/s"] = info["flops"] / med / 1e9
+    inrct.device_status()
     if rank == 0:
-        print(json.dumps({"mode": "projector-only", "workload": w.name, "rays": g.m, "voxels": g.n,
-                          "plan": plan, "calls": args.steps, "timing": res,
-                          "note": "each call includes its ray-table set-up; L2 flushed between calls"}), flush=True)
+        print(json.dumps({"mode": f"only {args.only}", "workload": w.name, **info, "calls": args.steps,
+                          "timing": res, "note": "each call is the library entry point (workspace set-up "
+                                                 "included); L2 flushed between calls"}), flush=True)
 
 
 def run_single(args, w, rank, world, local, dev, steps, warmup, e2e_steps, cpu_budget, headline):
@@ -795,8 +828,8 @@ def main():
     dev = torch.device("cuda", local)
     if isinstance(w, list):
         run_batched(args, w, rank, world, local, dev)
-    elif args.projector_only:
-        run_projector_only(args, w, rank, world, local, dev)
+    elif args.only:
+        run_stage_only(args, w, rank, world, local, dev)
     else:
         cpu_s = 0.0 if args.no_cpu_baseline else 15.0
         line = run_single(args, w, rank, world, local, dev, args.steps, args.warmup, args.e2e_steps, cpu_s,
