@@ -70,17 +70,20 @@ def test_loss_epilogue_matches_oracle():
     assert abs(L.item() - L0) <= 2 * TOL * L0
 
 
-def test_cone_256_sampled_parity():
-    # the 256^3 / 40 x 384^2 cone workload at full size: sampled rays and voxels
-    g = synth.workloads()["cone3d_256_ffn256"].geom
-    x = synth.phantom(3, g.N, 30, seed=3).astype(np.float32)
+@pytest.mark.parametrize("name,shapes,n_vox", [("cone3d_256_ffn256", 30, 24), ("cone3d_501_ffn512", 12, 8)],
+                         ids=["cone256", "cone501"])
+def test_cone_full_size_sampled_parity(name, shapes, n_vox):
+    # the cone workloads at full size (their volumes exceed L2, so P runs in z-slab order):
+    # sampled rays and voxels against the oracle, and the adjoint identity
+    g = synth.workloads()[name].geom
+    x = synth.phantom(3, g.N, shapes, seed=3).astype(np.float32)
     z = inrct.project(g, cuda(x.reshape(-1))).cpu().numpy()
     rng = np.random.default_rng(11)
     rays = rng.choice(g.m, 3000, replace=False)
     assert rel(z[rays], O.project_at(og(g), x, rays)) <= TOL
     r = rng.uniform(-1, 1, g.m).astype(np.float32)
     v = inrct.backproject(g, cuda(r)).cpu().numpy()
-    vox = rng.choice(g.n, 24, replace=False)
+    vox = rng.choice(g.n, n_vox, replace=False)
     assert rel(v[vox], O.backproject_at(og(g), r, vox)) <= TOL
     lhs = z.astype(np.float64) @ r.astype(np.float64)
     rhs = x.reshape(-1).astype(np.float64) @ v.astype(np.float64)
