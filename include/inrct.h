@@ -455,7 +455,9 @@ int inrct_profile_end(double* stage_ms, int n_stages, int* steps_out);
  * inrct_sincospi -- s[i] = sin(pi x[i]), c[i] = cos(pi x[i]) for x[i] in [-1, 1], computed
  * exactly as the Fourier features gamma(x) = [cos 2 pi B x; sin 2 pi B x] of the FFN
  * networks (Sec. 4) are inside the tensor-core VJP (the phase B x is first reduced
- * to t in [-1/2, 1/2], then sincospif(2t), about an FP32 ulp); exposed for diagnostics.
+ * to t in [-1/2, 1/2], then to the nearest quarter turn, and the Taylor series of sin and
+ * cos to degrees 9 and 10 are evaluated there: about 1e-7 absolute); exposed for
+ * diagnostics.
  * (The grid evaluation, whose features only enter BF16 operands, takes the hardware
  * sine and cosine of 2 pi t instead.)  x, s, c:
  * n FP32 device values.  INVALID_ARG for NULL buffers or n <= 0.

@@ -67,12 +67,15 @@ __device__ __forceinline__ float two_sum(float a, float b, float* e) {
 // point with coordinate numerators m (x_a = m_a / N), accurate to about an FP32 ulp of t.
 // With x_a = m_a / N the phase is (sum_a B_a m_a) / N: each product B_a m_a (m_a is an exact
 // FP32 integer) is p + e exactly by an FMA, the products are added with error-free sums into a
-// head s and a tail, the quotient by N is q = s / N with the exact remainder s - q N (an FMA),
-// and t = (q - rint q) + (remainder + tail) / N.  Forming B . x from rounded coordinates in FP32
+// head s and a tail, the quotient by N is q = s / N (a product with the reciprocal inv_N) with
+// the remainder s - q N formed exactly by an FMA (q is within a few ulp of s / N, so the
+// remainder is a small multiple of ulp(q) and representable), and
+// t = (q - rint q) + (remainder + tail) / N.  Forming B . x from rounded coordinates in FP32
 // instead leaves an absolute phase error of about |B . x| 2^-24 (2e-6 at |B . x| = 30), which
 // moves features by about 2 pi times that: enough to flip the ReLU masks of units within
 // 1e-5 of their RMS of zero.
-__device__ __forceinline__ float ffn_phase_exact(float b0, float b1, float b2, const int* m, int d, int N) {
+__device__ __forceinline__ float ffn_phase_exact(float b0, float b1, float b2, const int* m, int d, int N,
+                                                 float inv_N) {
   const float m0 = (float)m[0], m1 = (float)m[1], m2 = (float)m[2];
   const float p0 = __fmul_rn(b0, m0), e0 = __fmaf_rn(b0, m0, -p0);
   const float p1 = __fmul_rn(b1, m1), e1 = __fmaf_rn(b1, m1, -p1);
@@ -86,10 +89,38 @@ __device__ __forceinline__ float ffn_phase_exact(float b0, float b1, float b2, c
     tail = __fadd_rn(tail, __fadd_rn(e2, t2));
   }
   const float fN = (float)N;
-  const float q = __fdiv_rn(s, fN);
-  const float r = __fmaf_rn(-q, fN, s);  // s - q N, exact for a correctly rounded quotient
+  const float q = __fmul_rn(s, inv_N);
+  const float r = __fmaf_rn(-q, fN, s);  // s - q N, exact
   const float t = __fsub_rn(q, rintf(q));
-  return __fadd_rn(t, __fdiv_rn(__fadd_rn(r, tail), fN));
+  return __fmaf_rn(__fadd_rn(r, tail), inv_N, t);
+}
+
+// sin(2 pi t) and cos(2 pi t) for |t| <= 1/2 + a few ulp, to about 1e-7 absolute.  The angle is
+// reduced to the nearest quarter turn k / 4 (exactly: r = t - k/4 by Sterbenz's lemma), so that
+// x = 2 pi r lies in [-pi/4, pi/4]; 2 pi is taken as a two-term FP32 sum.  There the Taylor
+// series of sin to x^9 and of cos to x^10 are within 2e-9 of the functions (the first omitted
+// terms, x^11/11! and x^12/12!, at x = pi/4), evaluated by Horner's rule in FP32; the quarter
+// turn then rotates (sin, cos) by k pi / 2.  About twenty FP32 instructions, no branch.
+__device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
+  const float k = rintf(4.f * t);
+  const float r = __fmaf_rn(-0.25f, k, t);
+  const float kTwoPiHi = 6.28318548202514648f;        // fl(2 pi)
+  const float kTwoPiLo = -1.74845553146951715e-07f;   // 2 pi - fl(2 pi)
+  const float x = __fmaf_rn(r, kTwoPiHi, __fmul_rn(r, kTwoPiLo));
+  const float x2 = __fmul_rn(x, x);
+  float ps = __fmaf_rn(x2, 1.f / 362880.f, -1.f / 5040.f);
+  ps = __fmaf_rn(x2, ps, 1.f / 120.f);
+  ps = __fmaf_rn(x2, ps, -1.f / 6.f);
+  const float sn = __fmaf_rn(__fmul_rn(x2, ps), x, x);
+  float pc = __fmaf_rn(x2, -1.f / 3628800.f, 1.f / 40320.f);
+  pc = __fmaf_rn(x2, pc, -1.f / 720.f);
+  pc = __fmaf_rn(x2, pc, 1.f / 24.f);
+  pc = __fmaf_rn(x2, pc, -0.5f);
+  const float cs = __fmaf_rn(x2, pc, 1.f);
+  const int q = ((int)k) & 3;
+  const float a = (q & 1) ? cs : sn, b = (q & 1) ? sn : cs;  // (sin, cos) of r rotated by q quarter turns
+  *s = (q == 1 || q == 0) ? a : -a;
+  *c = (q == 0 || q == 3) ? b : -b;
 }
 
 // Coordinates of grid point i (x fastest).  Indices below 2^32 take 32-bit divisions (the

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256)
       const float* Bf = net.B + (int64_t)f * net.d;
       const int m[3] = {2 * ks[p][0] + 1 - net.N, 2 * ks[p][1] + 1 - net.N,
                         net.d == 3 ? 2 * ks[p][2] + 1 - net.N : 0};
-      const float t = ffn_phase_exact(Bf[0], Bf[1], net.d == 3 ? Bf[2] : 0.f, m, net.d, net.N);
+      const float t = ffn_phase_exact(Bf[0], Bf[1], net.d == 3 ? Bf[2] : 0.f, m, net.d, net.N, 1.f / (float)net.N);
       float s, c;
       sincospif(2.f * t, &s, &c);
       bufA[p * Kmax + f] = c;

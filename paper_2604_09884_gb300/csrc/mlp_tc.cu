@@ -541,7 +541,9 @@ __device__ __forceinline__ void load_row_bf16(const __nv_bfloat16* src, float* v
 // feed ReLU mask decisions downstream, so they are computed accurately rather than with the
 // hardware approximations (those, 2^-21.4 absolute, moved the BF16 gradient of a 3-D FFN by
 // more than 1 % through flipped masks; measured).
-__device__ __forceinline__ void feat_sincos(float t, float* s, float* c) { sincospif(2.f * t, s, c); }
+// Features of the VJP, whose ReLU masks downstream must be decided at FP32 accuracy: sin and
+// cos of 2 pi t to about 1e-7 (sincos_turns).
+__device__ __forceinline__ void feat_sincos(float t, float* s, float* c) { sincos_turns(t, s, c); }
 // Grid evaluation: the features only enter BF16 operands (rounded to about 4e-3 relative) and
 // decide no mask that a gradient uses, so after the same exact reduction to [-1/2, 1/2] the
 // hardware sine and cosine of 2 pi t (about 2^-21 absolute on [-pi, pi]) are accurate enough
@@ -826,6 +828,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
       return ((((int64_t)layer * n_tiles + tile) * (W / 64) + c) * NWG + g) * (kTile * CW) + (int64_t)r * CW;
     };
     const float bout = P.theta[P.offbout];
+    const float inv_N = 1.f / (float)P.N;
     const int n0 = P.in_panels < 4 ? P.in_panels : 4;  // first-stage panels published together
     float v[CW];
     double bsum = 0.0;  // VJP: this row's share of sum scale * v_i (warps of column group 0)
@@ -876,7 +879,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               const float4 bf = P.first_staged ? first_s[f0 + i] : __ldg(P.first + f0 + i);
               if (MODE == 1) {
                 // the VJP decides ReLU masks downstream: the phase to an FP32 ulp of t
-                feat_sincos(ffn_phase_exact(bf.x, bf.y, bf.z, mt, P.d, P.N), &v[8 + i], &v[i]);
+                feat_sincos(ffn_phase_exact(bf.x, bf.y, bf.z, mt, P.d, P.N, inv_N), &v[8 + i], &v[i]);
               } else {
                 float ph = fmaf(bf.y, xt[1], bf.x * xt[0]);
                 if (P.d == 3) ph = fmaf(bf.z, xt[2], ph);
