@@ -535,6 +535,7 @@ def run_single(args, w, rank, world, local, dev, steps, warmup, e2e_steps, cpu_b
     from paper_2604_09884_gb300 import inrct, synth
     g, a = w.geom, w.arch
     big = g.n > (1 << 24)
+    torch.cuda.reset_peak_memory_stats(dev)          # the peak of this workload alone
     pb = build_problem(w, rank, dev, args.prec)
     x_true, y, B, mlp, theta = pb["x_true"], pb["y"], pb["B"], pb["mlp"], pb["theta"]
     seed = pb["seed"]
