@@ -492,8 +492,9 @@ struct TileProg {
   __nv_bfloat16* E;     // [npts_pad][2F] layer-1 input (FFN)
   __nv_bfloat16* Act;   // [L][npts_pad][W] activations a_l; a_0 .. a_{L-2} arrive by TMA store
   __nv_bfloat16* Dlt;   // [L][npts_pad][W] deltas, all by TMA store from the input panels
-  // sigma'(u_l) for l = 0 .. L-2 (SIREN: cos u_l with omega0 folded in the weights; FFN: 1[u_l > 0]),
-  // read back only by this kernel: blocked so that a warp's 32 rows x CW columns are one
+  // sigma'(u_l) for l = 0 .. L-2 of the SIREN (cos u_l with omega0 folded in the weights; the split
+  // VJP of ReLU networks keeps its masks as bits instead), read back only by this kernel:
+  // blocked so that a warp's 32 rows x CW columns are one
   // contiguous 1 KB run, index (((l * n_tiles + tile) * W/64 + c) * NWG + g) * 128 + row
   __nv_bfloat16* Sg;
   int st_in_arr[kMaxStages];    // the stage's input panels are row block tile of: 0 Act, 1 Dlt, -1 none
@@ -831,6 +832,9 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     const float inv_N = 1.f / (float)P.N;
     const int n0 = P.in_panels < 4 ? P.in_panels : 4;  // first-stage panels published together
     float v[CW];
+    // split VJP (ReLU): the masks 1[u_l > 0] of this thread's 16 columns of every 64-column
+    // chunk, per hidden layer, as bits (local memory), in place of a scratch round trip
+    uint16_t mk[SPLIT ? 4 * kMaxLayers : 1];
     double bsum = 0.0;  // VJP: this row's share of sum scale * v_i (warps of column group 0)
     double fsum = 0.0;  // VJP: this row's share of sum scale * v_i * f(x_i) (the virtual loss)
     for (int64_t pr = 0; pr < n_groups; ++pr) {
@@ -956,7 +960,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           // backward: sigma'(u_{l-1}) of this tile; chunk c + 1 is fetched while chunk c is
           // processed, chunk 0 before the wait for the accumulator (a dummy tile reads nothing)
           uint4 sgn[CW / 8];
-          if (bwd) {
+          if (bwd && !SPLIT) {
 #pragma unroll
             for (int k = 0; k < CW / 8; ++k)
               sgn[k] = store_t ? reinterpret_cast<const uint4*>(P.Sg + sg_off(l - 1, tile_t, 0))[k]
@@ -982,7 +986,12 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               const int c = c2 + cc;
               const int col0 = 64 * c + CW * g;
               float* v = vv + cc * CW;
-              if (bwd) {
+              if (bwd && SPLIT) {
+                // ReLU: delta_{l-1} = v * 1[u_{l-1} > 0], the mask bits this thread kept
+                const uint32_t bits = mk[(l - 1) * 4 + c];
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] = ((bits >> i) & 1u) ? v[i] : 0.f;
+              } else if (bwd) {
                 // v = (W'_l^T delta_l) for layer l; delta_{l-1} = v * sigma'(u_{l-1})
                 float sg[CW];
 #pragma unroll
@@ -1028,11 +1037,19 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                     }
                   }
                 }
+                if (SPLIT && kind == kFwdHidden) {
+                  // the masks stay with this thread: it drains the same row and columns of the
+                  // backward stage of layer l + 1
+                  uint32_t bits = 0u;
+#pragma unroll
+                  for (int i = 0; i < CW; ++i) bits |= (cs[i] > 0.f ? 1u : 0u) << i;
+                  mk[l * 4 + c] = (uint16_t)bits;
+                }
                 if (MODE == 1 && store_t) {
-                  if (kind == kFwdHidden)  // a_l itself goes out from the panels
-                    store_row_bf16<CW>(P.Sg + sg_off(l, tile_t, c), cs);
-                  else                     // a_{L-1} is not a panel (the panels take delta_{L-1})
+                  if (kind == kFwdLast)  // a_{L-1} is not a panel (the panels take delta_{L-1})
                     store_row_bf16<CW>(P.Act + ((int64_t)l * P.npts_pad + prow_t) * W + col0, v);
+                  else if (!SPLIT)       // sigma'(u_l); a_l itself goes out from the panels
+                    store_row_bf16<CW>(P.Sg + sg_off(l, tile_t, c), cs);
                 }
                 if (kind == kFwdLast) {
                   // f(x) = w_out . a_{L-1} + b_out: this thread's share of the dot product
@@ -1522,7 +1539,8 @@ size_t vjp_layout(const Net& n, int64_t chunk, void* ws, size_t cap, TcVjpWs* ou
   w.E = n.kind == INRCT_FFN_RELU ? c.take<__nv_bfloat16>((size_t)pad * n.K0) : nullptr;
   w.Act = c.take<__nv_bfloat16>((size_t)pad * n.L * n.W);
   w.Dlt = c.take<__nv_bfloat16>((size_t)pad * n.L * n.W);
-  w.Sg = c.take<__nv_bfloat16>((size_t)pad * std::max(n.L - 1, 1) * n.W);
+  // sigma'(u_l) of the SIREN (cos u_l); the split VJP of ReLU networks keeps its masks as bits
+  w.Sg = n.kind == INRCT_SIREN ? c.take<__nv_bfloat16>((size_t)pad * std::max(n.L - 1, 1) * n.W) : nullptr;
   w.Y16c = c.take<__nv_bfloat16>((size_t)16 * pad);
   w.Y16o = c.take<__nv_bfloat16>((size_t)16 * pad);
   int64_t pf;
