@@ -582,10 +582,11 @@ __global__ void cone_prescale_kernel(GeomDev g, const int4* __restrict__ t0, con
   out[i] = sino[i] * cone_scale(vb, __ldg(t2 + ci), sa);
 }
 
-// No launch bound: with one, ptxas caps the registers and spills (56 suffice; blocks are
-// 128 threads, so any register count fits).
+// Launch bound: eight blocks of 128 threads per SM (at most 64 registers).  The 32-voxel chunk
+// then spills a little but runs fastest (501^3: 30.1 ms against 32.1 ms for 16 voxels without a
+// bound, whose 92 registers leave fewer warps resident); the smaller chunks fit in 64 registers.
 template <int ZC>
-__global__ void backproject3d_kernel(GeomDev g, const int4* __restrict__ t0, const int4* __restrict__ t1,
+__global__ void __launch_bounds__(128, 8) backproject3d_kernel(GeomDev g, const int4* __restrict__ t0, const int4* __restrict__ t1,
                             const float2* __restrict__ views, int64_t CzF,
                             const float* __restrict__ sino_s, float* __restrict__ vol) {
   extern __shared__ float2 sv[];
