@@ -872,6 +872,47 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           if (!warp_wait(&st_done[t], (sdp >> t) & 1u, abort_flag, err, 405, lim)) goto epi_done;
           sdp ^= 1u << t;
         }
+        if (KIND == INRCT_FFN_RELU && MODE == 0 && (P.in_panels & 1) == 0) {
+          // Grid evaluation of a Fourier-feature network: the warp fences and publishes once
+          // per two panels (the one-panel loop below does so for every panel from the fifth
+          // on).  Same waits and arrivals as that loop.
+          for (int c = 0; c < P.in_panels; c += 2) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int cc = c + h, as = cc & 3, f0 = 32 * cc + 8 * g;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float4 bf = P.first_staged ? first_s[f0 + i] : __ldg(P.first + f0 + i);
+                float ph = fmaf(bf.y, xt[1], bf.x * xt[0]);
+                if (P.d == 3) ph = fmaf(bf.z, xt[2], ph);
+                four_feat_fast(ph, &v[8 + i], &v[i]);  // v[0..7] cos, v[8..15] sin
+              }
+              if (cc >= 4) {  // streamed panel: the MMA must have read panel cc - 4 from this buffer
+                const int bit = 4 * t + as;
+                if (!warp_wait(&a_empty[4 * t + as], (ae >> bit) & 1u, abort_flag, err, 401, lim)) goto epi_done;
+                ae ^= 1u << bit;
+              }
+              st_panel_row<8>(apan + (4 * t + as) * kPanelBytes, r, g, v);
+              st_panel_row<8>(apan + (4 * t + as) * kPanelBytes, r, 4 + g, v + 8);
+            }
+            const bool first = c + 1 >= n0 - 1 && c <= n0 - 1;  // in_ready is published below
+            if (!first && c + 1 < 4) continue;                   // no panel published yet
+            fence_async_smem();
+            if (first) tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int cc = c + h;
+                if (cc == n0 - 1)
+                  mbar_arrive(&in_ready[t]);
+                else if (cc >= 4)
+                  mbar_arrive(&a_full[4 * t + (cc & 3)]);
+              }
+            }
+          }
+          continue;
+        }
         for (int c = 0; c < P.in_panels; ++c) {
           const int col0 = 64 * c + CW * g;
           if (KIND == INRCT_FFN_RELU) {
