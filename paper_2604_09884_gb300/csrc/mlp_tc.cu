@@ -663,7 +663,9 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   for (int i = threadIdx.x; i < W; i += blockDim.x) wout_s[i] = P.wout[i];
   if (P.first_staged)
     for (int i = threadIdx.x; i < P.n_first; i += blockDim.x) first_s[i] = P.first[i];
-  if (warp == 0) tmem_alloc(tmem_base, NSLOT * W);
+  // split mode: one tile in flight, its stages' accumulators alternate between two halves
+  const uint32_t tmem_cols = (uint32_t)(SPLIT ? 2 * W : NSLOT * W);
+  if (warp == 0) tmem_alloc(tmem_base, tmem_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -715,6 +717,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     if (lane == 0) {
       // phase parities: ring, in_ready (one bit per slot), a_full (one bit per slot and buffer)
       uint32_t slot = 0, wf = 0, irp = 0u, ap = 0u;
+      uint32_t sc = 0u;  // split mode: stages issued so far (the accumulator half is sc & 1)
       const uint32_t idesc = idesc_bf16(128, NW, false, false);
       bool issued = false;
       // VJP: the input panels of a slot (activations or deltas of its tile) are also the
@@ -732,27 +735,38 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
         const int64_t tile0 = blockIdx.x + (NSLOT * pr) * (int64_t)gridDim.x;
         for (int s = 0; s < P.n_stages; ++s) {
           const bool fsplit = SPLIT && P.st_kind[s] != kBwd;
+          // split mode, stages after the first: the epilogue publishes each input panel as soon
+          // as it has drained the previous stage's matching accumulator columns, and this stage
+          // accumulates into the other TMEM half, so its MMAs overlap the rest of that drain
+          const bool per_panel = SPLIT && s > 0;
           for (int t = 0; t < NSLOT; ++t) {
-            if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, abort_flag, err, 301, lim)) goto mma_done;
-            irp ^= 1u << t;
-            tc_fence_after();
-            if (MODE == 1 && P.st_in_arr[s] >= 0 && tile0 + t * gridDim.x < n_tiles)
-              store_panels(t, P.st_in_arr[s] ? P.map_dlt : P.map_act, P.st_in_layer[s],
-                           tile0 + t * gridDim.x);
+            const bool store_in = MODE == 1 && P.st_in_arr[s] >= 0 && tile0 + t * gridDim.x < n_tiles;
+            if (!per_panel) {
+              if (!mbar_wait(&in_ready[t], (irp >> t) & 1u, abort_flag, err, 301, lim)) goto mma_done;
+              irp ^= 1u << t;
+              tc_fence_after();
+              if (store_in)
+                store_panels(t, P.st_in_arr[s] ? P.map_dlt : P.map_act, P.st_in_layer[s],
+                             tile0 + t * gridDim.x);
+            }
+            const uint32_t dbase = tmem + (SPLIT ? (sc & 1u) * (uint32_t)W : (uint32_t)(t * W));
             const int np = P.st_panels[s];
             for (int c = 0; c < np; ++c) {
               const int as = c & 3;
-              if (c >= 4) {  // a streamed input panel (first stage only)
+              if (c >= 4 || per_panel) {  // a streamed input panel (first stage), or one of per_panel
                 const int bit = 4 * t + as;
                 if (!mbar_wait(&a_full[4 * t + as], (ap >> bit) & 1u, abort_flag, err, 302, lim)) goto mma_done;
                 ap ^= 1u << bit;
                 tc_fence_after();
+                if (per_panel && store_in)  // this panel goes out to the scratch as soon as it is in
+                  tma_store_2d(&maps.m[P.st_in_arr[s] ? P.map_dlt : P.map_act], apan + (4 * t + c) * kPanelBytes,
+                               64 * c, (int)(P.st_in_layer[s] * P.npts_pad + (tile0 + t * gridDim.x) * kTile));
               }
               const uint32_t abase = smem_u32(apan + (4 * t + as) * kPanelBytes);
               const uint32_t lbase = smem_u32(apan + (4 + as) * kPanelBytes);  // low parts (SPLIT)
               for (int kk = 0; kk < 64 / kKChunk; ++kk) {
                 for (int h = 0; h < kNSplit; ++h) {
-                  const uint32_t dcol = tmem + t * W + h * NW;
+                  const uint32_t dcol = dbase + h * NW;
                   // W_hi chunk: A_hi (and, split, A_lo) against it
                   if (!mbar_wait(&w_full[slot], wf, abort_flag, err, 303, lim)) goto mma_done;
                   tc_fence_after();
@@ -793,9 +807,11 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               }
               if (c + 4 < np) mma_commit(&a_empty[4 * t + as]);  // the buffer takes panel c + 4 next
             }
+            if (per_panel && store_in) bulk_commit_group();
             if (MODE == 1) bulk_wait_read_all();
             mma_commit(&acc_full[t]);
           }
+          if (SPLIT) ++sc;
         }
         if (MODE == 1) {
           // the deltas of the last stage: stored, then the feature pass of the next group may
@@ -824,6 +840,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     const int r = q * 32 + lane;                 // row of the tile = TMEM lane
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     uint32_t ae = 0u, af = 0u, sdp = 0u, dot_uses = 0u;  // phase parities (a_empty per slot and buffer; per slot)
+    uint32_t sc = 0u;  // split mode: stages drained so far (the accumulator half is sc & 1), as the MMA issuer counts
     // offset of this thread's CW sigma' values of (layer, tile, 64-column chunk c) in P.Sg
     auto sg_off = [&](int layer, int64_t tile, int c) -> int64_t {
       return ((((int64_t)layer * n_tiles + tile) * (W / 64) + c) * NWG + g) * (kTile * CW) + (int64_t)r * CW;
@@ -998,6 +1015,9 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           const int64_t tile_t = t ? tile1 : tile0;
           const bool bwd = MODE == 1 && kind == kBwd;
           const bool pub = write_panel || MODE == 1;  // VJP: the last deltas are stored from the panels
+          // split mode: each panel of the next stage's input is published as soon as it is written
+          const bool per_panel_out = SPLIT && s + 1 < P.n_stages;
+          const uint32_t hcol = SPLIT ? (sc & 1u) * (uint32_t)W : (uint32_t)(t * W);
           // backward: sigma'(u_{l-1}) of this tile; chunk c + 1 is fetched while chunk c is
           // processed, chunk 0 before the wait for the accumulator (a dummy tile reads nothing)
           uint4 sgn[CW / 8];
@@ -1018,10 +1038,10 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           for (int c2 = 0; c2 < W / 64; c2 += kPair) {
             float vv[kPair * CW];
             if constexpr (kPair == 2)
-              tmem_ld16x2(tmem + lane_off + t * W + 64 * c2 + CW * g,
-                          tmem + lane_off + t * W + 64 * (c2 + 1) + CW * g, vv);
+              tmem_ld16x2(tmem + lane_off + hcol + 64 * c2 + CW * g,
+                          tmem + lane_off + hcol + 64 * (c2 + 1) + CW * g, vv);
             else
-              tmem_ld<CW>(tmem + lane_off + t * W + 64 * c2 + CW * g, vv);
+              tmem_ld<CW>(tmem + lane_off + hcol + 64 * c2 + CW * g, vv);
 #pragma unroll
             for (int cc = 0; cc < kPair; ++cc) {
               const int c = c2 + cc;
@@ -1121,12 +1141,22 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
                 st_panel_row<CW>(apan + (4 * t + c) * kPanelBytes, r, (CW / 8) * g, v);
                 if (write_lo) st_panel_row_lo<CW>(apan + (4 + c) * kPanelBytes, r, (CW / 8) * g, v);
               }
+              if (per_panel_out) {
+                // this warp's rows and columns of panel c are written (and its accumulator
+                // columns read): with the other 15 warps' arrivals the MMAs may take the panel
+                fence_async_smem();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&a_full[4 * t + c]);
+              }
             }
           }
-          if (pub) fence_async_smem();
-          tc_fence_before();
-          __syncwarp();
-          if (pub && lane == 0) mbar_arrive(&in_ready[t]);
+          if (!per_panel_out) {
+            if (pub) fence_async_smem();
+            tc_fence_before();
+            __syncwarp();
+            if (pub && lane == 0) mbar_arrive(&in_ready[t]);
+          }
           if (kind == kFwdLast) {
             // f = b_out + sum of the NWG column-group partial dot products of row r; one
             // scratch buffer per row quarter, released by its summing warp (dot_free)
@@ -1152,6 +1182,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
             ++dot_uses;
           }
         }
+        if (SPLIT) ++sc;
       }
     }
     if (MODE == 1 && g == 0) {
@@ -1171,7 +1202,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, NSLOT * W);
+    tmem_dealloc(tmem, tmem_cols);
   }
 }
 
