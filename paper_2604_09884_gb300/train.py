@@ -7,7 +7,7 @@ the index sets, keeps the Adam state, and reports:
 - a JSON line per logged step: the loss at the incoming theta, the MSE of the INR image against
   the phantom (when one is given), the norm of the estimated gradient and the step's wall time;
 - checkpoints holding theta, the Adam moments, the step index, the seed and the projector's launch
-  plan.  Index set t is drawn from (seed, t) alone and loading a checkpoint pins its plan, so a
+  plans.  Index set t is drawn from (seed, t) alone and loading a checkpoint pins its plan, so a
   run resumed from a checkpoint takes exactly the steps an uninterrupted run takes (bit for bit:
   every kernel of the step is deterministic, except the FP64 atomics of the hash-encoded INR's
   table gradient).
@@ -58,16 +58,22 @@ class Trainer:
     mlp: an ``inrct.MlpHandle`` (its precision selects the BF16 or the FP32 path); theta: the
     initial parameters (copied); n_idx: |I| (g.n for the plain full-gradient form); seed: the
     seed of the index sets.  Index set t is drawn on the device: the first |I| entries of a
-    permutation of [0, n) from a generator seeded with seed * 1000003 + t, sorted.
+    permutation of [0, n) from a generator seeded with seed * 1000003 + t, sorted.  subsets: S > 1
+    takes the ordered-subsets form of Sec. 3, step t fitting interleaved view subset (t - 1) mod S
+    (``inrct.view_subset``) with that subset's rows of the data; each subset keeps its own
+    workspace, so its ray tables are built once.
     """
 
     def __init__(self, problem: Problem, mlp: inrct.MlpHandle, theta: torch.Tensor, n_idx: int, lr: float,
-                 seed: int = 0, loss_kind: int = inrct.LOSS_LS):
+                 seed: int = 0, loss_kind: int = inrct.LOSS_LS, subsets: int = 1):
         g = problem.geom
         if not 1 <= n_idx <= g.n:
             raise ValueError(f"|I| = {n_idx} outside [1, {g.n}]")
         self.problem, self.mlp, self.n_idx, self.lr, self.seed = problem, mlp, int(n_idx), float(lr), int(seed)
         self.loss_kind = loss_kind
+        self.subsets = S = int(subsets)
+        self.sub_g = [inrct.view_subset(g, S, k) for k in range(S)] if S > 1 else [g]
+        self.sub_y = [inrct.view_subset_rows(g, problem.y, S, k) for k in range(S)] if S > 1 else [problem.y]
         dev = theta.device
         self.theta = theta.detach().clone().contiguous()
         self.m = torch.zeros_like(self.theta)
@@ -75,7 +81,8 @@ class Trainer:
         self.t = 0                                        # steps taken
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
         self.grad = torch.zeros(mlp.p, dtype=torch.float64, device=dev)
-        self.ws = torch.empty(inrct.step_ws_bytes(g, mlp, self.n_idx), dtype=torch.uint8, device=dev)
+        self.ws = [torch.empty(inrct.step_ws_bytes(q, mlp, self.n_idx), dtype=torch.uint8, device=dev)
+                   for q in self.sub_g]
 
     def index_set(self, t: int) -> torch.Tensor:
         n, dev = self.problem.geom.n, self.theta.device
@@ -88,10 +95,10 @@ class Trainer:
 
     def step(self) -> None:
         """One step of Algorithm 1 followed by Adam (step index t + 1)."""
-        g = self.problem.geom
+        k = self.t % self.subsets
         idx = self.index_set(self.t + 1)
-        inrct.grad_step(g, self.mlp, self.theta, self.problem.y, idx, g.n / self.n_idx,
-                        inrct.adam(lr=self.lr, t=self.t + 1), self.m, self.s, self.loss, self.grad, self.ws,
+        inrct.grad_step(self.sub_g[k], self.mlp, self.theta, self.sub_y[k], idx, self.problem.geom.n / self.n_idx,
+                        inrct.adam(lr=self.lr, t=self.t + 1), self.m, self.s, self.loss, self.grad, self.ws[k],
                         self.loss_kind)
         self.t += 1
 
@@ -108,24 +115,25 @@ class Trainer:
 
     # ---- checkpoints ----
     def state(self) -> dict:
-        plan = inrct.tune_plan(self.problem.geom)
+        plans = [inrct.tune_plan(q) for q in self.sub_g]
         return {"theta": self.theta.clone(), "m": self.m.clone(), "s": self.s.clone(), "t": self.t,
-                "seed": self.seed, "n_idx": self.n_idx, "lr": self.lr,
-                "plan": (plan["seg"], plan["bp_splits"], plan["zc"])}
+                "seed": self.seed, "n_idx": self.n_idx, "lr": self.lr, "subsets": self.subsets,
+                "plans": [(p["seg"], p["bp_splits"], p["zc"]) for p in plans]}
 
     def save(self, path: str) -> None:
         torch.save(self.state(), path)
 
     def load(self, path: str) -> None:
         st = torch.load(path, map_location=self.theta.device)
-        if st["n_idx"] != self.n_idx or st["seed"] != self.seed:
-            raise ValueError("checkpoint of another run (|I| or seed differ)")
+        if st["n_idx"] != self.n_idx or st["seed"] != self.seed or st["subsets"] != self.subsets:
+            raise ValueError("checkpoint of another run (|I|, seed or view subsets differ)")
         self.theta.copy_(st["theta"])
         self.m.copy_(st["m"])
         self.s.copy_(st["s"])
         self.t = int(st["t"])
         self.lr = float(st["lr"])
-        inrct.tune_set(self.problem.geom, *st["plan"])  # the summation order of P and P^T
+        for q, plan in zip(self.sub_g, st["plans"]):
+            inrct.tune_set(q, *plan)  # the summation order of P and P^T
 
 
 def run(tr: Trainer, steps: int, log_every: int = 1, log=None, checkpoint: str | None = None,
@@ -170,6 +178,7 @@ def main(argv=None):
     p.add_argument("--lr", type=float, default=None)
     p.add_argument("--log-every", type=int, default=10)
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--subsets", type=int, default=1, help="ordered subsets of the views (Sec. 3)")
     p.add_argument("--out", default="runs", help="directory of the JSONL logs and checkpoints")
     a = p.parse_args(argv)
     w = synth.workloads()[a.workload]
@@ -184,7 +193,7 @@ def main(argv=None):
     summary = {}
     for name, prec, n_idx in runs:
         mlp = inrct.mlp_desc(arch, prec if arch.kind != "hash" else inrct.FP32, B)
-        tr = Trainer(prob, mlp, theta0, n_idx, a.lr if a.lr is not None else w.lr, seed=a.seed)
+        tr = Trainer(prob, mlp, theta0, n_idx, a.lr if a.lr is not None else w.lr, seed=a.seed, subsets=a.subsets)
         with open(os.path.join(a.out, f"{name}.jsonl"), "w") as log:
             recs = run(tr, a.steps, a.log_every, log, os.path.join(a.out, f"{name}.pt"), a.steps)
         timed = [r["step_ms"] for r in recs if r["step_ms"] is not None]

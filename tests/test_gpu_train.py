@@ -21,7 +21,7 @@ def mods():
     return inrct, synth, train
 
 
-def _trainer(mods, wname, prec, frac, seed=0):
+def _trainer(mods, wname, prec, frac, seed=0, subsets=1):
     inrct, synth, train = mods
     w = synth.workloads()[wname]
     a, g = w.arch, w.geom
@@ -29,14 +29,15 @@ def _trainer(mods, wname, prec, frac, seed=0):
     B = synth.fourier_matrix(a.n_feat, a.d, a.sigma, w.seed + 2) if a.kind == "ffn" else None
     mlp = inrct.mlp_desc(a, prec, B)
     theta0 = torch.tensor(synth.init_theta(a, w.seed + 3), dtype=torch.float32, device="cuda")
-    return train.Trainer(prob, mlp, theta0, max(1, int(round(frac * g.n))), w.lr, seed=seed)
+    return train.Trainer(prob, mlp, theta0, max(1, int(round(frac * g.n))), w.lr, seed=seed, subsets=subsets)
 
 
-@pytest.mark.parametrize("wname,prec_name", [("fan2d_512_siren256", "BF16"), ("par2d_128_ffn64", "FP32")])
-def test_resume_from_checkpoint_is_bit_exact(mods, tmp_path, wname, prec_name):
+@pytest.mark.parametrize("wname,prec_name,subsets", [("fan2d_512_siren256", "BF16", 1), ("par2d_128_ffn64", "FP32", 1),
+                                                     ("fan2d_512_siren256", "BF16", 3)])
+def test_resume_from_checkpoint_is_bit_exact(mods, tmp_path, wname, prec_name, subsets):
     inrct, synth, train = mods
     prec = getattr(inrct, prec_name)
-    ref = _trainer(mods, wname, prec, 0.25)
+    ref = _trainer(mods, wname, prec, 0.25, subsets=subsets)
     with open(tmp_path / "ref.jsonl", "w") as log:
         recs = train.run(ref, 20, log_every=5, log=log)
     lines = [json.loads(x) for x in open(tmp_path / "ref.jsonl")]
@@ -46,10 +47,10 @@ def test_resume_from_checkpoint_is_bit_exact(mods, tmp_path, wname, prec_name):
     for r in recs[1:]:
         assert r["loss"] > 0 and r["grad_norm"] > 0 and r["step_ms"] > 0 and r["mse_vs_x_true"] > 0
 
-    first = _trainer(mods, wname, prec, 0.25)
+    first = _trainer(mods, wname, prec, 0.25, subsets=subsets)
     ck = str(tmp_path / "ck.pt")
     train.run(first, 10, log_every=10, checkpoint=ck, checkpoint_every=10)
-    resumed = _trainer(mods, wname, prec, 0.25)
+    resumed = _trainer(mods, wname, prec, 0.25, subsets=subsets)
     resumed.load(ck)
     assert resumed.t == 10
     train.run(resumed, 20, log_every=10)
@@ -57,7 +58,7 @@ def test_resume_from_checkpoint_is_bit_exact(mods, tmp_path, wname, prec_name):
     assert torch.equal(resumed.m, ref.m) and torch.equal(resumed.s, ref.s)
     assert resumed.metrics()["loss"] == recs[-1]["loss"]
 
-    other = _trainer(mods, wname, prec, 0.25, seed=1)
+    other = _trainer(mods, wname, prec, 0.25, seed=1, subsets=subsets)
     with pytest.raises(ValueError):
         other.load(ck)
 
@@ -92,3 +93,14 @@ def test_fan512_training_curves_track_the_full_gradient(mods, tmp_path):
         # measured: every logged MSE within 0.88-1.13 of the FP32 full-gradient run's
         for k, (a, b) in enumerate(zip(c, ref)):
             assert a < 1.25 * b, (name, 50 * k, a, b)
+
+
+def test_ordered_subsets_training_reduces_the_error(mods):
+    """Ordered subsets (Sec. 3): 3 interleaved subsets of the 90 views, one per step, 120 steps."""
+    inrct, synth, train = mods
+    tr = _trainer(mods, "fan2d_512_siren256", inrct.BF16, 0.25, subsets=3)
+    assert [q.V for q in tr.sub_g] == [30, 30, 30]
+    recs = train.run(tr, 120, log_every=40)
+    mse = [r["mse_vs_x_true"] for r in recs]
+    assert mse[-1] < 0.5 * mse[0]
+    assert all(b < a for a, b in zip(mse, mse[1:]))
