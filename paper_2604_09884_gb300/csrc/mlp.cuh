@@ -14,6 +14,7 @@ struct Net {
   int d, F, W, L;  // input dim, Fourier features, width, nonlinear layers
   float omega0;
   const float* B;  // device F x d
+  const float* B_host;  // optional host copy of B (NULL if not given)
   int K0;          // input width of layer 1 (2F, d, or hash levels x features)
   int64_t p;       // parameter count
   // hash encoding: levels, features per level, log2 of the table size, the level

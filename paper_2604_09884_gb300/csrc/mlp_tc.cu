@@ -37,6 +37,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 
 #include "mlp.cuh"
 #include "tc_ptx.cuh"
@@ -160,6 +161,28 @@ int make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, u
 
 struct Maps {
   CUtensorMap m[kMaxJobs];
+};
+
+// Launch-parameter copy of the first-layer table of a Fourier-feature network (entries
+// {B_0, B_1, B_2, 0} as in PrepTable), for the grid evaluation: read through the constant
+// cache, it takes nothing from the shared-memory bandwidth the MMAs' operand reads use.  n = 0:
+// not given (the kernel reads the table from shared memory).  Other kernel instances take the
+// 4-byte placeholder.
+constexpr int kMaxConstFirst = 1024;
+struct FirstConst {
+  int n;
+  float4 c[kMaxConstFirst];
+};
+struct NoFirstConst {
+  int n;
+};
+template <int MODE, int KIND, bool SPLIT>
+struct FirstArg {
+  using type = NoFirstConst;
+};
+template <>
+struct FirstArg<0, INRCT_FFN_RELU, false> {
+  using type = FirstConst;
 };
 
 // ---------------------------------------------------------------------------
@@ -589,6 +612,7 @@ __device__ __forceinline__ void four_feat_fast(float ph, float* s, float* c) {
 template <int MODE, int KIND, int NWG, bool SPLIT>
 __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
     mlp_tile_kernel(const __grid_constant__ Maps maps, const __grid_constant__ TileProg P,
+                    const __grid_constant__ typename FirstArg<MODE, KIND, SPLIT>::type FC,
                     int* __restrict__ err) {
   constexpr int NSLOT = SPLIT ? 1 : 2;
   static_assert(!SPLIT || MODE == 1, "split operands serve the VJP's mask decisions");
@@ -954,9 +978,7 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
           for (int c = 0; c < P.in_panels; ++c) {
             const int as = c & 3, f0 = 32 * c + 8 * g;
             float v0[16], v1[16];  // [0, 8) cos, [8, 16) sin of tile 0's and tile 1's point
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float4 bf = P.first_staged ? first_s[f0 + i] : __ldg(P.first + f0 + i);
+            auto feature = [&](int i, const float4 bf) {
               float p0 = fmaf(bf.y, x0[1], bf.x * x0[0]);
               float p1 = fmaf(bf.y, x1[1], bf.x * x1[0]);
               if (P.d == 3) {
@@ -965,6 +987,17 @@ __global__ void __launch_bounds__(32 * (4 * NWG + 2), 1)
               }
               four_feat_fast(p0, &v0[8 + i], &v0[i]);
               four_feat_fast(p1, &v1[8 + i], &v1[i]);
+            };
+            // the table's source is uniform for the launch: one branch, not a select per read
+            if (FC.n) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) feature(i, FC.c[f0 + i]);
+            } else if (P.first_staged) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) feature(i, first_s[f0 + i]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) feature(i, __ldg(P.first + f0 + i));
             }
             if (c >= 4) {  // streamed panels: the MMAs must have read panel c - 4 of both tiles
 #pragma unroll
@@ -1316,7 +1349,17 @@ int launch_tile_t(const Net& n, const Maps& maps, const TileProg& P, int grid, i
     set_error("tile kernel shared memory (%zu bytes): %s", sm, cudaGetErrorString(e));
     return INRCT_ERR_CUDA;
   }
-  mlp_tile_kernel<MODE, KIND, kTileNWG, SPLIT><<<grid, 32 * (4 * kTileNWG + 2), sm, st>>>(maps, P, err);
+  typename FirstArg<MODE, KIND, SPLIT>::type fc{};
+  if constexpr (std::is_same_v<typename FirstArg<MODE, KIND, SPLIT>::type, FirstConst>) {
+    if (n.B_host && n.F <= kMaxConstFirst) {  // the same entries prep_all_kernel writes
+      fc.n = n.F;
+      for (int f = 0; f < n.F; ++f) {
+        const float* b = n.B_host + (size_t)f * n.d;
+        fc.c[f] = make_float4(b[0], b[1], n.d == 3 ? b[2] : 0.f, 0.f);
+      }
+    }
+  }
+  mlp_tile_kernel<MODE, KIND, kTileNWG, SPLIT><<<grid, 32 * (4 * kTileNWG + 2), sm, st>>>(maps, P, fc, err);
   INRCT_CHECK_LAUNCH("mlp tile kernel");
   return INRCT_OK;
 }

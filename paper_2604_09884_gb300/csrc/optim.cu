@@ -63,6 +63,7 @@ int make_net(const inrct_mlp* mlp, const inrct_grid* grid, Net* n) {
   n->L = mlp->n_hidden;
   n->omega0 = mlp->omega0;
   n->B = mlp->B;
+  n->B_host = mlp->kind == INRCT_FFN_RELU ? mlp->B_host : nullptr;
   n->K0 = mlp->kind == INRCT_FFN_RELU ? 2 * mlp->n_feat
           : mlp->kind == INRCT_HASH    ? n->hL * n->hF
                                        : mlp->d;

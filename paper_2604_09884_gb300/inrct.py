@@ -51,7 +51,7 @@ class Mlp(ctypes.Structure):
                 ("width", ctypes.c_int), ("prec", ctypes.c_int),
                 ("hash_levels", ctypes.c_int), ("hash_feats", ctypes.c_int),
                 ("hash_log2_T", ctypes.c_int), ("hash_base", ctypes.c_int),
-                ("hash_growth", ctypes.c_double)]
+                ("hash_growth", ctypes.c_double), ("B_host", ctypes.c_void_p)]
 
 
 class Adam(ctypes.Structure):
@@ -193,10 +193,12 @@ def view_subset_rows(g: synth.GeomSpec, sino: torch.Tensor, n_subsets: int, s: i
 
 @dataclass
 class MlpHandle:
-    """An inrct_mlp descriptor plus the device Fourier matrix it points to."""
+    """An inrct_mlp descriptor plus the device Fourier matrix it points to (and the host copy
+    that B_host points to)."""
     desc: Mlp
     B: torch.Tensor | None
     spec: synth.ArchSpec
+    B_host: torch.Tensor | None = None
 
     @property
     def p(self):
@@ -204,17 +206,20 @@ class MlpHandle:
 
 
 def mlp_desc(a: synth.ArchSpec, prec: int, B=None, device="cuda") -> MlpHandle:
-    Bt = None
+    Bt = Bh = None
     if a.kind == "ffn":
         Bt = torch.as_tensor(B, dtype=torch.float32, device=device).contiguous()
         assert Bt.shape == (a.n_feat, a.d)
+        Bh = Bt.cpu().contiguous()  # the same values, for B_host
     kind = {"ffn": FFN_RELU, "siren": SIREN, "hash": HASH}[a.kind]
     desc = Mlp(kind, a.d, a.n_feat, Bt.data_ptr() if Bt is not None else None, a.omega0,
                a.n_hidden, a.width, prec)
     if a.kind == "hash":
         desc.hash_levels, desc.hash_feats, desc.hash_log2_T = a.hash_levels, a.hash_feats, a.hash_log2_T
         desc.hash_base, desc.hash_growth = a.hash_base, a.hash_growth
-    return MlpHandle(desc, Bt, a)
+    if Bh is not None:
+        desc.B_host = Bh.data_ptr()
+    return MlpHandle(desc, Bt, a, Bh)
 
 
 # ----------------------------------------------------------------------------

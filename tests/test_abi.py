@@ -236,3 +236,13 @@ def test_binding_refuses_wrong_buffers_before_any_launch(L):
         inrct.project(g, torch.zeros(g.n - 1))
     with pytest.raises(ValueError, match="sino"):
         inrct.backproject(g, torch.zeros(g.m - 1))
+
+
+def test_mlp_struct_mirrors_the_header():
+    """The binding's inrct_mlp mirror has the header's fields, in the header's order."""
+    hdr = open(os.path.join(ROOT, "include", "inrct.h")).read()
+    body = hdr[:hdr.index("} inrct_mlp;")]
+    body = body[body.rindex("typedef struct {") + len("typedef struct {"):]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = [re.findall(r"\**(\w+)\s*$", decl.strip())[0] for decl in body.split(";") if decl.strip()]
+    assert names == [f[0] for f in inrct.Mlp._fields_]

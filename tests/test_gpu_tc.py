@@ -79,6 +79,22 @@ def test_eval_grid_bf16_matches_oracle(spec):
     assert err <= 2e-2, err
 
 
+@pytest.mark.parametrize("spec", [a for a in ARCHS if a.kind == "ffn"],
+                         ids=lambda a: f"{a.kind}{a.d}d_{a.width}x{a.n_hidden}")
+def test_eval_grid_coefficients_as_launch_parameters_change_nothing(spec):
+    """With B_host the Fourier coefficients reach the kernel as launch parameters instead of a
+    shared-memory table: the image must be bit-identical (the same values, the same arithmetic)."""
+    N = 67 if spec.d == 2 else 21
+    _, B32 = arch_pair(spec, 1)
+    theta = cuda(synth.init_theta(spec, 2).astype(np.float32))
+    h = inrct.mlp_desc(spec, inrct.BF16, B32)
+    assert h.desc.B_host
+    with_params = inrct.inr_eval_grid(h, theta, N)
+    h.desc.B_host = None
+    from_shared = inrct.inr_eval_grid(h, theta, N)
+    assert torch.equal(with_params, from_shared)
+
+
 def kink_free(oa, theta, X, tau=1e-6):
     """Points whose ReLU pre-activations (FP64) all stay at least tau * rms away from zero."""
     if oa.kind != "ffn":
