@@ -582,6 +582,158 @@ __global__ void cone_prescale_kernel(GeomDev g, const int4* __restrict__ t0, con
   out[i] = sino[i] * cone_scale(vb, __ldg(t2 + ci), sa);
 }
 
+// As cone_prescale_kernel, written column-major per view ([view][column][row]) for the column
+// kernel below, which stages one detector column's rows at a time.
+__global__ void cone_prescale_t_kernel(GeomDev g, const int4* __restrict__ t0, const float* __restrict__ t2,
+                                       float pv_half, const float* __restrict__ sino, float* __restrict__ out) {
+  const int64_t m = (int64_t)g.V * g.B * g.A;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int a = (int)(i % g.A);
+  const int64_t kb = i / g.A;
+  const int b = (int)(kb % g.B), k = (int)(kb / g.B);
+  const size_t ci = (size_t)k * g.A + a;
+  const float sa = fabsf(__int_as_float(__ldg(t0 + ci).w));
+  const float vb = __fmul_rn((float)(2 * b - (g.B - 1)), pv_half);
+  out[ci * g.B + b] = sino[i] * cone_scale(vb, __ldg(t2 + ci), sa);
+}
+
+// Cone adjoint, one warp per (x, y) column of the volume: lane l gathers voxels l*VL .. l*VL+VL-1.
+// For a view and a detector column, the window, the tap weight and the row pitch are the same
+// for the whole warp, so the lanes run the row sweep of backproject3d_kernel in step (there,
+// neighbouring lanes are neighbouring x with their own windows and row counts, and about half
+// of the lanes idle on average).  The warp first stages the detector column's rows that can reach
+// the volume ([view][column][row] sinogram: one coalesced read) in shared memory; each lane then
+// sweeps its chunk exactly as backproject3d_kernel<VL> does.  N <= 32 VL, at most kColStrip rows.
+constexpr int kColStrip = 1024;
+constexpr int kColWarps = 8;
+template <int VL>
+__global__ void __launch_bounds__(32 * kColWarps, 4) backproject3d_col_kernel(GeomDev g, const int4* __restrict__ t0,
+    const int4* __restrict__ t1, const float2* __restrict__ views, int64_t CzF,
+    const float* __restrict__ sino_t, float* __restrict__ vol) {
+  extern __shared__ float2 sv[];  // [V] view directions, then kColWarps strips of kColStrip rows
+  float* strips = reinterpret_cast<float*>(sv + g.V);
+  for (int k = threadIdx.x; k < g.V; k += blockDim.x) sv[k] = views[k];
+  __syncthreads();
+  const int N = g.N, A = g.A, B = g.B;
+  const int jref = N / 2;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int ix = blockIdx.x * kColWarps + wi, iy = blockIdx.y;
+  if (ix >= N) return;  // a whole warp
+  float* strip = strips + wi * kColStrip;
+  const int z0 = lane * VL;
+  const float D = 2.f / (float)N;
+  const float px = -1.f + ((float)ix + 0.5f) * D, py = -1.f + ((float)iy + 0.5f) * D;
+  const float cA = 0.5f * (float)(A - 1), Bm1 = (float)(B - 1);
+  const float Cz = 0.5f * (float)N - 0.5f;
+  const float R = (float)(g.sod * (2.0 / N));
+  const float kcol = (float)(g.sod / g.du);
+  const float kha = (float)(1.3 * (2.0 / N) * g.sod / g.du);
+  float acc[VL];
+#pragma unroll
+  for (int q = 0; q < VL; ++q) acc[q] = 0.f;
+  for (int k = 0; k < g.V; ++k) {
+    const float cb = sv[k].x, sb = sv[k].y;
+    const float depth = R - (cb * px + sb * py);
+    const float ucoord = -sb * px + cb * py;
+    const float ac = fmaf(ucoord / depth, kcol, cA);
+    const float ha = kha / depth + 0.02f;
+    const int a0i = max(0, (int)ceilf(ac - ha));
+    const int a1i = min(A - 1, (int)floorf(ac + ha));
+    for (int a = a0i; a <= a1i; ++a) {
+      const size_t ci = (size_t)k * A + a;
+      const int4 P = __ldg(t0 + ci);
+      const float sa = __int_as_float(P.w);
+      const bool xd = sa > 0.f;
+      const int j = xd ? ix : iy, q = xd ? iy : ix;
+      const int64_t dj = j - jref;
+      const float wq = tap_weight(ray_U0(P) + dj * slope_fx(P), q);
+      if (wq == 0.f) continue;
+      const int4 T1 = __ldg(t1 + ci);
+      const int64_t Hh = ((int64_t)T1.y << 32) | (int64_t)(uint32_t)T1.x;
+      const int64_t Kk = ((int64_t)T1.w << 32) | (int64_t)(uint32_t)T1.z;
+      const float hg = fmaf((float)dj,
+                            fmaf(__uint2float_rn((uint32_t)T1.z), 3.552713678800501e-15f,
+                                 __int2float_rn(T1.w) * 1.52587890625e-05f),
+                            fmaf(__uint2float_rn((uint32_t)T1.x), 2.3283064365386963e-10f, __int2float_rn(T1.y)));
+      const float inv_hg = __frcp_rn(hg);
+      const float hb = 0.5f * fabsf(inv_hg) * 1.001f + 0.02f;
+      const float* scol = sino_t + ci * B;  // this view's detector column, rows contiguous
+      if (fabsf(hg) > 1e-3f) {
+        // the rows that can reach any voxel of the column (the chunks' bounds, united)
+        const float cz0 = 0.5f * fmaf(-Cz, inv_hg, Bm1);
+        const float cz1 = 0.5f * fmaf((float)(N - 1) - Cz, inv_hg, Bm1);
+        const int sl = max(0, (int)ceilf(fminf(cz0, cz1) - hb));
+        const int sh = min(B - 1, (int)floorf(fmaxf(cz0, cz1) + hb));
+        if (sl > sh) continue;
+        __syncwarp();  // the previous strip is no longer read
+        for (int i = lane; i <= sh - sl; i += 32) strip[i] = __ldg(scol + sl + i);
+        __syncwarp();
+        if (z0 >= N) continue;
+        // this lane's chunk: the row sweep of backproject3d_kernel, its rows clipped to the strip
+        const float bzA = 0.5f * fmaf((float)z0 - Cz, inv_hg, Bm1);
+        const float bzB = 0.5f * fmaf((float)(z0 + VL - 1) - Cz, inv_hg, Bm1);
+        const int bl = max(sl, (int)ceilf(fminf(bzA, bzB) - hb));
+        const int bh = min(sh, (int)floorf(fmaxf(bzA, bzB) + hb));
+        if (bl > bh) continue;
+        const int dir = hg > 0.f ? 1 : -1;
+        const int bfirst = dir > 0 ? bl : bh;
+        const float nrow = (float)(bh - bl + 1);
+        const int mr = 2 * bfirst - (B - 1);
+        const int64_t Zf = CzF + (int64_t)mr * Hh + dj * (((int64_t)mr * Kk) >> 16) - ((int64_t)z0 << 32);
+        const float u0 = (float)Zf * 2.3283064365386963e-10f;  // * 2^-32
+        const float du = 2.f * fabsf(hg);
+        const float* sp = strip + (bfirst - sl);
+        float rr = 0.f, u = u0;
+        while (rr < nrow && u < -1.f) {
+          rr += 1.f;
+          sp += dir;
+          u = fmaf(rr, du, u0);
+        }
+        while (rr < nrow && u < 0.f) {  // floor(u) = -1: f = u + 1 to voxel 0
+          acc[0] = fmaf(wq * (u + 1.f), *sp, acc[0]);
+          rr += 1.f;
+          sp += dir;
+          u = fmaf(rr, du, u0);
+        }
+#pragma unroll
+        for (int zq = 0; zq < VL; ++zq) {
+          while (rr < nrow && u < (float)(zq + 1)) {  // floor(u) = zq
+            const float ws = wq * *sp;
+            const float f = u - (float)zq;
+            acc[zq] = fmaf(-f, ws, acc[zq] + ws);
+            if (zq + 1 < VL) acc[zq + 1] = fmaf(f, ws, acc[zq + 1]);
+            rr += 1.f;
+            sp += dir;
+            u = fmaf(rr, du, u0);
+          }
+        }
+        continue;
+      }
+      if (z0 >= N) continue;
+#pragma unroll
+      for (int zq = 0; zq < VL; ++zq) {
+        const int iz = z0 + zq;
+        if (iz >= N) break;
+        const float bz = 0.5f * fmaf((float)iz - Cz, inv_hg, Bm1);
+        const int bb0 = max(0, (int)ceilf(bz - hb));
+        const int bb1 = min(B - 1, (int)floorf(bz + hb));
+        int mr = 2 * bb0 - (B - 1);
+        int64_t Zb = CzF + (int64_t)mr * Hh, Pk = (int64_t)mr * Kk;
+        for (int b = bb0; b <= bb1; ++b, Zb += 2 * Hh, Pk += 2 * Kk) {
+          const float wz = tap_weight(Zb + dj * (Pk >> 16), iz);
+          if (wz != 0.f) acc[zq] = fmaf(wq * wz, __ldg(scol + b), acc[zq]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int zq = 0; zq < VL; ++zq) {
+    const int iz = z0 + zq;
+    if (iz < N) vol[((size_t)iz * N + iy) * N + ix] = acc[zq];
+  }
+}
+
 // Launch bound: eight blocks of 128 threads per SM (at most 64 registers).  The 32-voxel chunk
 // then spills a little but runs fastest (501^3: 30.1 ms against 32.1 ms for 16 voxels without a
 // bound, whose 92 registers leave fewer warps resident); the smaller chunks fit in 64 registers.
@@ -868,7 +1020,9 @@ static int default_bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
 // A plan fixes the launch shape of P and P^T for one geometry: the ray segments per
 // block of the forward (2-D 4, 8 or 16; cone 2, 4 or 8), the view splits of the 2-D
 // adjoint (1 up to twice the default, at most one split per 8 views) and the voxels per
-// thread along z of the cone adjoint (4, 8, 16 or 32).  Without tuning the defaults above apply;
+// thread along z of the cone adjoint (4, 8, 16 or 32; 0 selects backproject3d_col_kernel, one warp
+// per (x, y) column, where it fits: N <= 512, at most kColStrip detector rows; 501^3 P^T 30.1 ->
+// 23.1 ms against 32 voxels per thread).  Without tuning the defaults above apply;
 // tune_impl times every candidate on the caller's stream and keeps the fastest in a
 // process-wide table keyed by the geometry's kind and sizes, which every later call
 // consults.  Workspaces are sized for the largest candidate, so a workspace sized before
@@ -880,11 +1034,17 @@ static int max_bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
   return std::max(1, std::min(most, 2 * default_bp_splits(geom, grid)));
 }
 
+// The cone adjoint's column kernel (plan zc = 0: one warp per (x, y) column) takes volumes of
+// side N <= 512 and detector columns of at most kColStrip rows.
+static bool col_kernel_fits(const inrct_geom* geom, const inrct_grid* grid) {
+  return geom->kind == INRCT_CONE3D && grid->N <= 512 && geom->n_bins_v <= kColStrip;
+}
+
 static ProjPlan default_plan(const inrct_geom* geom, const inrct_grid* grid) {
   ProjPlan p;
   p.seg = geom->kind == INRCT_CONE3D ? 4 : 8;
   p.bp_splits = default_bp_splits(geom, grid);
-  p.zc = 8;
+  p.zc = col_kernel_fits(geom, grid) ? 0 : 8;
   return p;
 }
 
@@ -931,8 +1091,9 @@ int plan_set(const inrct_geom* geom, const inrct_grid* grid, const ProjPlan& p) 
   INRCT_REQUIRE(seg_ok, "segments per ray %d not a candidate for this geometry", p.seg);
   INRCT_REQUIRE(p.bp_splits >= 1 && p.bp_splits <= max_bp_splits(geom, grid), "view splits %d out of range (1..%d)",
                 p.bp_splits, max_bp_splits(geom, grid));
-  INRCT_REQUIRE(p.zc == 4 || p.zc == 8 || p.zc == 16 || p.zc == 32, "voxels per thread along z %d not 4, 8, 16 or 32",
-                p.zc);
+  INRCT_REQUIRE(p.zc == 4 || p.zc == 8 || p.zc == 16 || p.zc == 32 || (p.zc == 0 && (!cone || col_kernel_fits(geom, grid))),
+                "voxels per thread along z %d not 4, 8, 16 or 32 (or 0: the column kernel, N <= 512 and at most %d "
+                "detector rows)", p.zc, kColStrip);
   std::lock_guard<std::mutex> lk(g_plan_mu);
   g_plans[plan_key(geom, grid)] = p;
   return INRCT_OK;
@@ -1070,6 +1231,24 @@ static int backproject_run(const inrct_geom* geom, const inrct_grid* grid, const
     int64_t CzF;
     cone_consts(g, &pvh, &CzF);
     const int64_t m = num_rays(geom);
+    if (plan.zc == 0) {
+      // one warp per (x, y) column (see backproject3d_col_kernel); plan_set and default_plan
+      // only give zc = 0 when the kernel fits the geometry
+      INRCT_REQUIRE(col_kernel_fits(geom, grid), "column kernel: N=%d or %d detector rows out of range", g.N, g.B);
+      cone_prescale_t_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(g, w.t.tab0, w.t.tab2, pvh, sino, w.sino_s);
+      INRCT_CHECK_LAUNCH("backproject3d (ray scale)");
+      const size_t smem = sizeof(float2) * g.V + sizeof(float) * kColWarps * kColStrip;  // < 48 KB
+      dim3 grd(ceil_div(g.N, kColWarps), g.N);
+      if (g.N <= 256) {
+        backproject3d_col_kernel<8><<<grd, 32 * kColWarps, smem, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
+                                                                        w.sino_s, image);
+      } else {
+        backproject3d_col_kernel<16><<<grd, 32 * kColWarps, smem, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
+                                                                         w.sino_s, image);
+      }
+      INRCT_CHECK_LAUNCH("backproject3d (column kernel)");
+      return INRCT_OK;
+    }
     cone_prescale_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(g, w.t.tab0, w.t.tab2, pvh, sino, w.sino_s);
     INRCT_CHECK_LAUNCH("backproject3d (ray scale)");
     dim3 blk(32, 4);
@@ -1196,6 +1375,7 @@ int tune_impl(const inrct_geom* geom, const inrct_grid* grid, void* ws, size_t w
   std::vector<int> cands;
   if (cone) {
     cands = {4, 8, 16, 32};
+    if (col_kernel_fits(geom, grid)) cands.insert(cands.begin(), 0);
   } else {
     const int mx = max_bp_splits(geom, grid), df = default_bp_splits(geom, grid);
     for (int k = 1; k < mx; k *= 2) cands.push_back(k);

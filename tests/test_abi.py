@@ -168,7 +168,10 @@ def test_projector_plans_default_without_tuning(L):
     # 2-D: 8 segments; view splits = min(ceil(456 / tiles), views / 8) = min(114, 11)
     assert p == {"seg": 8, "bp_splits": 11, "zc": 8, "tuned": False}
     g3 = synth.GeomSpec("cone3d", 64, 10, 96, 96, sod=200.0, sdd=300.0)
-    assert inrct.tune_plan(g3) == {"seg": 4, "bp_splits": 1, "zc": 8, "tuned": False}
+    # cone adjoint: the column kernel (zc = 0) where it fits (N <= 512, <= 1024 detector rows)
+    assert inrct.tune_plan(g3) == {"seg": 4, "bp_splits": 1, "zc": 0, "tuned": False}
+    g4 = synth.GeomSpec("cone3d", 600, 10, 96, 96, sod=2000.0, sdd=3000.0)
+    assert inrct.tune_plan(g4) == {"seg": 4, "bp_splits": 1, "zc": 8, "tuned": False}
     gd, grd = inrct.geom_desc(g2), inrct.grid_desc(2, 64)
     nb = L.inrct_tune_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
     assert nb > 0
@@ -186,9 +189,12 @@ def test_pinned_plans_are_validated_on_the_host(L):
     inrct.tune_set(g2, 16, 3, 8)                        # 16 segments per ray, 3 view splits
     assert inrct.tune_plan(g2) == {"seg": 16, "bp_splits": 3, "zc": 8, "tuned": True}
     g3 = synth.GeomSpec("cone3d", 64, 10, 96, 96, sod=200.0, sdd=300.0)
+    inrct.tune_set(g3, 2, 1, 0)                         # the column kernel fits this geometry
+    assert inrct.tune_plan(g3)["zc"] == 0
+    g4 = synth.GeomSpec("cone3d", 600, 10, 96, 96, sod=2000.0, sdd=3000.0)
     big = synth.GeomSpec("par2d", 2048, 30, 2900)
     for g, plan in [(g2, (3, 1, 8)), (g2, (1, 1, 8)), (g2, (8, 0, 8)), (g2, (8, 12, 8)), (g2, (8, 1, 5)),
-                    (g3, (1, 1, 8)), (g3, (16, 1, 8)), (big, (8, 1, 64))]:
+                    (g3, (1, 1, 8)), (g3, (16, 1, 8)), (g4, (2, 1, 0)), (big, (8, 1, 64))]:
         with pytest.raises(inrct.InrctError) as e:
             inrct.tune_set(g, *plan)
         assert e.value.code == 1
