@@ -415,17 +415,17 @@ def run_batched(args, probs, rank, world, local, dev):
     batch.close()
 
 
-def projector_roofline(g, m_step, per, hbm_peak, peak_src, name, zc=None):
+def projector_roofline(g, m_step, per, hbm_peak, peak_src, name, zc=None, seg=None):
     """Rates of P and P^T from the stage profile against the measured HBM bandwidth, under both
     byte models: compulsory bytes (P: image in, sinogram, residual out and y in: 4n + 12m;
     P^T: sinogram in, image out: 4n + 4m) and the per-view streaming model (the image read once
     per view, 4nV + 4m, and 12m / 4m of sinogram traffic), with the DRAM bytes per launch of the
-    committed ncu record where one matches the current source (the cone adjoint's record is that
-    of the kernel the plan runs: zc = 0 the column kernel)."""
+    committed ncu record where one matches the current source (the cone record is that of the
+    kernel the plan runs: seg = 1 the row-patch projector, zc = 0 the column adjoint)."""
     out = {}
     V = g.V
-    for key, stage, sino_bytes, traffic_key in (("project", "project_loss", 12.0, "project3d_kernel" if g.d == 3
-                                                 else "project2d_kernel"),
+    for key, stage, sino_bytes, traffic_key in (("project", "project_loss", 12.0, ("project3d_rows_kernel" if seg == 1
+                                                  else "project3d_kernel") if g.d == 3 else "project2d_kernel"),
                                                 ("backproject", "backproject", 4.0,
                                                  ("backproject3d_col_kernel" if zc == 0 else "backproject3d_kernel")
                                                  if g.d == 3 else "backproject2d_tile_kernel")):
@@ -746,7 +746,8 @@ def run_single(args, w, rank, world, local, dev, steps, warmup, e2e_steps, cpu_b
         key = "vjp_dw_gemm_reduce" if n_idx <= VJP_CHUNK else "vjp_rest (further chunks + dW GEMMs)"
         kernels[key] = {"ms": per["vjp_dw_gemm_reduce"], "TFLOP/s": f_dw / per["vjp_dw_gemm_reduce"] / 1e9}
     m_step = g.m // S                                # rays per step (a view subset when S > 1)
-    roof_proj = projector_roofline(g, m_step, per, hbm_peak, peak_src, w.name, plans[0]["zc"])
+    roof_proj = projector_roofline(g, m_step, per, hbm_peak, peak_src, w.name, plans[0]["zc"],
+                                   plans[0]["seg"])
     pair_ms = per["project_loss"] + per["backproject"]
     dominant = max(("eval_mlp_kernel", "vjp_mlp_kernel"), key=lambda k: per[k])
     flops = f_eval if dominant == "eval_mlp_kernel" else f_vjp

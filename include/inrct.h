@@ -381,7 +381,8 @@ int inrct_check_index_set(const inrct_grid* grid, const int32_t* idx, int64_t n_
  *
  * A plan is the launch shape of project()/backproject() for one geometry: the
  * ray segments per block of the forward projector (2-D: 4, 8 or 16; cone: 2, 4
- * or 8), the view splits of the 2-D adjoint (1 up to twice the default, at most
+ * or 8, or 1: whole rays, 32 detector columns by 4 detector rows per block, the cone default),
+ * the view splits of the 2-D adjoint (1 up to twice the default, at most
  * n_views / 8) and the voxels per thread along z of the cone adjoint (4, 8, 16 or 32; or 0,
  * one warp per (x, y) column of the volume, for N <= 512 and at most 1024 detector rows, the
  * default where it applies).

@@ -169,9 +169,9 @@ def test_projector_plans_default_without_tuning(L):
     assert p == {"seg": 8, "bp_splits": 11, "zc": 8, "tuned": False}
     g3 = synth.GeomSpec("cone3d", 64, 10, 96, 96, sod=200.0, sdd=300.0)
     # cone adjoint: the column kernel (zc = 0) where it fits (N <= 512, <= 1024 detector rows)
-    assert inrct.tune_plan(g3) == {"seg": 4, "bp_splits": 1, "zc": 0, "tuned": False}
+    assert inrct.tune_plan(g3) == {"seg": 1, "bp_splits": 1, "zc": 0, "tuned": False}
     g4 = synth.GeomSpec("cone3d", 600, 10, 96, 96, sod=2000.0, sdd=3000.0)
-    assert inrct.tune_plan(g4) == {"seg": 4, "bp_splits": 1, "zc": 8, "tuned": False}
+    assert inrct.tune_plan(g4) == {"seg": 1, "bp_splits": 1, "zc": 8, "tuned": False}
     gd, grd = inrct.geom_desc(g2), inrct.grid_desc(2, 64)
     nb = L.inrct_tune_ws_bytes(ctypes.byref(gd), ctypes.byref(grd))
     assert nb > 0
@@ -194,7 +194,7 @@ def test_pinned_plans_are_validated_on_the_host(L):
     g4 = synth.GeomSpec("cone3d", 600, 10, 96, 96, sod=2000.0, sdd=3000.0)
     big = synth.GeomSpec("par2d", 2048, 30, 2900)
     for g, plan in [(g2, (3, 1, 8)), (g2, (1, 1, 8)), (g2, (8, 0, 8)), (g2, (8, 12, 8)), (g2, (8, 1, 5)),
-                    (g3, (1, 1, 8)), (g3, (16, 1, 8)), (g4, (2, 1, 0)), (big, (8, 1, 64))]:
+                    (g3, (3, 1, 8)), (g3, (16, 1, 8)), (g4, (2, 1, 0)), (big, (8, 1, 64))]:
         with pytest.raises(inrct.InrctError) as e:
             inrct.tune_set(g, *plan)
         assert e.value.code == 1

@@ -41,7 +41,7 @@ def test_tuned_plans_match_the_oracle(g):
     v0 = inrct.backproject(g, rd).cpu().numpy()
     plan = inrct.tune(g)
     assert plan["tuned"]
-    assert plan["seg"] in ((2, 4, 8) if g.kind == "cone3d" else (4, 8, 16))
+    assert plan["seg"] in ((1, 2, 4, 8) if g.kind == "cone3d" else (4, 8, 16))
     assert plan["zc"] in ((0, 4, 8, 16, 32) if g.kind == "cone3d" and g.N <= 512 else (4, 8, 16, 32))
     assert plan["bp_splits"] >= 1
     if g.kind != "cone3d":
