@@ -700,14 +700,18 @@ __global__ void cone_prescale_t_kernel(GeomDev g, const int4* __restrict__ t0, c
 // of the lanes idle on average).  The warp first stages the detector column's rows that can reach
 // the volume ([view][column][row] sinogram: one coalesced read) in shared memory; each lane then
 // sweeps its chunk exactly as backproject3d_kernel<VL> does.  N <= 32 VL, at most kColStrip rows.
+// With V4 (B a multiple of 4 and sino_t 16-byte aligned) the strip is staged in 16-byte copies
+// from the aligned row at or below its first row.
 constexpr int kColStrip = 1024;
 constexpr int kColWarps = 8;
-template <int VL>
+template <int VL, bool V4>
 __global__ void __launch_bounds__(32 * kColWarps, 4) backproject3d_col_kernel(GeomDev g, const int4* __restrict__ t0,
     const int4* __restrict__ t1, const float2* __restrict__ views, int64_t CzF,
     const float* __restrict__ sino_t, float* __restrict__ vol) {
-  extern __shared__ float2 sv[];  // [V] view directions, then kColWarps strips of kColStrip rows
-  float* strips = reinterpret_cast<float*>(sv + g.V);
+  // [V] view directions (padded to an even count: the strips start 16-byte aligned), then
+  // kColWarps strips of kColStrip rows
+  extern __shared__ float2 sv[];
+  float* strips = reinterpret_cast<float*>(sv + ((g.V + 1) & ~1));
   for (int k = threadIdx.x; k < g.V; k += blockDim.x) sv[k] = views[k];
   __syncthreads();
   const int N = g.N, A = g.A, B = g.B;
@@ -762,7 +766,17 @@ __global__ void __launch_bounds__(32 * kColWarps, 4) backproject3d_col_kernel(Ge
         const int sh = min(B - 1, (int)floorf(fmaxf(cz0, cz1) + hb));
         if (sl > sh) continue;
         __syncwarp();  // the previous strip is no longer read
-        for (int i = lane; i <= sh - sl; i += 32) strip[i] = __ldg(scol + sl + i);
+        int s0 = sl;   // the row held in strip[0]
+        if constexpr (V4) {
+          // rows s0 .. 4 floor(sh / 4) + 3: inside the column (B % 4 == 0) and at most B rows
+          s0 = sl & ~3;
+          const float4* src = reinterpret_cast<const float4*>(scol + s0);
+          float4* dst = reinterpret_cast<float4*>(strip);
+#pragma unroll 2
+          for (int i = lane; i <= (sh - s0) >> 2; i += 32) dst[i] = __ldg(src + i);
+        } else {
+          for (int i = lane; i <= sh - sl; i += 32) strip[i] = __ldg(scol + sl + i);
+        }
         __syncwarp();
         if (z0 >= N) continue;
         // this lane's chunk: the row sweep of backproject3d_kernel, its rows clipped to the strip
@@ -778,7 +792,7 @@ __global__ void __launch_bounds__(32 * kColWarps, 4) backproject3d_col_kernel(Ge
         const int64_t Zf = CzF + (int64_t)mr * Hh + dj * (((int64_t)mr * Kk) >> 16) - ((int64_t)z0 << 32);
         const float u0 = (float)Zf * 2.3283064365386963e-10f;  // * 2^-32
         const float du = 2.f * fabsf(hg);
-        const float* sp = strip + (bfirst - sl);
+        const float* sp = strip + (bfirst - s0);
         float rr = 0.f, u = u0;
         while (rr < nrow && u < -1.f) {
           rr += 1.f;
@@ -1119,7 +1133,7 @@ static int default_bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
 // adjoint (1 up to twice the default, at most one split per 8 views) and the voxels per
 // thread along z of the cone adjoint (4, 8, 16 or 32; 0 selects backproject3d_col_kernel, one warp
 // per (x, y) column, where it fits: N <= 512, at most kColStrip detector rows; 501^3 P^T 30.1 ->
-// 23.1 ms against 32 voxels per thread).  Without tuning the defaults above apply;
+// 20.6 ms against 32 voxels per thread).  Without tuning the defaults above apply;
 // tune_impl times every candidate on the caller's stream and keeps the fastest in a
 // process-wide table keyed by the geometry's kind and sizes, which every later call
 // consults.  Workspaces are sized for the largest candidate, so a workspace sized before
@@ -1345,15 +1359,18 @@ static int backproject_run(const inrct_geom* geom, const inrct_grid* grid, const
       INRCT_REQUIRE(col_kernel_fits(geom, grid), "column kernel: N=%d or %d detector rows out of range", g.N, g.B);
       cone_prescale_t_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(g, w.t.tab0, w.t.tab2, pvh, sino, w.sino_s);
       INRCT_CHECK_LAUNCH("backproject3d (ray scale)");
-      const size_t smem = sizeof(float2) * g.V + sizeof(float) * kColWarps * kColStrip;  // < 48 KB
+      const size_t smem = sizeof(float2) * ((g.V + 1) & ~1) + sizeof(float) * kColWarps * kColStrip;  // < 48 KB
+      const bool v4 = g.B % 4 == 0 && reinterpret_cast<uintptr_t>(w.sino_s) % 16 == 0;
       dim3 grd(ceil_div(g.N, kColWarps), g.N);
+#define INRCT_COL(VL, V4)                                                                                    \
+  backproject3d_col_kernel<VL, V4><<<grd, 32 * kColWarps, smem, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF, \
+                                                                      w.sino_s, image)
       if (g.N <= 256) {
-        backproject3d_col_kernel<8><<<grd, 32 * kColWarps, smem, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
-                                                                        w.sino_s, image);
+        if (v4) INRCT_COL(8, true); else INRCT_COL(8, false);
       } else {
-        backproject3d_col_kernel<16><<<grd, 32 * kColWarps, smem, st>>>(g, w.t.tab0, w.t.tab1, w.t.views, CzF,
-                                                                         w.sino_s, image);
+        if (v4) INRCT_COL(16, true); else INRCT_COL(16, false);
       }
+#undef INRCT_COL
       INRCT_CHECK_LAUNCH("backproject3d (column kernel)");
       return INRCT_OK;
     }

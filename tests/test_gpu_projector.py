@@ -36,6 +36,8 @@ CASES = [
     synth.GeomSpec("cone3d", 48, 12, 80, 72, sod=150.0, sdd=230.0, span=2 * math.pi),
     synth.GeomSpec("cone3d", 33, 5, 47, 39, du=1.2, dv=0.9, sod=70.0, sdd=100.0, span=2 * math.pi),
     synth.GeomSpec("par2d", 2, 1, 3),                                        # degenerate tiny
+    # odd view count with rows a multiple of 4: the cone adjoint's 16-byte strip copies
+    synth.GeomSpec("cone3d", 40, 7, 52, 44, du=1.1, sod=120.0, sdd=180.0, span=2 * math.pi),
 ]
 
 
