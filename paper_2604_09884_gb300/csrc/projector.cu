@@ -428,8 +428,10 @@ __global__ void __launch_bounds__(32 * SEG)
 // neighbouring rows run far apart in launch order).  Same samples and weights as
 // project3d_kernel; the sum runs in two accumulators, even and odd samples, added at the end, so
 // its rounding chain is as short as that of the two-segment plan (sinograms agree with it to
-// about 4e-7 relative) and the two FMA chains are independent.
+// about 4e-7 relative) and the two FMA chains are independent.  OFF32 (N <= 1024, so N^3 + N^2 <
+// 2^31) forms the tap addresses from 32-bit offsets, stepping j N by N along the ray.
 constexpr int kRowsPerBlock = 4;
+template <bool OFF32>
 __global__ void __launch_bounds__(32 * kRowsPerBlock)
     project3d_rows_kernel(const int4* __restrict__ t0, const int4* __restrict__ t1,
                           const float* __restrict__ t2, int A, int B, int N, float pv_half, int64_t CzF,
@@ -462,16 +464,27 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock)
     float s0 = 0.f, s1 = 0.f;
     int64_t uq = Uq + (int64_t)(lo - jref) * Sq;
     int64_t uz = cr.Z0 + (int64_t)(lo - jref) * cr.Sz;
+    const int NN32 = N * N;
+    int jN = lo * N;
     auto sample = [&](int j, float& acc) {
       int iq, iz;
       float fq, fz;
       split_fx(uq, iq, fq);
       split_fx(uz, iz, fz);
       const float wq0 = __fsub_rn(1.f, fq), wz0 = __fsub_rn(1.f, fz);
-      const bool q0ok = iq >= 0 && iq < N, q1ok = iq >= -1 && iq + 1 < N;
-      const bool z0ok = iz >= 0 && iz < N, z1ok = iz >= -1 && iz + 1 < N;
-      const float* p0 = base + (ptrdiff_t)iz * (ptrdiff_t)NN + (ptrdiff_t)j * N + iq;
-      const float* p1 = p0 + NN;
+      // 0 <= i < N and -1 <= i < N - 1 as unsigned compares
+      const bool q0ok = (unsigned)iq < (unsigned)N, q1ok = (unsigned)(iq + 1) < (unsigned)N;
+      const bool z0ok = (unsigned)iz < (unsigned)N, z1ok = (unsigned)(iz + 1) < (unsigned)N;
+      const float* p0;
+      const float* p1;
+      if constexpr (OFF32) {
+        p0 = base + (iz * NN32 + jN + iq);
+        p1 = p0 + NN32;
+        jN += N;
+      } else {
+        p0 = base + (ptrdiff_t)iz * (ptrdiff_t)NN + (ptrdiff_t)j * N + iq;
+        p1 = p0 + NN;
+      }
       const float v00 = (z0ok && q0ok) ? __ldg(p0) : 0.f;
       const float v01 = (z0ok && q1ok) ? __ldg(p0 + 1) : 0.f;
       const float v10 = (z1ok && q0ok) ? __ldg(p1) : 0.f;
@@ -1133,7 +1146,7 @@ static int default_bp_splits(const inrct_geom* geom, const inrct_grid* grid) {
 //
 // A plan fixes the launch shape of P and P^T for one geometry: the ray segments per
 // block of the forward (2-D 4, 8 or 16; cone 2, 4 or 8, or 1: whole rays in patches of
-// kRowsPerBlock detector rows, project3d_rows_kernel, the cone default; 501^3 P 18.5 -> 16.9 ms
+// kRowsPerBlock detector rows, project3d_rows_kernel, the cone default; 501^3 P 18.5 -> 14.3 ms
 // against 2 segments), the view splits of the 2-D
 // adjoint (1 up to twice the default, at most one split per 8 views) and the voxels per
 // thread along z of the cone adjoint (4, 8, 16 or 32; 0 selects backproject3d_col_kernel, one warp
@@ -1288,8 +1301,13 @@ static int project_run(const inrct_geom* geom, const inrct_grid* grid, const flo
     cone_consts(g, &pvh, &CzF);
     if (plan.seg == 1) {  // project3d_rows_kernel
       dim3 grr(ceil_div(g.A, 32), g.V, ceil_div(g.B, kRowsPerBlock));
-      project3d_rows_kernel<<<grr, dim3(32, kRowsPerBlock), 0, st>>>(w.t.tab0, w.t.tab1, w.t.tab2, g.A, g.B, N, pvh,
-                                                                      CzF, image, w.imgT, sino, y, resid, w.loss_part);
+#define INRCT_PR(OFF32)                                                                                 \
+  project3d_rows_kernel<OFF32><<<grr, dim3(32, kRowsPerBlock), 0, st>>>(w.t.tab0, w.t.tab1, w.t.tab2, g.A, g.B, N, \
+                                                                      pvh, CzF, image, w.imgT, sino, y, resid,  \
+                                                                      w.loss_part)
+      if (N <= 1024) INRCT_PR(true);
+      else INRCT_PR(false);
+#undef INRCT_PR
       INRCT_CHECK_LAUNCH("project3d (rows)");
       if (y) {
         reduce_f64_kernel<<<1, 1024, 0, st>>>(w.loss_part, (int64_t)grr.x * grr.y * grr.z, loss_out);
