@@ -308,13 +308,15 @@ __global__ void __launch_bounds__(32 * SEG)
     const int per = (hi - lo + SEG - 1) / SEG;
     const int j0 = lo + s * per, j1 = min(hi, j0 + per);
     int64_t u = U0 + (int64_t)(j0 - jref) * S4;
-    for (int j = j0; j < j1; ++j, u += S4) {
+    int jN = j0 * N;  // 32-bit row offset: N^2 <= 4096^2
+    for (int j = j0; j < j1; ++j, u += S4, jN += N) {
       int i0;
       float f;
       split_fx(u, i0, f);
-      const float* row = base + (size_t)j * N;
-      const float v0 = (i0 >= 0 && i0 < N) ? __ldg(row + i0) : 0.f;
-      const float v1 = (i0 >= -1 && i0 + 1 < N) ? __ldg(row + i0 + 1) : 0.f;
+      const float* row = base + jN;
+      // 0 <= i0 < N and -1 <= i0 < N - 1 as unsigned compares
+      const float v0 = (unsigned)i0 < (unsigned)N ? __ldg(row + i0) : 0.f;
+      const float v1 = (unsigned)(i0 + 1) < (unsigned)N ? __ldg(row + i0 + 1) : 0.f;
       sum = fmaf(__fsub_rn(1.f, f), v0, fmaf(f, v1, sum));
     }
   }
